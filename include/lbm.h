@@ -1,0 +1,174 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) time step of the weakly-compressible
+ * D2Q9 multi-relaxation-time lattice Boltzmann scheme with the absorbing-layer
+ * damping terms of Xu & Sagaut, "Analysis of the absorbing layers for the
+ * weakly-compressible lattice Boltzmann schemes" (arXiv:1203.6350).
+ *
+ * The scheme (Sec. 2, Eq. blbs-abc-1 with Gamma = chi I, Eq. eq:gamma):
+ *
+ *   f_i(x + c_i, t + 1) = f_i + Lambda_ij (f^eq_j(rho*, u*) - f_j)
+ *                         + chi(x) (f^ref_i - f*_i),       Lambda = M^-1 S M,
+ *
+ * with three choices of (f^ref, f*) (Secs. 2.2.1-2.2.3): type I f^eq(q_ref)
+ * and f; type II f^eq(q_ref) and f^eq(rho*, u*); type III the linear
+ * equilibria of both.  rho*, j* = rho* u* follow the Guo parameterisation
+ * with weights n, m, solved exactly:
+ *   rho* = (rho + n chi rho_ref) / (1 + n chi),  j* = (j + m chi j_ref) / (1 + m chi).
+ * The velocity set and M are those of App. A.1:
+ *   c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - delta t = 1, lattice units, c_s^2 = 1/3.
+ *  - Fields passed in or out are FP64, [ny][nx] row-major (x fastest).
+ *  - The lattice is double-buffered in device memory as 9 planes per buffer
+ *    of populations stored as DEVIATIONS g_i = f_i - f^eq_i(rho0, u0) from the
+ *    far-field state given to lbm_create (FP64, FP32, or 16-bit with a fixed
+ *    power-of-two scale per plane).
+ *  - "Time" counts steps; lbm_init_equilibrium sets time 0.
+ *  - Boundary: LBM_BC_DIRICHLET_EQ makes every population that would stream
+ *    in from outside equal to f^eq(rho0, u0), at every time level including
+ *    t = 0; LBM_BC_PERIODIC wraps both axes.
+ *  - Calls that launch work are asynchronous on the handle's stream unless
+ *    they say they synchronise.  Calls on one handle must not overlap from
+ *    several host threads.
+ *
+ * Return codes: LBM_OK (0); a positive value is a warning (the call did its
+ * work); a negative value is an error (the call did nothing unless it says
+ * otherwise).  lbm_last_error() gives a message for the last non-zero code.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx* lbm_handle;
+
+/* Storage of the populations.  F16DEV / BF16DEV keep 16-bit deviations; the
+ * arithmetic is FP32 for every storage but F64. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16DEV = 2, LBM_BF16DEV = 3 } lbm_storage;
+
+/* Damping term (Sec. 2.2): none, type I (Eq. app:newbgka), type II
+ * (Eq. app:newbgka2), type III (Eq. app:bgk_no2ordor2). */
+typedef enum {
+    LBM_SPONGE_NONE = 0,
+    LBM_SPONGE_I = 1,
+    LBM_SPONGE_II = 2,
+    LBM_SPONGE_III = 3
+} lbm_variant;
+
+typedef enum { LBM_BC_DIRICHLET_EQ = 0, LBM_BC_PERIODIC = 1 } lbm_bc;
+
+/* Relaxation rates: s[k] is the diagonal of S in the row order of M
+ * (App. A.1): s[0..2] act on the conserved rows rho, j_x, j_y (rate s_c,
+ * which multiplies rho* - rho and j* - j), s[3] = s_e, s[4] = s_eps,
+ * s[5..6] = s_q, s[7..8] = s_nu.  All nine equal gives the BGK scheme the
+ * paper analyses.  n, m are the weights of the Guo parameterisation. */
+typedef struct {
+    double s[9];
+    double n;
+    double m;
+} lbm_rates;
+
+/* Optional device allocator.  alloc returns a device pointer (>= 256-byte
+ * aligned) or NULL; free releases it.  ctx is passed back unchanged.  The
+ * library calls them inside lbm_create, lbm_destroy, and the first
+ * lbm_init_equilibrium / lbm_moments that uses host buffers (a staging area
+ * of 24 bytes per cell, kept until lbm_destroy). */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* ctx);
+    void* ctx;
+} lbm_allocator;
+
+#define LBM_OK 0
+#define LBM_WARN_UNSTABLE_PARAMS 1 /* chi > 4/s (type II/III), s + chi > 2 (type I), s_k outside (0, 2) */
+#define LBM_ERR_ARG (-1)           /* bad argument: nothing was done */
+#define LBM_ERR_OOM (-2)           /* device allocation failed */
+#define LBM_ERR_CUDA (-3)          /* a CUDA call failed; see lbm_last_error */
+#define LBM_ERR_NONFINITE (-4)     /* the state holds NaN or Inf (diagnostics found it) */
+#define LBM_ERR_STATE (-5)         /* call out of order (e.g. step before init) */
+
+/* Create a lattice of nx * ny cells (1 <= nx, ny; nx * ny <= 2^31 - 1) with
+ * far-field state (rho0 > 0, u0) -- the deviation base and the Dirichlet
+ * boundary state -- relaxation rates *rates (Sec. 2.1), boundary bc, on the
+ * CUDA stream cuda_stream (a cudaStream_t, borrowed; NULL = legacy default
+ * stream).  alloc = NULL uses cudaMalloc / cudaFree.  The damping term is
+ * off until lbm_set_sponge.  On success *out owns two population buffers of
+ * 9 * ny * pitch elements each (pitch = nx rounded up to 128 bytes).
+ * Returns LBM_WARN_UNSTABLE_PARAMS if some s_k is outside (0, 2) (the paper's
+ * constraint, Sec. 2.1), LBM_ERR_ARG, LBM_ERR_OOM or LBM_ERR_CUDA. */
+int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, double uy0,
+               const lbm_rates* rates, lbm_bc bc, void* cuda_stream, const lbm_allocator* alloc,
+               lbm_handle* out);
+
+/* Set the damping term: variant, per-axis strengths chi_x[nx], chi_y[ny]
+ * (host arrays, >= 0, copied; the strength at cell (ix, iy) is
+ * max(chi_x[ix], chi_y[iy])), and the reference state q_ref = (rho_ref,
+ * u_ref) of Eq. (eq:reff).  Takes effect from the next lbm_step.
+ * Returns LBM_WARN_UNSTABLE_PARAMS when max chi exceeds the paper's critical
+ * value (4/s_nu for types II and III, Eq. criticalchi; 2 - s_nu for type I,
+ * Eq. effectrelax), LBM_ERR_ARG for NULL / negative / non-finite input. */
+int lbm_set_sponge(lbm_handle h, lbm_variant variant, const double* chi_x, const double* chi_y,
+                   double rho_ref, double ux_ref, double uy_ref);
+
+/* Time 0: f = f^eq(rho(x), u(x)) at every cell (Sec. 4.1 initialises the
+ * pulse at equilibrium), then the boundary rule.  rho, ux, uy are FP64
+ * [ny][nx]; on_device != 0 means they are device pointers (read on the
+ * handle's stream), else host pointers (copied; the call synchronises the
+ * stream).  Resets the step counter. */
+int lbm_init_equilibrium(lbm_handle h, const double* rho, const double* ux, const double* uy,
+                         int on_device);
+
+/* Advance nsteps >= 0 time steps: one fused kernel per step (pull-stream,
+ * moments, rho* and j*, MRT relaxation, damping term, back-transform,
+ * store), asynchronous on the handle's stream. */
+int lbm_step(lbm_handle h, int nsteps);
+
+/* Fields at the current time: rho_dev = rho - rho0, ux, uy (FP64 [ny][nx];
+ * any pointer may be NULL to skip it).  on_device != 0: device pointers,
+ * asynchronous; else host pointers and the call synchronises. */
+int lbm_moments(lbm_handle h, double* rho_dev, double* ux, double* uy, int on_device);
+
+/* FP64 reductions over the cells x0 <= ix < x1, y0 <= iy < y1 at the current
+ * time (host out[6], synchronises):
+ *   out[0] sum rho'           out[1] sum (j_x - rho0 u0x)   out[2] sum (j_y - rho0 u0y)
+ *   out[3] acoustic energy sum [c_s^2 rho'^2 / (2 rho0) + rho0 |u - u0|^2 / 2]
+ *   out[4] sum rho'^2 (numerator of E_L2, Sec. 4.1, with rho_ref = rho0)
+ *   out[5] number of cells with a non-finite rho' or u
+ * Returns LBM_ERR_NONFINITE (with out filled) when out[5] > 0. */
+int lbm_diagnostics(lbm_handle h, int x0, int y0, int x1, int y1, double out[6]);
+
+/* Checkpoint: the raw population buffer of the current time (bytes =
+ * lbm_state_bytes) and the step counter.  on_device selects device or host
+ * memory for dst/src; host transfers synchronise. */
+size_t lbm_state_bytes(lbm_handle h);
+int lbm_get_state(lbm_handle h, void* dst, size_t bytes, int on_device, int64_t* time);
+int lbm_set_state(lbm_handle h, const void* src, size_t bytes, int on_device, int64_t time);
+
+/* Steps taken since lbm_init_equilibrium (or set by lbm_set_state). */
+int64_t lbm_time(lbm_handle h);
+
+/* Replace the handle's stream (borrowed; NULL = legacy default stream). */
+int lbm_set_stream(lbm_handle h, void* cuda_stream);
+
+/* Free the device buffers and the handle.  NULL is allowed. */
+void lbm_destroy(lbm_handle h);
+
+/* Message of the last non-zero return on h (h = NULL: of the last
+ * lbm_create that failed).  Owned by the library. */
+const char* lbm_last_error(lbm_handle h);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H_ */

@@ -1,0 +1,433 @@
+// C-ABI layer of liblbm (declared in include/lbm.h): handle management,
+// parameter checks, host-side constants of the step, and launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using lbm::Geometry;
+using lbm::StepConst;
+
+struct lbm_ctx {
+    int nx = 0, ny = 0;
+    int storage = 0;
+    int bc = 0;
+    int device = 0;
+    double rho0 = 1, ux0 = 0, uy0 = 0;
+    lbm_rates rates{};
+    cudaStream_t stream = nullptr;
+    lbm_allocator alloc{};
+    bool custom_alloc = false;
+    Geometry geo{};
+    size_t buf_bytes = 0;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;  // buffer holding the post-collision state the next pull reads
+    void* chi_x = nullptr;  // device, compute precision
+    void* chi_y = nullptr;
+    size_t chi_bytes_x = 0, chi_bytes_y = 0;
+    double* diag = nullptr;  // kDiagBlocks * kDiag partials followed by kDiag results
+    size_t diag_bytes = 0;
+    double* staging = nullptr;  // 3 FP64 fields for host transfers, allocated on first use
+    size_t staging_bytes = 0;
+    int variant = 0;
+    double rho_f = 1, ux_f = 0, uy_f = 0;
+    StepConst<double> k64{};
+    StepConst<float> k32{};
+    bool initialised = false;
+    int64_t time = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(lbm_ctx* h, int code, const std::string& msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where) {
+    return fail(h, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(lbm_ctx* h, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (h->custom_alloc) return h->alloc.alloc(bytes, h->alloc.ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(lbm_ctx* h, void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (h->custom_alloc)
+        h->alloc.free(p, bytes, h->alloc.ctx);
+    else
+        cudaFree(p);
+}
+
+// Make the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+// Moment equilibria m^eq(rho, j) of the second-order D2Q9 equilibrium, in the
+// row order of M (App. A.1).
+void meq(double rho, double jx, double jy, double out[9]) {
+    const double q = (jx * jx + jy * jy) / rho;
+    out[0] = rho;
+    out[1] = jx;
+    out[2] = jy;
+    out[3] = -2.0 * rho + 3.0 * q;
+    out[4] = rho - 3.0 * q;
+    out[5] = -jx;
+    out[6] = -jy;
+    out[7] = (jx * jx - jy * jy) / rho;
+    out[8] = jx * jy / rho;
+}
+
+template <typename CT>
+void fill_const(const lbm_ctx* h, StepConst<CT>& k) {
+    for (int i = 0; i < 9; ++i) k.s[i] = static_cast<CT>(h->rates.s[i]);
+    k.n = static_cast<CT>(h->rates.n);
+    k.m = static_cast<CT>(h->rates.m);
+    const double jx0 = h->rho0 * h->ux0, jy0 = h->rho0 * h->uy0;
+    k.rho0 = static_cast<CT>(h->rho0);
+    k.jx0 = static_cast<CT>(jx0);
+    k.jy0 = static_cast<CT>(jy0);
+    k.jj0 = static_cast<CT>(jx0 * jx0 + jy0 * jy0);
+    k.jxy0 = static_cast<CT>(jx0 * jx0 - jy0 * jy0);
+    k.pxy0 = static_cast<CT>(jx0 * jy0);
+    const double jfx = h->rho_f * h->ux_f, jfy = h->rho_f * h->uy_f;
+    k.drf = static_cast<CT>(h->rho_f - h->rho0);
+    k.djfx = static_cast<CT>(jfx - jx0);
+    k.djfy = static_cast<CT>(jfy - jy0);
+    double mr[9], mb[9];
+    meq(h->rho_f, jfx, jfy, mr);
+    meq(h->rho0, jx0, jy0, mb);
+    for (int i = 0; i < 9; ++i) k.dmeq_ref[i] = static_cast<CT>(mr[i] - mb[i]);
+}
+
+void refresh_consts(lbm_ctx* h) {
+    fill_const<double>(h, h->k64);
+    fill_const<float>(h, h->k32);
+}
+
+int ensure_staging(lbm_ctx* h) {
+    const size_t need = 3 * sizeof(double) * (size_t)h->nx * h->ny;
+    if (h->staging && h->staging_bytes >= need) return LBM_OK;
+    dev_free(h, h->staging, h->staging_bytes);
+    h->staging = static_cast<double*>(dev_alloc(h, need));
+    h->staging_bytes = h->staging ? need : 0;
+    if (!h->staging) return fail(h, LBM_ERR_OOM, "staging allocation failed");
+    return LBM_OK;
+}
+
+lbm::BaseState base_of(const lbm_ctx* h) { return lbm::BaseState{h->rho0, h->ux0, h->uy0}; }
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_version(void) { return "liblbm 0.1 (D2Q9 MRT + absorbing layers, sm_103a)"; }
+
+const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, double uy0,
+               const lbm_rates* rates, lbm_bc bc, void* cuda_stream, const lbm_allocator* alloc,
+               lbm_handle* out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || (long long)nx * ny > 2147483647LL)
+        return fail(nullptr, LBM_ERR_ARG, "lattice size out of range");
+    if (storage < LBM_F64 || storage > LBM_BF16DEV) return fail(nullptr, LBM_ERR_ARG, "bad storage");
+    if (bc != LBM_BC_DIRICHLET_EQ && bc != LBM_BC_PERIODIC) return fail(nullptr, LBM_ERR_ARG, "bad bc");
+    if (!rates) return fail(nullptr, LBM_ERR_ARG, "rates is NULL");
+    if (!(rho0 > 0) || !is_finite(rho0) || !is_finite(ux0) || !is_finite(uy0))
+        return fail(nullptr, LBM_ERR_ARG, "far-field state must be finite with rho0 > 0");
+    int warn = LBM_OK;
+    for (int i = 0; i < 9; ++i) {
+        if (!is_finite(rates->s[i])) return fail(nullptr, LBM_ERR_ARG, "non-finite relaxation rate");
+        if (!(rates->s[i] > 0 && rates->s[i] < 2)) warn = LBM_WARN_UNSTABLE_PARAMS;
+    }
+    if (!is_finite(rates->n) || !is_finite(rates->m) || rates->n < 0 || rates->m < 0)
+        return fail(nullptr, LBM_ERR_ARG, "Guo weights n, m must be finite and >= 0");
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail(nullptr, LBM_ERR_ARG, "allocator lacks alloc or free");
+
+    lbm_ctx* h = new lbm_ctx();
+    h->nx = nx;
+    h->ny = ny;
+    h->storage = storage;
+    h->bc = bc;
+    h->rho0 = rho0;
+    h->ux0 = ux0;
+    h->uy0 = uy0;
+    h->rates = *rates;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (alloc) {
+        h->alloc = *alloc;
+        h->custom_alloc = true;
+    }
+    h->rho_f = rho0;
+    h->ux_f = ux0;
+    h->uy_f = uy0;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+    const size_t es = lbm::storage_bytes(storage);
+    const long long per_row = (long long)((nx * es + 127) / 128 * 128 / es);
+    h->geo = Geometry{nx, ny, per_row, per_row * ny};
+    h->buf_bytes = 9 * (size_t)h->geo.plane * es;
+    const size_t cts = storage == LBM_F64 ? 8 : 4;
+    h->chi_bytes_x = nx * cts;
+    h->chi_bytes_y = ny * cts;
+    h->diag_bytes = sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag);
+    h->buf[0] = dev_alloc(h, h->buf_bytes);
+    h->buf[1] = dev_alloc(h, h->buf_bytes);
+    h->chi_x = dev_alloc(h, h->chi_bytes_x);
+    h->chi_y = dev_alloc(h, h->chi_bytes_y);
+    h->diag = static_cast<double*>(dev_alloc(h, h->diag_bytes));
+    if (!h->buf[0] || !h->buf[1] || !h->chi_x || !h->chi_y || !h->diag) {
+        lbm_destroy(h);
+        return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
+    }
+    // zero the absorbing strength and both buffers (a zero deviation is the far-field state)
+    e = cudaMemsetAsync(h->chi_x, 0, h->chi_bytes_x, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->chi_y, 0, h->chi_bytes_y, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, h->buf_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->buf_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        lbm_destroy(h);
+        return cuda_fail(nullptr, e, "initial clear");
+    }
+    refresh_consts(h);
+    *out = h;
+    if (warn) g_create_error = "a relaxation rate lies outside (0, 2)";
+    return warn;
+}
+
+int lbm_set_sponge(lbm_handle h, lbm_variant variant, const double* chi_x, const double* chi_y,
+                   double rho_ref, double ux_ref, double uy_ref) {
+    if (!h) return LBM_ERR_ARG;
+    if (variant < LBM_SPONGE_NONE || variant > LBM_SPONGE_III) return fail(h, LBM_ERR_ARG, "bad variant");
+    if (!chi_x || !chi_y) return fail(h, LBM_ERR_ARG, "chi arrays are NULL");
+    if (!(rho_ref > 0) || !is_finite(rho_ref) || !is_finite(ux_ref) || !is_finite(uy_ref))
+        return fail(h, LBM_ERR_ARG, "reference state must be finite with rho_ref > 0");
+    double chi_max = 0.0;
+    for (int i = 0; i < h->nx; ++i) {
+        if (!(chi_x[i] >= 0) || !is_finite(chi_x[i])) return fail(h, LBM_ERR_ARG, "chi_x must be finite and >= 0");
+        chi_max = std::fmax(chi_max, chi_x[i]);
+    }
+    for (int i = 0; i < h->ny; ++i) {
+        if (!(chi_y[i] >= 0) || !is_finite(chi_y[i])) return fail(h, LBM_ERR_ARG, "chi_y must be finite and >= 0");
+        chi_max = std::fmax(chi_max, chi_y[i]);
+    }
+    DeviceGuard dg(h->device);
+    cudaError_t e;
+    if (h->storage == LBM_F64) {
+        e = cudaMemcpyAsync(h->chi_x, chi_x, h->chi_bytes_x, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->chi_y, chi_y, h->chi_bytes_y, cudaMemcpyHostToDevice, h->stream);
+    } else {
+        std::vector<float> fx(chi_x, chi_x + h->nx), fy(chi_y, chi_y + h->ny);
+        e = cudaMemcpyAsync(h->chi_x, fx.data(), h->chi_bytes_x, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->chi_y, fy.data(), h->chi_bytes_y, cudaMemcpyHostToDevice, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_sponge copy");
+    h->variant = variant;
+    h->rho_f = rho_ref;
+    h->ux_f = ux_ref;
+    h->uy_f = uy_ref;
+    refresh_consts(h);
+    const double s_nu = h->rates.s[7];
+    if ((variant == LBM_SPONGE_II || variant == LBM_SPONGE_III) && chi_max > 4.0 / s_nu)
+        return fail(h, LBM_WARN_UNSTABLE_PARAMS, "max chi exceeds the critical value 4/s");
+    if (variant == LBM_SPONGE_I && s_nu + chi_max > 2.0)
+        return fail(h, LBM_WARN_UNSTABLE_PARAMS, "type I with s + chi > 2 is unstable");
+    return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_handle h, const double* rho, const double* ux, const double* uy,
+                         int on_device) {
+    if (!h) return LBM_ERR_ARG;
+    if (!rho || !ux || !uy) return fail(h, LBM_ERR_ARG, "field pointer is NULL");
+    DeviceGuard dg(h->device);
+    const double *dr = rho, *dx = ux, *dy = uy;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        int rc = ensure_staging(h);
+        if (rc) return rc;
+        const size_t n = (size_t)h->nx * h->ny;
+        double* s = h->staging;
+        e = cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "lbm_init_equilibrium upload");
+        dr = s;
+        dx = s + n;
+        dy = s + 2 * n;
+    }
+    h->cur = 0;
+    e = lbm::launch_init(h->storage, h->buf[0], h->geo, base_of(h), dr, dx, dy, h->bc, h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_init_equilibrium");
+    h->initialised = true;
+    h->time = 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, int nsteps) {
+    if (!h) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init_equilibrium / lbm_set_state");
+    DeviceGuard dg(h->device);
+    for (int t = 0; t < nsteps; ++t) {
+        const void* src = h->buf[h->cur];
+        void* dst = h->buf[1 - h->cur];
+        cudaError_t e;
+        switch (h->storage) {
+            case LBM_F64:
+                e = lbm::launch_step_f64(src, dst, h->geo, h->k64, static_cast<const double*>(h->chi_x),
+                                         static_cast<const double*>(h->chi_y), h->variant, h->bc, h->stream);
+                break;
+            case LBM_F32:
+                e = lbm::launch_step_f32(src, dst, h->geo, h->k32, static_cast<const float*>(h->chi_x),
+                                         static_cast<const float*>(h->chi_y), h->variant, h->bc, h->stream);
+                break;
+            case LBM_F16DEV:
+                e = lbm::launch_step_f16(src, dst, h->geo, h->k32, static_cast<const float*>(h->chi_x),
+                                         static_cast<const float*>(h->chi_y), h->variant, h->bc, h->stream);
+                break;
+            default:
+                e = lbm::launch_step_bf16(src, dst, h->geo, h->k32, static_cast<const float*>(h->chi_x),
+                                          static_cast<const float*>(h->chi_y), h->variant, h->bc, h->stream);
+                break;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step launch");
+        h->cur = 1 - h->cur;
+        ++h->time;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle h, double* rho_dev, double* ux, double* uy, int on_device) {
+    if (!h) return LBM_ERR_ARG;
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_moments before initialisation");
+    DeviceGuard dg(h->device);
+    const size_t n = (size_t)h->nx * h->ny;
+    double *dr = rho_dev, *dx = ux, *dy = uy;
+    if (!on_device) {
+        int rc = ensure_staging(h);
+        if (rc) return rc;
+        dr = rho_dev ? h->staging : nullptr;
+        dx = ux ? h->staging + n : nullptr;
+        dy = uy ? h->staging + 2 * n : nullptr;
+    }
+    cudaError_t e = lbm::launch_moments(h->storage, h->buf[h->cur], h->geo, base_of(h), h->bc, dr, dx,
+                                        dy, h->stream);
+    if (e == cudaSuccess && !on_device) {
+        if (rho_dev) e = cudaMemcpyAsync(rho_dev, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_moments");
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_handle h, int x0, int y0, int x1, int y1, double out[6]) {
+    if (!h) return LBM_ERR_ARG;
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_diagnostics before initialisation");
+    if (x0 < 0 || y0 < 0 || x1 > h->nx || y1 > h->ny || x0 > x1 || y0 > y1)
+        return fail(h, LBM_ERR_ARG, "region outside the lattice");
+    DeviceGuard dg(h->device);
+    double* partial = h->diag;
+    double* res = h->diag + lbm::kDiagBlocks * lbm::kDiag;
+    cudaError_t e = lbm::launch_diagnostics(h->storage, h->buf[h->cur], h->geo, base_of(h), h->bc, x0, y0,
+                                            x1, y1, partial, res, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, lbm::kDiag * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_diagnostics");
+    if (out[5] > 0) return fail(h, LBM_ERR_NONFINITE, "the state holds non-finite values");
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(lbm_handle h) { return h ? h->buf_bytes : 0; }
+
+int lbm_get_state(lbm_handle h, void* dst, size_t bytes, int on_device, int64_t* time) {
+    if (!h) return LBM_ERR_ARG;
+    if (!dst || bytes != h->buf_bytes) return fail(h, LBM_ERR_ARG, "dst / bytes do not match lbm_state_bytes");
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaMemcpyAsync(dst, h->buf[h->cur], bytes,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_state");
+    if (time) *time = h->time;
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle h, const void* src, size_t bytes, int on_device, int64_t time) {
+    if (!h) return LBM_ERR_ARG;
+    if (!src || bytes != h->buf_bytes) return fail(h, LBM_ERR_ARG, "src / bytes do not match lbm_state_bytes");
+    if (time < 0) return fail(h, LBM_ERR_ARG, "time < 0");
+    DeviceGuard dg(h->device);
+    h->cur = 0;
+    cudaError_t e = cudaMemcpyAsync(h->buf[0], src, bytes,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_state");
+    h->time = time;
+    h->initialised = true;
+    return LBM_OK;
+}
+
+int64_t lbm_time(lbm_handle h) { return h ? h->time : -1; }
+
+int lbm_set_stream(lbm_handle h, void* cuda_stream) {
+    if (!h) return LBM_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    dev_free(h, h->buf[0], h->buf_bytes);
+    dev_free(h, h->buf[1], h->buf_bytes);
+    dev_free(h, h->chi_x, h->chi_bytes_x);
+    dev_free(h, h->chi_y, h->chi_bytes_y);
+    dev_free(h, h->diag, h->diag_bytes);
+    dev_free(h, h->staging, h->staging_bytes);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Internal declarations shared by the kernels and the C-ABI layer of liblbm.
+// Not part of the public interface (include/lbm.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// Geometry of one double-buffered population store: 9 planes of ny rows of
+// `pitch` elements; plane i starts at i * plane elements from the buffer base.
+struct Geometry {
+    int nx, ny;
+    long long pitch;  // elements per row (row bytes are a multiple of 128)
+    long long plane;  // elements per plane = ny * pitch
+};
+
+// Per-lattice constants of the step, in the compute precision CT (double for
+// FP64 storage, float otherwise).  All "d" quantities are deviations from the
+// far-field (base) state rho0, j0 = rho0 u0.
+template <typename CT>
+struct StepConst {
+    CT s[9];          // relaxation rates, row order of M
+    CT n, m;          // Guo weights
+    CT rho0, jx0, jy0;
+    CT jj0;           // |j0|^2
+    CT jxy0;          // jx0^2 - jy0^2
+    CT pxy0;          // jx0 * jy0
+    CT drf, djfx, djfy;  // reference state minus base: rho_f - rho0, j_f - j0
+    CT dmeq_ref[9];   // m^eq(rho_f, j_f) - m^eq(rho0, j0), evaluated in FP64 on the host
+};
+
+enum Storage { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
+enum Variant { kNone = 0, kTypeI = 1, kTypeII = 2, kTypeIII = 3 };
+enum Bc { kDirichlet = 0, kPeriodic = 1 };
+
+// Step launchers, one translation unit per storage type.  src holds the
+// post-collision state of time t (pulled), dst receives that of time t + 1.
+cudaError_t launch_step_f64(const void* src, void* dst, const Geometry& g,
+                            const StepConst<double>& k, const double* chi_x,
+                            const double* chi_y, int variant, int bc, cudaStream_t st);
+cudaError_t launch_step_f32(const void* src, void* dst, const Geometry& g,
+                            const StepConst<float>& k, const float* chi_x, const float* chi_y,
+                            int variant, int bc, cudaStream_t st);
+cudaError_t launch_step_f16(const void* src, void* dst, const Geometry& g,
+                            const StepConst<float>& k, const float* chi_x, const float* chi_y,
+                            int variant, int bc, cudaStream_t st);
+cudaError_t launch_step_bf16(const void* src, void* dst, const Geometry& g,
+                             const StepConst<float>& k, const float* chi_x, const float* chi_y,
+                             int variant, int bc, cudaStream_t st);
+
+// Base-state parameters of the auxiliary kernels (always FP64).
+struct BaseState {
+    double rho0, ux0, uy0;
+};
+
+// Time-0 store from FP64 fields (device pointers, [ny][nx]).
+cudaError_t launch_init(int storage, void* dst, const Geometry& g, const BaseState& b,
+                        const double* rho, const double* ux, const double* uy, int bc,
+                        cudaStream_t st);
+// Fields of the current time (device outputs, any may be null).
+cudaError_t launch_moments(int storage, const void* src, const Geometry& g, const BaseState& b,
+                           int bc, double* rho_dev, double* ux, double* uy, cudaStream_t st);
+// Diagnostics: first pass writes `blocks` partial sums of kDiag doubles to
+// partial[], second pass reduces them in a fixed order into out[kDiag].
+constexpr int kDiag = 6;
+constexpr int kDiagBlocks = 608;  // 4 per SM on a 152-SM GB300
+cudaError_t launch_diagnostics(int storage, const void* src, const Geometry& g,
+                               const BaseState& b, int bc, int x0, int y0, int x1, int y1,
+                               double* partial, double* out, cudaStream_t st);
+
+// Bytes per stored population.
+inline size_t storage_bytes(int storage) {
+    return storage == kF64 ? 8 : storage == kF32 ? 4 : 2;
+}
+
+}  // namespace lbm

@@ -1,0 +1,271 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 of the compared field against the oracle's):
+  FP64 storage: 1e-10.  Both sides are FP64 but take different routes
+    (moments of deviations vs populations; the oracle carries ~1 values, so
+    its own round-off is ~1e-16 absolute against a 1e-3 signal, ~1e-13
+    relative per step; 1e-10 leaves room for 300-5000 steps).
+  FP32 storage: 1e-5 (the stated target for FP32 deviation storage).
+  16-bit deviation storage: 1e-2 for FP16 at rho' amplitude 1e-3 (the stated
+    target); BF16 keeps 8 significant bits and is held to 5e-2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from helpers import rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-5, "f16dev": 1e-2, "bf16dev": 5e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6350_gb300 import lbm
+
+    lbm.load()
+
+
+# --------------------------------------------------- 100 x 100 pulse ----
+
+_oracle_cache = {}
+
+
+def _oracle(w, steps):
+    key = (w.name, w.variant, steps, w.nx, w.ny, tuple(w.u0))
+    if key not in _oracle_cache:
+        _oracle_cache[key] = run_oracle(w, steps)
+    return _oracle_cache[key]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["none", "II", "III"])
+def test_small_pulse_all_fields(storage, variant):
+    """100 x 100, nu = 1e-3, eps = 1e-3, b = 3, 20-cell layer chi = 0.1 (d/20)^2,
+    300 steps: rho', u_x, u_y against the oracle."""
+    w = wl.small_pulse(variant, storage)
+    ref = _oracle(w, w.steps)
+    got = run_gpu(w, storage)
+    tol = TOL[storage]
+    assert rel_l2(got[0], ref[0]) <= tol
+    assert rel_l2(got[1], ref[1]) <= tol
+    assert rel_l2(got[2], ref[2]) <= tol
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_small_pulse_type_I(storage):
+    """Type I on the same workload has s + chi > 2 in most of the layer and grows
+    (Eq. effectrelax).  Parity is checked while the field is still moderate
+    (60 steps); after 300 steps both sides must have blown up alike."""
+    w = wl.small_pulse("I", storage)
+    ref = _oracle(w, 60)
+    got = run_gpu(w, storage, 60)
+    assert rel_l2(got[0], ref[0]) <= TOL[storage]
+    r300 = _oracle(w, 300)[0]
+    g300 = run_gpu(w, storage, 300)[0]
+    big_r = (~np.isfinite(r300)).any() or np.abs(r300).max() > 1.0
+    big_g = (~np.isfinite(g300)).any() or np.abs(g300).max() > 1.0
+    assert big_r and big_g
+
+
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+def test_small_pulse_16bit_deviation_storage(storage):
+    w = wl.small_pulse("II", storage)
+    ref = _oracle(w, w.steps)
+    got = run_gpu(w, storage)
+    assert rel_l2(got[0], ref[0]) <= TOL[storage]
+
+
+def test_time_zero_fields_equal_the_initial_condition():
+    w = wl.small_pulse("II", "f32").with_(u0=(0.05, 0.01), u_f=(0.05, 0.01))
+    for storage in ("f64", "f32"):
+        got = run_gpu(w, storage, 0)
+        ref = _oracle(w, 0)
+        assert rel_l2(got[0], ref[0]) <= TOL[storage] * 1e-2
+        np.testing.assert_allclose(got[1], ref[1], atol=1e-7)
+
+
+# ------------------------------------------- tiny, ragged, periodic, MRT ----
+
+def _rand_workload(nx, ny, bc, variant, seed, mrt=True):
+    rng = np.random.default_rng(seed)
+    s = np.array([1.6, 1.6, 1.6, 1.1, 1.2, 1.3, 1.3, 1.9, 1.9]) if mrt else np.full(9, 1.95)
+    w = wl.Workload(name=f"rand-{nx}x{ny}", nx=nx, ny=ny, s=s, variant=variant, bc=bc, n=0.4,
+                    m=0.6, rho0=1.0, u0=(0.04, -0.02), rho_f=1.002, u_f=(0.05, -0.01),
+                    chi_x=rng.uniform(0, 0.5, nx), chi_y=rng.uniform(0, 0.5, ny),
+                    rho_dev=1e-3 * rng.standard_normal((ny, nx)), steps=25, storage="f64")
+    return w
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 7), (130, 3), (257, 129), (33, 64)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("variant", ["none", "I", "II", "III"])
+def test_ragged_and_tiny_lattices(shape, bc, variant):
+    """Tiles of 128 x 2 cells with ragged edges, 1-cell lattices, periodic wrap,
+    distinct MRT rates, mean flow, q_ref different from the far field, random
+    chi: FP64 and FP32 storage against the oracle after 25 steps."""
+    nx, ny = shape
+    w = _rand_workload(nx, ny, bc, variant, seed=nx * 1000 + ny)
+    ref = run_oracle(w)
+    for storage in ("f64", "f32"):
+        got = run_gpu(w, storage)
+        for a, b in zip(got, ref):
+            assert rel_l2(a, b) <= TOL[storage], (storage, rel_l2(a, b))
+
+
+# ------------------------------------------------------------ diagnostics ----
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_diagnostics_match_the_oracle(storage):
+    from oracle import diagnostics as dg
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.small_pulse("II", storage).with_(u0=(0.05, 0.0), u_f=(0.05, 0.0))
+    ref = _oracle(w, 120)
+    for region in [(0, 0, 100, 100), (20, 20, 80, 80), (5, 37, 6, 99), (0, 0, 0, 0)]:
+        want = dg.reduce_fields(*ref, rho0=1.0, u0=w.u0, region=region)
+        with lbm.Lattice.from_workload(w, storage=storage) as lat:
+            lat.step(120)
+            got = lat.diagnostics(region)
+        scale = np.array([np.abs(ref[0]).sum(), np.abs(ref[0]).sum(), np.abs(ref[0]).sum(),
+                          want[3], want[4], 1.0]) + 1e-300
+        assert np.all(np.abs(got - want) <= (TOL[storage] * 10) * scale), (region, got, want)
+
+
+def test_nonfinite_state_is_reported():
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.small_pulse("I", "f32")
+    with lbm.Lattice.from_workload(w) as lat:
+        lat.step(2000)
+        out = lat.diagnostics()
+        assert out[5] > 0
+        with pytest.raises(lbm.LbmError) as ei:
+            lat.diagnostics(raise_nonfinite=True)
+        assert ei.value.code == lbm.LBM_ERR_NONFINITE
+
+
+def test_conservation_on_a_periodic_lattice():
+    """chi = 0, periodic: sum rho' and sum j' are invariants (FP64 storage)."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = _rand_workload(96, 80, "periodic", "none", seed=5)
+    w = w.with_(chi_x=np.zeros(96), chi_y=np.zeros(80))
+    with lbm.Lattice.from_workload(w, storage="f64") as lat:
+        d0 = lat.diagnostics()
+        lat.step(500)
+        d1 = lat.diagnostics()
+    assert abs(d1[0] - d0[0]) < 1e-12
+    assert abs(d1[1] - d0[1]) < 1e-12 and abs(d1[2] - d0[2]) < 1e-12
+
+
+# ---------------------------------------------------- state and errors ----
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev"])
+def test_checkpoint_round_trip_is_bit_exact(storage):
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.small_pulse("II", storage)
+    with lbm.Lattice.from_workload(w) as lat:
+        lat.step(10)
+        buf, t = lat.get_state()
+        assert t == 10
+        lat.step(15)
+        a = lat.moments()[0]
+        lat.set_state(buf, t)
+        assert lat.time == 10
+        lat.step(15)
+        b = lat.moments()[0]
+    np.testing.assert_array_equal(a, b)
+
+
+def test_step_before_init_is_a_state_error():
+    from paper_1203_6350_gb300 import lbm
+
+    lat = lbm.Lattice(8, 8, "f32")
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(1)
+    assert ei.value.code == lbm.LBM_ERR_STATE
+    lat.close()
+
+
+def test_unstable_parameters_warn():
+    from paper_1203_6350_gb300 import lbm
+
+    lat = lbm.Lattice(8, 8, "f32", s=1.99)
+    with pytest.warns(RuntimeWarning):
+        lat.set_sponge("II", np.full(8, 4 / 1.99 + 0.1), np.zeros(8))
+    with pytest.warns(RuntimeWarning):
+        lat.set_sponge("I", np.full(8, 0.05), np.zeros(8))
+    with pytest.raises(lbm.LbmError):
+        lat.set_sponge("II", np.full(8, -1.0), np.zeros(8))
+    lat.close()
+
+
+def test_device_buffers_and_cuda_allocator():
+    """Device-pointer inputs/outputs and the plain cudaMalloc allocator give the
+    same bits as host buffers and the torch allocator."""
+    import torch
+
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.small_pulse("III", "f32").with_(u0=(0.03, 0.0), u_f=(0.03, 0.0))
+    host = run_gpu(w, "f32", 50)
+    lat = lbm.Lattice(w.nx, w.ny, "f32", w.rho0, w.u0, w.s, bc=w.bc, allocator="cuda")
+    lat.set_sponge(w.variant, w.chi_x, w.chi_y)
+    rho, ux, uy = (torch.from_numpy(a).cuda() for a in w.initial_fields())
+    lat.init_equilibrium(rho, ux, uy)
+    lat.step(50)
+    dev = lat.moments(device=True)
+    torch.cuda.synchronize()
+    lat.close()
+    for a, b in zip(host, dev):
+        np.testing.assert_array_equal(a, b.cpu().numpy())
+
+
+# ------------------------------------------------------- full-size runs ----
+
+def test_mean_flow_pulse_1024_parity_200_steps():
+    """The 1024 x 1024 Mach-0.2 mean-flow workload in FP32, in the launch
+    configuration the benchmark times, against the oracle after 200 steps."""
+    w = wl.mean_flow_pulse(seed=0, variant="II", storage="f32", steps=200)
+    ref = run_oracle(w)
+    got = run_gpu(w, "f32")
+    assert rel_l2(got[0], ref[0]) <= TOL["f32"]
+    assert rel_l2(got[1] - w.u0[0], ref[1] - w.u0[0]) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("variant", ["II", "III"])
+def test_mean_flow_pulse_1024_full_run_properties(variant):
+    """The full 5000-step run stays finite and the layer removes the pulse: the
+    interior acoustic energy left is a small fraction of the initial one."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.mean_flow_pulse(seed=0, variant=variant, storage="f32")
+    W = w.width
+    reg = (W, W, w.nx - W, w.ny - W)
+    with lbm.Lattice.from_workload(w) as lat:
+        e0 = lat.diagnostics(reg)[3]
+        lat.step(w.steps)
+        d = lat.diagnostics(reg)
+    assert d[5] == 0
+    assert d[3] < 0.05 * e0
+
+
+def test_quiescent_lattice_stays_exactly_at_rest():
+    """A medium at rest with q_ref = the far field is a fixed point: every deviation
+    stays exactly zero at any size (here 4096^2, 20 steps, FP32 and FP16)."""
+    from paper_1203_6350_gb300 import lbm
+
+    for storage in ("f32", "f16dev"):
+        w = wl.quiescent(4096, storage=storage, steps=20)
+        with lbm.Lattice.from_workload(w) as lat:
+            lat.step(20)
+            d = lat.diagnostics()
+        assert d[0] == 0 and d[3] == 0 and d[4] == 0 and d[5] == 0
