@@ -26,7 +26,7 @@
  *     type I   (Eq. app:newbgka):       T_i = chi (f^eq_i(rho^f,u^f) - f_i)
  *     type II  (Eq. app:newbgka2):      T_i = chi (f^eq_i(rho^f,u^f) - f^eq_i(rho*,u*))
  *     type III (Eq. app:bgk_no2ordor2): T_i = chi (f^Leq_i(rho^f,j^f) - f^Leq_i(rho*,j*))
- *     none:                             T_i = 0
+ *     none:                             T_i = 0, and chi = 0 (no absorbing term at all)
  *   f_i(x + c_i, t + 1) = fhat_i(x, t)                               (Eq. blbs)
  *
  * Readings of points the paper leaves open (each is listed in the design doc):
@@ -156,6 +156,8 @@ int oracle_lambda(const double* s, double* out) {
  * with Gamma = chi I), for the chosen damping variant. */
 void oracle_collide_cell(const oracle_params* p, const double* lam, double chi, const double* f,
                          double* fhat) {
+    /* Without a damping term Gamma = 0, so F = 0 and rho* = rho, j* = j (Eq. blbs). */
+    if (p->variant == 0) chi = 0.0;
     double rho = 0.0, jx = 0.0, jy = 0.0;
     for (int i = 0; i < 9; ++i) {
         rho += f[i];

@@ -69,6 +69,8 @@ def step(f, chi, s, variant="II", n=0.5, m=0.5, rho_f=1.0, u_f=(0.0, 0.0), bc="d
          rho0=1.0, u0=(0.0, 0.0)):
     """One time step of the scheme.  f: [9, ny, nx]; chi: [ny, nx]."""
     lam = np.linalg.inv(M) @ np.diag(s) @ M
+    if variant == "none":  # no absorbing term: F = 0, so rho* = rho and j* = j
+        chi = np.zeros_like(chi)
     rho = f.sum(0)
     jx = np.tensordot(C[:, 0], f, 1)
     jy = np.tensordot(C[:, 1], f, 1)
