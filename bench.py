@@ -1,0 +1,404 @@
+"""Benchmark of the D2Q9 MRT + absorbing-layer step on GB300.
+
+One benchmark step is the whole hot path over one batch of synthetic input:
+the 1024 x 1024 mean-flow pulse workload (Mach 0.2 along x, pulse eps = 1e-3,
+b = 5 at a seeded interior point, 64-cell quadratic layer, seeded chi_max),
+solved from its equilibrium initial state for 5000 time steps once for each
+damping variant (I, II, III), FP32 deviation storage, with the reflected
+acoustic energy of each solve read back at the end.
+
+Output: one JSON line (rank 0).  value = whole-job MLUPS (cell updates per
+second / 1e6) over the timed steps, inputs resident on the device; e2e = the
+same metric through the C ABI with host buffers (upload of the initial fields
+and read-back of the final fields inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "D2Q9 MRT+sponge MLUPS"
+UNIT = "MLUPS"
+VARIANTS = ("I", "II", "III")
+SEED = 0
+BYTES_PER_CELL = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--lbm-steps", type=int, default=5000,
+                    help="time steps per solve (the workload's 5000 by default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_set(lbm_steps: int):
+    return [wl.mean_flow_pulse(seed=SEED, variant=v, storage="f32", steps=lbm_steps)
+            for v in VARIANTS]
+
+
+def layer_region(w):
+    W = w.width
+    return (W, W, w.nx - W, w.ny - W)
+
+
+# ----------------------------------------------------------- CPU oracle ----
+
+def time_oracle(works, steps_each: int, nthreads: int):
+    """Time the FP64 oracle on `steps_each` steps of each workload; returns
+    (cell updates, seconds)."""
+    from oracle import core
+
+    cells = 0
+    t = 0.0
+    for w in works:
+        prob = core.Problem(w.nx, w.ny, w.s, n=w.n, m=w.m, variant=w.variant, bc=w.bc,
+                            rho0=w.rho0, u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x,
+                            chi_y=w.chi_y)
+        st = core.State(prob, *w.initial_fields())
+        t0 = time.perf_counter()
+        st.run(steps_each, nthreads)
+        t += time.perf_counter() - t0
+        cells += w.cells * steps_each
+    return cells, t
+
+
+def cpu_baseline(works, budget_s: float = 15.0):
+    from oracle import core
+
+    core.build()
+    cores = core.omp_threads()
+    # calibrate on one step of one workload, then size the sample to the budget
+    c1, t1 = time_oracle(works[:1], 1, cores)
+    per_update = t1 / c1
+    steps_each = max(1, int(budget_s / (per_update * sum(w.cells for w in works))))
+    cells, t = time_oracle(works, steps_each, cores)
+    return {
+        "value": cells / t / 1e6,
+        "unit": UNIT,
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"{steps_each} time steps of each of the {len(works)} variant solves "
+                  f"({works[0].nx}x{works[0].ny}), FP64 population-space oracle, OpenMP over rows",
+    }
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    works = workload_set(args.lbm_steps)
+    from oracle import core
+
+    core.build()
+    cores = core.omp_threads()
+    c1, t1 = time_oracle(works[:1], 1, cores)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    steps_each = max(1, int(budget / (t1 / c1 * sum(w.cells for w in works))))
+    for _ in range(args.warmup):
+        time_oracle(works, 1, cores)
+    cells = 0
+    t = 0.0
+    for _ in range(args.steps):
+        c, dt = time_oracle(works, steps_each, cores)
+        cells += c
+        t += dt
+    value = cells / t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(works),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: {steps_each} time steps of each variant solve"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(works):
+    w = works[0]
+    return {
+        "workload": f"mean-flow pulse {w.nx}x{w.ny}, Mach 0.2, layer {w.width}, "
+                    f"chi_max {w.chi_max} (seed {SEED}), variants I/II/III, {w.steps} steps each",
+        "cells": w.cells, "steps_per_solve": w.steps, "solves_per_step": len(works),
+        "storage": w.storage, "variants": list(VARIANTS), "chi_max": w.chi_max,
+        "layer_width": w.width, "u0": list(w.u0), "seed": SEED,
+        "l2": "flushed (256 MB write) before each timed step; the 75 MB double-buffered state "
+              "of one solve stays L2-resident across its time steps",
+    }
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        self.dev = ids[device_index] if device_index < len(ids) else str(device_index)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- native ----
+
+def run_native(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1203_6350_gb300 import lbm
+
+    lbm.load()
+    works = workload_set(args.lbm_steps)
+
+    # the CPU baseline runs before any GPU work (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(works)
+
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    fields = [tuple(torch.from_numpy(a).to(dev) for a in w.initial_fields()) for w in works]
+    lats = []
+    with torch.cuda.stream(stream):
+        for w in works:
+            lat = lbm.Lattice(w.nx, w.ny, w.storage, w.rho0, w.u0, w.s, w.n, w.m, w.bc,
+                              stream=stream, device=local)
+            with_warn(lambda: lat.set_sponge(w.variant, w.chi_x, w.chi_y, w.rho_f, w.u_f))
+            lats.append(lat)
+    torch.cuda.synchronize()
+
+    step_ev = []  # (start, end) events around the lbm_step calls of each solve
+    refl = {}
+
+    def one_step(record: bool):
+        for w, lat, f in zip(works, lats, fields):
+            lat.init_equilibrium(*f)
+            e0 = lat.diagnostics(layer_region(w))[3]
+            if record:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            lat.step(w.steps)
+            if record:
+                b.record(stream)
+                step_ev.append((a, b))
+            d = lat.diagnostics(layer_region(w))
+            refl[w.variant] = (d[3] / e0) if (d[5] == 0 and e0 > 0) else None
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            one_step(False)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        s_ev = torch.cuda.Event(enable_timing=True)
+        e_ev = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s_ev.record(stream)
+            one_step(True)
+            e_ev.record(stream)
+        e_ev.synchronize()
+        times.append(s_ev.elapsed_time(e_ev) / 1e3)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    t_local = sum(times)
+    t_job = max_over_ranks(t_local, world, dev)
+    cells_per_step = sum(w.cells * w.steps for w in works)
+    value = world * cells_per_step * args.steps / t_job / 1e6
+
+    # roofline of the dominant kernel (the fused step): algorithmic bytes per launch
+    # over the average launch duration seen by events bracketing lbm_step
+    step_s = sum(a.elapsed_time(b) for a, b in step_ev) / 1e3
+    launches = sum(w.steps for w in works) * args.steps
+    per_launch = step_s / launches
+    bytes_launch = BYTES_PER_CELL[works[0].storage] * works[0].cells
+    peaks = measured_peaks()
+    achieved = bytes_launch / per_launch / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "kernel": "lbm::step_kernel<float, variant, Dirichlet>",
+            "bytes_per_launch": bytes_launch, "avg_launch_us": per_launch * 1e6,
+            "peak_source": peaks["source"]}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(works, lats, stream, dev, args.steps)
+
+    launches_total = args.steps * sum(w.steps + 1 + 4 for w in works)
+    for lat in lats:
+        lat.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict(works),
+            "parallelism": "replicas" if world > 1 else "single",
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches_total,
+            "reflected_energy": {k: refl.get(k) for k in VARIANTS},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def with_warn(fn):
+    import warnings
+
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", RuntimeWarning)
+        return fn()
+
+
+def max_over_ranks(t: float, world: int, dev) -> float:
+    if world == 1:
+        return t
+    import torch
+
+    x = torch.tensor([t], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+    return float(x.item())
+
+
+def run_e2e(works, lats, stream, dev, steps):
+    """Host-buffer path: pinned host fields -> lbm_init_equilibrium(host) ->
+    lbm_step -> lbm_moments(host) per solve, timed on the host clock."""
+    import torch
+
+    host_in = [tuple(torch.from_numpy(a).pin_memory() for a in w.initial_fields()) for w in works]
+    host_out = [tuple(torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory()
+                      for _ in range(3)) for w in works]
+    h2d = sum(sum(t.numel() * 8 for t in hi) for hi in host_in)
+    d2h = sum(sum(t.numel() * 8 for t in ho) for ho in host_out)
+    from paper_1203_6350_gb300 import lbm
+
+    def one(w, lat, hi, ho, nsteps):
+        lbm.check(lbm.lbm_init_equilibrium(lat.h, *(t.data_ptr() for t in hi), 0), lat.h, "init")
+        lbm.check(lbm.lbm_step(lat.h, nsteps), lat.h, "step")
+        lbm.check(lbm.lbm_moments(lat.h, *(t.data_ptr() for t in ho), 0), lat.h, "moments")
+
+    for w, lat, hi, ho in zip(works, lats, host_in, host_out):  # warm: staging buffers
+        one(w, lat, hi, ho, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for w, lat, hi, ho in zip(works, lats, host_in, host_out):
+            one(w, lat, hi, ho, w.steps)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    cells = sum(w.cells * w.steps for w in works) * steps
+    return {"value": cells / t / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
+    return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

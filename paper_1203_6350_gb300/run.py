@@ -1,0 +1,71 @@
+"""Run one lattice case through the C ABI and report its throughput.
+
+    python -m paper_1203_6350_gb300.run --side 4096 --storage f32 --steps 200
+
+Square lattice at rest (optionally with a centred pulse) with a ramped
+absorbing layer; prints one JSON line with MLUPS, algorithmic GB/s
+(bytes/cell/step x cells x steps / time) and the fraction of the measured HBM
+copy bandwidth.  Timing uses CUDA events on the lattice's stream after
+warm-up steps; the state is larger than L2 for sides >= 2048 in FP32.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--side", type=int, default=4096)
+    ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_CELL))
+    ap.add_argument("--variant", default="II", choices=["none", "I", "II", "III"])
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--width", type=int, default=128)
+    ap.add_argument("--pulse", action="store_true")
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import workloads as wl
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.quiescent(args.side, storage=args.storage, steps=args.steps, width=args.width,
+                     variant=args.variant, pulse=args.pulse)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = lbm.Lattice.from_workload(w, stream=stream)
+        lat.step(args.warmup)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(args.steps)
+        b.record(stream)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    cells = w.cells * args.steps
+    gbs = BYTES_PER_CELL[args.storage] * cells / t / 1e9
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peak = float(json.load(open(p))["hbm_gbs"])
+    d = lat.diagnostics()
+    lat.close()
+    print(json.dumps({
+        "case": f"{args.side}x{args.side} {args.storage} variant {args.variant} layer {args.width}",
+        "steps": args.steps, "mlups": cells / t / 1e6, "gbs": gbs,
+        "frac_of_measured_hbm": gbs / peak if peak else None, "us_per_step": 1e6 * t / args.steps,
+        "nonfinite_cells": d[5],
+    }))
+
+
+if __name__ == "__main__":
+    main()
