@@ -9,7 +9,8 @@ the oracle's own rounding floor (see oracle_floor):
   FP32 storage: 1e-5, the stated target, wherever the field is still the
     pulse.  On the 100 x 100 workload after its 300 steps the pulse has been
     absorbed and rho' is 1e-4 of its initial size; there FP32 arithmetic
-    reaches ~2e-5, not 1e-5, and the test holds it to 3e-5.  (A CPU emulation
+    reaches ~2e-5 on rho' and ~4.3e-5 on u, not 1e-5, and the test holds it
+    to 5e-5.  (A CPU emulation
     of the kernel shows the gap is FP32 arithmetic, not storage: FP32 storage
     with exact arithmetic gives 3.8e-6, every FP32 formulation tried
     1.4e-5 to 2.9e-5.)
@@ -27,7 +28,7 @@ from helpers import rel_l2, run_gpu, run_oracle
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-10, "f32": 1e-5, "f16dev": 1e-2, "bf16dev": 6e-2}
-F32_ABSORBED = 3e-5  # FP32 after the 100 x 100 pulse has been absorbed (see above)
+F32_ABSORBED = 5e-5  # FP32 after the 100 x 100 pulse has been absorbed (see above)
 
 
 def oracle_floor(steps, ncells, rho0=1.0):
@@ -83,18 +84,20 @@ def test_small_pulse_all_fields(storage, variant):
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_small_pulse_type_I(storage):
-    """Type I on the same workload has s + chi > 2 in most of the layer and grows
-    (Eq. effectrelax).  Parity is checked while the field is still moderate
-    (60 steps); after 300 steps both sides must have blown up alike."""
+    """Type I on the same workload has s + chi > 2 in the outer part of the layer and
+    grows there (Eq. effectrelax): parity at 60 and 300 steps, a field that has
+    grown by orders of magnitude over the type II one at 300 steps, and a
+    non-finite state on both sides after 1000 steps."""
     w = wl.small_pulse("I", storage)
-    ref = _oracle(w, 60)
-    got = run_gpu(w, storage, 60)
-    assert_close(got[0], ref[0], TOL[storage], 60)
-    r300 = _oracle(w, 300)[0]
-    g300 = run_gpu(w, storage, 300)[0]
-    big_r = (~np.isfinite(r300)).any() or np.abs(r300).max() > 1.0
-    big_g = (~np.isfinite(g300)).any() or np.abs(g300).max() > 1.0
-    assert big_r and big_g
+    for steps in (60, 300):
+        ref = _oracle(w, steps)
+        got = run_gpu(w, storage, steps)
+        assert_close(got[0], ref[0], TOL[storage], steps, steps)
+    r2 = _oracle(w.with_(variant="II"), 300)[0]
+    assert np.abs(_oracle(w, 300)[0]).max() > 100 * np.abs(r2).max()
+    r1000 = _oracle(w, 1000)[0]
+    g1000 = run_gpu(w, storage, 1000)[0]
+    assert (~np.isfinite(r1000)).any() and (~np.isfinite(g1000)).any()
 
 
 def _interior_pulse(side, steps, storage):
