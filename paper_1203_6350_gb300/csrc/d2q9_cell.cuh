@@ -21,6 +21,10 @@
 // keeps the ~1e-3 acoustic signal: every quantity below is a deviation from
 // the base state, and the quadratic equilibria are differenced in a form that
 // never subtracts two O(1) numbers.
+//
+// Where chi = 0 (the bulk of a lattice) rho* = rho, j* = j and the damping
+// term vanishes, so the conserved rows pass through unchanged; the bulk path
+// skips that algebra.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -91,55 +95,112 @@ struct Codec<__nv_bfloat16> {
     }
 };
 
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+// Reciprocal of a value near rho0^2.  FP32: the hardware approximation
+// (max 1 ulp); it only scales the |j|^2/rho terms of the equilibrium.
+__device__ __forceinline__ float rcp_eq(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_eq(double x) { return __drcp_rn(x); }
 
-// Collide one cell in place: g holds the nine pulled deviations on entry and
-// the post-collision deviations on exit.  chi is the absorbing strength here.
-template <typename CT, int VAR>
-__device__ __forceinline__ void collide(CT (&g)[9], CT chi, const StepConst<CT>& k) {
-    // m = M g (App. A.1), written as sums and differences
+// Moments m = M g (App. A.1), written as sums and differences.
+template <typename CT>
+__device__ __forceinline__ void moments9(const CT (&g)[9], CT (&m)[9]) {
     const CT a13 = g[1] - g[3], a24 = g[2] - g[4];
     const CT b57 = g[5] - g[7], c86 = g[8] - g[6];
-    const CT s14 = (g[1] + g[3]) + (g[2] + g[4]);
-    const CT s58 = (g[5] + g[7]) + (g[6] + g[8]);
-    CT m[9];
-    m[0] = g[0] + s14 + s58;                          // rho'
-    m[1] = a13 + b57 + c86;                           // j_x'
-    m[2] = a24 + b57 - c86;                           // j_y'
-    m[3] = CT(-4) * g[0] - s14 + CT(2) * s58;         // e
-    m[4] = CT(4) * g[0] - CT(2) * s14 + s58;          // epsilon
-    m[5] = CT(-2) * a13 + b57 + c86;                  // q_x
-    m[6] = CT(-2) * a24 + b57 - c86;                  // q_y
-    m[7] = (g[1] + g[3]) - (g[2] + g[4]);             // p_xx
-    m[8] = (g[5] + g[7]) - (g[6] + g[8]);             // p_xy
+    const CT p13 = g[1] + g[3], p24 = g[2] + g[4];
+    const CT p57 = g[5] + g[7], p68 = g[6] + g[8];
+    const CT s14 = p13 + p24, s58 = p57 + p68;
+    m[0] = g[0] + s14 + s58;                   // rho'
+    m[1] = a13 + b57 + c86;                    // j_x'
+    m[2] = a24 + b57 - c86;                    // j_y'
+    m[3] = CT(2) * s58 - s14 - CT(4) * g[0];   // e
+    m[4] = CT(4) * g[0] - CT(2) * s14 + s58;   // epsilon
+    m[5] = b57 + c86 - CT(2) * a13;            // q_x
+    m[6] = b57 - c86 - CT(2) * a24;            // q_y
+    m[7] = p13 - p24;                          // p_xx
+    m[8] = p57 - p68;                          // p_xy
+}
 
+// m^eq(rho*, j*) - m^eq(rho0, j0) for rows 3, 4, 7, 8 (the nonlinear ones),
+// without cancellation:
+//   |j*|^2/rho* - |j0|^2/rho0 = (rho0 (|j*|^2 - |j0|^2) - |j0|^2 drho*) / (rho* rho0).
+template <typename CT>
+__device__ __forceinline__ void quad_eq(CT drs, CT djx, CT djy, const StepConst<CT>& k, CT& e3,
+                                        CT& e4, CT& e7, CT& e8) {
+    const CT inv = rcp_eq((k.rho0 + drs) * k.rho0);
+    const CT ax = djx * (CT(2) * k.jx0 + djx);
+    const CT ay = djy * (CT(2) * k.jy0 + djy);
+    const CT q = (k.rho0 * (ax + ay) - k.jj0 * drs) * inv;
+    e3 = CT(3) * q - CT(2) * drs;
+    e4 = drs - CT(3) * q;
+    e7 = (k.rho0 * (ax - ay) - k.jxy0 * drs) * inv;
+    e8 = (k.rho0 * (djx * k.jy0 + k.jx0 * djy + djx * djy) - k.pxy0 * drs) * inv;
+}
+
+// g = M^T D^-1 m^+ for the post-collision moments.
+template <typename CT>
+__device__ __forceinline__ void back9(const CT (&mp)[9], CT (&g)[9]) {
+    const CT a0 = mp[0] * (CT(1) / CT(9));
+    const CT a1 = mp[1] * (CT(1) / CT(6)), a2 = mp[2] * (CT(1) / CT(6));
+    const CT a3 = mp[3] * (CT(1) / CT(36)), a4 = mp[4] * (CT(1) / CT(36));
+    const CT a5 = mp[5] * (CT(1) / CT(12)), a6 = mp[6] * (CT(1) / CT(12));
+    const CT a7 = mp[7] * CT(0.25), a8 = mp[8] * CT(0.25);
+    const CT e1 = a0 - a3 - CT(2) * a4;  // shared by the axis populations
+    const CT e5 = a0 + CT(2) * a3 + a4;  // shared by the diagonal populations
+    const CT x1 = a1 - CT(2) * a5, y1 = a2 - CT(2) * a6;
+    const CT x5 = a1 + a5, y5 = a2 + a6;
+    g[0] = a0 - CT(4) * a3 + CT(4) * a4;
+    g[1] = e1 + x1 + a7;
+    g[2] = e1 + y1 - a7;
+    g[3] = e1 - x1 + a7;
+    g[4] = e1 - y1 - a7;
+    g[5] = e5 + x5 + y5 + a8;
+    g[6] = e5 - x5 + y5 - a8;
+    g[7] = e5 - x5 - y5 + a8;
+    g[8] = e5 + x5 - y5 - a8;
+}
+
+// Collision where chi = 0: rho* = rho, j* = j, no damping term.  The
+// conserved rows are unchanged; the other six relax toward m^eq(rho, j).
+template <typename CT>
+__device__ __forceinline__ void collide_bulk(CT (&g)[9], const StepConst<CT>& k) {
+    CT m[9];
+    moments9(g, m);
+    CT e3, e4, e7, e8;
+    quad_eq(m[0], m[1], m[2], k, e3, e4, e7, e8);
+    CT mp[9];
+    mp[0] = m[0];
+    mp[1] = m[1];
+    mp[2] = m[2];
+    mp[3] = m[3] + k.s[3] * (e3 - m[3]);
+    mp[4] = m[4] + k.s[4] * (e4 - m[4]);
+    mp[5] = m[5] + k.s[5] * (-m[1] - m[5]);
+    mp[6] = m[6] + k.s[6] * (-m[2] - m[6]);
+    mp[7] = m[7] + k.s[7] * (e7 - m[7]);
+    mp[8] = m[8] + k.s[8] * (e8 - m[8]);
+    back9(mp, g);
+}
+
+// Collision with an absorbing strength chi > 0 and its Guo factors rn, rm.
+template <typename CT, int VAR>
+__device__ __forceinline__ void collide_layer(CT (&g)[9], CT chi, CT rn, CT rm,
+                                              const StepConst<CT>& k) {
+    CT m[9];
+    moments9(g, m);
     // rho*, j*: the Guo definitions solved exactly (sum F = chi (rho_f - rho*),
     // sum c F = chi (j_f - j*)), as deviations from the base state.
-    const CT rn = rcp(CT(1) + k.n * chi);
-    const CT rm = rcp(CT(1) + k.m * chi);
     const CT drs = (m[0] + k.n * chi * k.drf) * rn;
     const CT djxs = (m[1] + k.m * chi * k.djfx) * rm;
     const CT djys = (m[2] + k.m * chi * k.djfy) * rm;
-
-    // m^eq(rho*, j*) - m^eq(rho0, j0) without cancellation:
-    //   |j*|^2/rho* - |j0|^2/rho0 = (rho0 (|j*|^2 - |j0|^2) - |j0|^2 drho*) / (rho* rho0)
-    const CT inv = rcp((k.rho0 + drs) * k.rho0);
-    const CT ax = djxs * (CT(2) * k.jx0 + djxs);
-    const CT ay = djys * (CT(2) * k.jy0 + djys);
-    const CT q = (k.rho0 * (ax + ay) - k.jj0 * drs) * inv;
-    const CT pxx = (k.rho0 * (ax - ay) - k.jxy0 * drs) * inv;
-    const CT pxy = (k.rho0 * (djxs * k.jy0 + k.jx0 * djys + djxs * djys) - k.pxy0 * drs) * inv;
     CT meq[9];
     meq[0] = drs;
     meq[1] = djxs;
     meq[2] = djys;
-    meq[3] = CT(-2) * drs + CT(3) * q;
-    meq[4] = drs - CT(3) * q;
+    quad_eq(drs, djxs, djys, k, meq[3], meq[4], meq[7], meq[8]);
     meq[5] = -djxs;
     meq[6] = -djys;
-    meq[7] = pxx;
-    meq[8] = pxy;
 
     CT t[9];
     if (VAR == kTypeI) {
@@ -148,7 +209,7 @@ __device__ __forceinline__ void collide(CT (&g)[9], CT chi, const StepConst<CT>&
     } else if (VAR == kTypeII) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) t[i] = k.dmeq_ref[i] - meq[i];
-    } else if (VAR == kTypeIII) {
+    } else {  // type III: linear equilibria (rho, j, -2 rho, rho, -j, 0, 0)
         const CT dr = k.drf - drs, dx = k.djfx - djxs, dy = k.djfy - djys;
         t[0] = dr;
         t[1] = dx;
@@ -160,62 +221,53 @@ __device__ __forceinline__ void collide(CT (&g)[9], CT chi, const StepConst<CT>&
         t[7] = CT(0);
         t[8] = CT(0);
     }
-
-    // relax and damp, then scale by D^-1
-    CT a[9];
-    const CT dinv[9] = {CT(1) / CT(9),  CT(1) / CT(6),  CT(1) / CT(6),
-                        CT(1) / CT(36), CT(1) / CT(36), CT(1) / CT(12),
-                        CT(1) / CT(12), CT(1) / CT(4),  CT(1) / CT(4)};
+    CT mp[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        CT mp = m[i] + k.s[i] * (meq[i] - m[i]);
-        if (VAR != kNone) mp += chi * t[i];
-        a[i] = mp * dinv[i];
-    }
-
-    // g = M^T a
-    const CT e1 = a[0] - a[3] - CT(2) * a[4];  // axis populations share this
-    const CT e5 = a[0] + CT(2) * a[3] + a[4];  // diagonal populations share this
-    const CT x1 = a[1] - CT(2) * a[5], y1 = a[2] - CT(2) * a[6];
-    const CT x5 = a[1] + a[5], y5 = a[2] + a[6];
-    g[0] = a[0] - CT(4) * a[3] + CT(4) * a[4];
-    g[1] = e1 + x1 + a[7];
-    g[2] = e1 + y1 - a[7];
-    g[3] = e1 - x1 + a[7];
-    g[4] = e1 - y1 - a[7];
-    g[5] = e5 + x5 + y5 + a[8];
-    g[6] = e5 - x5 + y5 - a[8];
-    g[7] = e5 - x5 - y5 + a[8];
-    g[8] = e5 + x5 - y5 - a[8];
+    for (int i = 0; i < 9; ++i) mp[i] = m[i] + k.s[i] * (meq[i] - m[i]) + chi * t[i];
+    back9(mp, g);
 }
 
-// Offsets (in elements, within one plane) of the cells a population is pulled
-// from, and whether that cell is inside the lattice.  Population i at (x, y)
-// comes from (x - c_ix, y - c_iy).
+// Per-plane base pointers of one population buffer.
+template <typename T>
+struct PlanePtrs {
+    T* p[9];
+};
+
+// Neighbour offsets (elements within a plane) of a cell at (x, y) and whether
+// each neighbour is inside the lattice.  Population i at (x, y) is pulled from
+// (x - c_ix, y - c_iy).
 struct PullSites {
-    long long from_xm, from_xp, from_ym, from_yp;  // read x-1, x+1, y-1, y+1
+    int from_xm, from_xp, from_ym, from_yp;  // read x-1, x+1, y-1, y+1
     bool in_xm, in_xp, in_ym, in_yp;
 
-    template <int BC>
-    __device__ __forceinline__ void init(int x, int y, const Geometry& g) {
-        in_xm = x > 0;
-        in_xp = x < g.nx - 1;
-        in_ym = y > 0;
-        in_yp = y < g.ny - 1;
+    // Interior cells: every neighbour exists, no wrap.
+    __device__ __forceinline__ void interior(int pitch) {
         from_xm = -1;
         from_xp = 1;
-        from_ym = -g.pitch;
-        from_yp = g.pitch;
+        from_ym = -pitch;
+        from_yp = pitch;
+        in_xm = in_xp = in_ym = in_yp = true;
+    }
+    template <int BC>
+    __device__ __forceinline__ void edge(int x, int y, int nx, int ny, int pitch) {
+        in_xm = x > 0;
+        in_xp = x < nx - 1;
+        in_ym = y > 0;
+        in_yp = y < ny - 1;
+        from_xm = -1;
+        from_xp = 1;
+        from_ym = -pitch;
+        from_yp = pitch;
         if (BC == kPeriodic) {
-            if (!in_xm) from_xm = g.nx - 1;
-            if (!in_xp) from_xp = -(g.nx - 1);
-            if (!in_ym) from_ym = (long long)(g.ny - 1) * g.pitch;
-            if (!in_yp) from_yp = -(long long)(g.ny - 1) * g.pitch;
+            if (!in_xm) from_xm = nx - 1;
+            if (!in_xp) from_xp = -(nx - 1);
+            if (!in_ym) from_ym = (ny - 1) * pitch;
+            if (!in_yp) from_yp = -(ny - 1) * pitch;
         }
     }
     template <int I>
-    __device__ __forceinline__ long long offset() const {
-        long long o = 0;
+    __device__ __forceinline__ int offset() const {
+        int o = 0;
         if (cx(I) == 1) o += from_xm;
         if (cx(I) == -1) o += from_xp;
         if (cy(I) == 1) o += from_ym;
@@ -233,44 +285,50 @@ struct PullSites {
     }
 };
 
-// Pull population I of the cell at element offset o (the boundary rule gives
-// a zero deviation for Dirichlet far-field walls).
-template <typename T, int BC, int I>
-__device__ __forceinline__ typename Codec<T>::CT pull(const T* __restrict__ src, long long plane,
-                                                      long long o, const PullSites& ps) {
+// Pull population I of the cell at element offset o (a Dirichlet far-field
+// wall contributes a zero deviation).  CHECK = false: the cell is interior.
+template <typename T, int BC, bool CHECK, int I>
+__device__ __forceinline__ typename Codec<T>::CT pull(const PlanePtrs<T>& src, int o,
+                                                      const PullSites& ps) {
     using CT = typename Codec<T>::CT;
-    if (BC == kPeriodic || ps.inside<I>()) {
-        return Codec<T>::template dec<I>(__ldg(src + I * plane + o + ps.offset<I>()));
-    }
+    if (!CHECK || BC == kPeriodic || ps.inside<I>())
+        return Codec<T>::template dec<I>(__ldg(src.p[I] + (o + ps.offset<I>())));
     return CT(0);
 }
 
-template <typename T, int BC>
-__device__ __forceinline__ void pull_all(const T* __restrict__ src, long long plane, long long o,
-                                         const PullSites& ps, typename Codec<T>::CT (&g)[9]) {
-    g[0] = pull<T, BC, 0>(src, plane, o, ps);
-    g[1] = pull<T, BC, 1>(src, plane, o, ps);
-    g[2] = pull<T, BC, 2>(src, plane, o, ps);
-    g[3] = pull<T, BC, 3>(src, plane, o, ps);
-    g[4] = pull<T, BC, 4>(src, plane, o, ps);
-    g[5] = pull<T, BC, 5>(src, plane, o, ps);
-    g[6] = pull<T, BC, 6>(src, plane, o, ps);
-    g[7] = pull<T, BC, 7>(src, plane, o, ps);
-    g[8] = pull<T, BC, 8>(src, plane, o, ps);
+template <typename T, int BC, bool CHECK>
+__device__ __forceinline__ void pull_all(const PlanePtrs<T>& src, int o, const PullSites& ps,
+                                         typename Codec<T>::CT (&g)[9]) {
+    g[0] = pull<T, BC, CHECK, 0>(src, o, ps);
+    g[1] = pull<T, BC, CHECK, 1>(src, o, ps);
+    g[2] = pull<T, BC, CHECK, 2>(src, o, ps);
+    g[3] = pull<T, BC, CHECK, 3>(src, o, ps);
+    g[4] = pull<T, BC, CHECK, 4>(src, o, ps);
+    g[5] = pull<T, BC, CHECK, 5>(src, o, ps);
+    g[6] = pull<T, BC, CHECK, 6>(src, o, ps);
+    g[7] = pull<T, BC, CHECK, 7>(src, o, ps);
+    g[8] = pull<T, BC, CHECK, 8>(src, o, ps);
 }
 
 template <typename T>
-__device__ __forceinline__ void store_all(T* __restrict__ dst, long long plane, long long o,
+__device__ __forceinline__ void store_all(const PlanePtrs<T>& dst, int o,
                                           const typename Codec<T>::CT (&g)[9]) {
-    dst[0 * plane + o] = Codec<T>::template enc<0>(g[0]);
-    dst[1 * plane + o] = Codec<T>::template enc<1>(g[1]);
-    dst[2 * plane + o] = Codec<T>::template enc<2>(g[2]);
-    dst[3 * plane + o] = Codec<T>::template enc<3>(g[3]);
-    dst[4 * plane + o] = Codec<T>::template enc<4>(g[4]);
-    dst[5 * plane + o] = Codec<T>::template enc<5>(g[5]);
-    dst[6 * plane + o] = Codec<T>::template enc<6>(g[6]);
-    dst[7 * plane + o] = Codec<T>::template enc<7>(g[7]);
-    dst[8 * plane + o] = Codec<T>::template enc<8>(g[8]);
+    dst.p[0][o] = Codec<T>::template enc<0>(g[0]);
+    dst.p[1][o] = Codec<T>::template enc<1>(g[1]);
+    dst.p[2][o] = Codec<T>::template enc<2>(g[2]);
+    dst.p[3][o] = Codec<T>::template enc<3>(g[3]);
+    dst.p[4][o] = Codec<T>::template enc<4>(g[4]);
+    dst.p[5][o] = Codec<T>::template enc<5>(g[5]);
+    dst.p[6][o] = Codec<T>::template enc<6>(g[6]);
+    dst.p[7][o] = Codec<T>::template enc<7>(g[7]);
+    dst.p[8][o] = Codec<T>::template enc<8>(g[8]);
+}
+
+template <typename T>
+__host__ __device__ inline PlanePtrs<T> plane_ptrs(void* base, long long plane) {
+    PlanePtrs<T> r;
+    for (int i = 0; i < 9; ++i) r.p[i] = static_cast<T*>(base) + i * plane;
+    return r;
 }
 
 }  // namespace lbm

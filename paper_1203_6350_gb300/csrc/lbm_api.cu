@@ -2,6 +2,7 @@
 // parameter checks, host-side constants of the step, and launches.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -26,7 +27,7 @@ struct lbm_ctx {
     size_t buf_bytes = 0;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;  // buffer holding the post-collision state the next pull reads
-    void* chi_x = nullptr;  // device, compute precision
+    void* chi_x = nullptr;  // device AxisCoef tables (chi, 1/(1+n chi), 1/(1+m chi)), compute precision
     void* chi_y = nullptr;
     size_t chi_bytes_x = 0, chi_bytes_y = 0;
     double* diag = nullptr;  // kDiagBlocks * kDiag partials followed by kDiag results
@@ -39,10 +40,19 @@ struct lbm_ctx {
     StepConst<float> k32{};
     bool initialised = false;
     int64_t time = 0;
+    int launch_mode = 2;              // kLaunchGraph; LBM_LAUNCH=plain|pdl|graph overrides
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphChunk steps from buffer 0 / 1
+    cudaStream_t capture_stream = nullptr;
     std::string err;
 };
 
 namespace {
+
+// How lbm_step issues its kernels: one launch per step; one launch per step as
+// a programmatic dependent of the previous (its launch overlaps the previous
+// step's tail); or replays of a captured graph of kGraphChunk such launches.
+enum { kLaunchPlain = 0, kLaunchPdl = 1, kLaunchGraph = 2 };
+constexpr int kGraphChunk = 64;  // even, so a replay returns to the same buffer
 
 thread_local std::string g_create_error;
 
@@ -146,6 +156,56 @@ lbm::BaseState base_of(const lbm_ctx* h) { return lbm::BaseState{h->rho0, h->ux0
 
 bool is_finite(double v) { return std::isfinite(v); }
 
+cudaError_t launch_one_step(lbm_ctx* h, const void* src, void* dst, cudaStream_t st, bool pdl) {
+    const int p = pdl ? 1 : 0;
+    switch (h->storage) {
+        case LBM_F64:
+            return lbm::launch_step_f64(src, dst, h->geo, h->k64, static_cast<const lbm::AxisCoef<double>*>(h->chi_x),
+                                        static_cast<const lbm::AxisCoef<double>*>(h->chi_y), h->variant, h->bc, st, p);
+        case LBM_F32:
+            return lbm::launch_step_f32(src, dst, h->geo, h->k32, static_cast<const lbm::AxisCoef<float>*>(h->chi_x),
+                                        static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p);
+        case LBM_F16DEV:
+            return lbm::launch_step_f16(src, dst, h->geo, h->k32, static_cast<const lbm::AxisCoef<float>*>(h->chi_x),
+                                        static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p);
+        default:
+            return lbm::launch_step_bf16(src, dst, h->geo, h->k32, static_cast<const lbm::AxisCoef<float>*>(h->chi_x),
+                                         static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p);
+    }
+}
+
+void drop_graphs(lbm_ctx* h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        h->graph[i] = nullptr;
+    }
+}
+
+// Capture kGraphChunk consecutive steps starting from buffer `parity` on the
+// handle's private capture stream (programmatic dependent launches between
+// them) and instantiate the graph; it is replayed on the handle's stream.
+cudaError_t ensure_graph(lbm_ctx* h, int parity) {
+    if (h->graph[parity]) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!h->capture_stream) {
+        e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    int c = parity;
+    for (int t = 0; t < kGraphChunk && e == cudaSuccess; ++t) {
+        e = launch_one_step(h, h->buf[c], h->buf[1 - c], h->capture_stream, t > 0);
+        c = 1 - c;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -203,8 +263,12 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     h->geo = Geometry{nx, ny, per_row, per_row * ny};
     h->buf_bytes = 9 * (size_t)h->geo.plane * es;
     const size_t cts = storage == LBM_F64 ? 8 : 4;
-    h->chi_bytes_x = nx * cts;
-    h->chi_bytes_y = ny * cts;
+    if (h->geo.plane > 2147483647LL) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "lattice too large: one plane must hold fewer than 2^31 elements");
+    }
+    h->chi_bytes_x = (size_t)nx * 4 * cts;
+    h->chi_bytes_y = (size_t)ny * 4 * cts;
     h->diag_bytes = sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag);
     h->buf[0] = dev_alloc(h, h->buf_bytes);
     h->buf[1] = dev_alloc(h, h->buf_bytes);
@@ -226,6 +290,11 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
         return cuda_fail(nullptr, e, "initial clear");
     }
     refresh_consts(h);
+    if (const char* m = std::getenv("LBM_LAUNCH")) {
+        if (!std::strcmp(m, "plain")) h->launch_mode = kLaunchPlain;
+        else if (!std::strcmp(m, "pdl")) h->launch_mode = kLaunchPdl;
+        else if (!std::strcmp(m, "graph")) h->launch_mode = kLaunchGraph;
+    }
     *out = h;
     if (warn) g_create_error = "a relaxation rate lies outside (0, 2)";
     return warn;
@@ -249,18 +318,39 @@ int lbm_set_sponge(lbm_handle h, lbm_variant variant, const double* chi_x, const
     }
     DeviceGuard dg(h->device);
     cudaError_t e;
+    // Per-axis tables {chi, 1/(1 + n chi), 1/(1 + m chi), 0}, the factors in FP64.
+    const double nn = h->rates.n, mm = h->rates.m;
     if (h->storage == LBM_F64) {
-        e = cudaMemcpyAsync(h->chi_x, chi_x, h->chi_bytes_x, cudaMemcpyHostToDevice, h->stream);
+        std::vector<double> tx(4 * (size_t)h->nx), ty(4 * (size_t)h->ny);
+        for (int i = 0; i < h->nx; ++i) {
+            tx[4 * i] = chi_x[i]; tx[4 * i + 1] = 1.0 / (1.0 + nn * chi_x[i]);
+            tx[4 * i + 2] = 1.0 / (1.0 + mm * chi_x[i]); tx[4 * i + 3] = 0.0;
+        }
+        for (int i = 0; i < h->ny; ++i) {
+            ty[4 * i] = chi_y[i]; ty[4 * i + 1] = 1.0 / (1.0 + nn * chi_y[i]);
+            ty[4 * i + 2] = 1.0 / (1.0 + mm * chi_y[i]); ty[4 * i + 3] = 0.0;
+        }
+        e = cudaMemcpyAsync(h->chi_x, tx.data(), h->chi_bytes_x, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->chi_y, chi_y, h->chi_bytes_y, cudaMemcpyHostToDevice, h->stream);
+            e = cudaMemcpyAsync(h->chi_y, ty.data(), h->chi_bytes_y, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     } else {
-        std::vector<float> fx(chi_x, chi_x + h->nx), fy(chi_y, chi_y + h->ny);
-        e = cudaMemcpyAsync(h->chi_x, fx.data(), h->chi_bytes_x, cudaMemcpyHostToDevice, h->stream);
+        std::vector<float> tx(4 * (size_t)h->nx), ty(4 * (size_t)h->ny);
+        for (int i = 0; i < h->nx; ++i) {
+            tx[4 * i] = (float)chi_x[i]; tx[4 * i + 1] = (float)(1.0 / (1.0 + nn * chi_x[i]));
+            tx[4 * i + 2] = (float)(1.0 / (1.0 + mm * chi_x[i])); tx[4 * i + 3] = 0.0f;
+        }
+        for (int i = 0; i < h->ny; ++i) {
+            ty[4 * i] = (float)chi_y[i]; ty[4 * i + 1] = (float)(1.0 / (1.0 + nn * chi_y[i]));
+            ty[4 * i + 2] = (float)(1.0 / (1.0 + mm * chi_y[i])); ty[4 * i + 3] = 0.0f;
+        }
+        e = cudaMemcpyAsync(h->chi_x, tx.data(), h->chi_bytes_x, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->chi_y, fy.data(), h->chi_bytes_y, cudaMemcpyHostToDevice, h->stream);
+            e = cudaMemcpyAsync(h->chi_y, ty.data(), h->chi_bytes_y, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_sponge copy");
+    drop_graphs(h);  // the captured launches carry the old constants
     h->variant = variant;
     h->rho_f = rho_ref;
     h->ux_f = ux_ref;
@@ -308,28 +398,25 @@ int lbm_step(lbm_handle h, int nsteps) {
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
     if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init_equilibrium / lbm_set_state");
     DeviceGuard dg(h->device);
-    for (int t = 0; t < nsteps; ++t) {
-        const void* src = h->buf[h->cur];
-        void* dst = h->buf[1 - h->cur];
-        cudaError_t e;
-        switch (h->storage) {
-            case LBM_F64:
-                e = lbm::launch_step_f64(src, dst, h->geo, h->k64, static_cast<const double*>(h->chi_x),
-                                         static_cast<const double*>(h->chi_y), h->variant, h->bc, h->stream);
-                break;
-            case LBM_F32:
-                e = lbm::launch_step_f32(src, dst, h->geo, h->k32, static_cast<const float*>(h->chi_x),
-                                         static_cast<const float*>(h->chi_y), h->variant, h->bc, h->stream);
-                break;
-            case LBM_F16DEV:
-                e = lbm::launch_step_f16(src, dst, h->geo, h->k32, static_cast<const float*>(h->chi_x),
-                                         static_cast<const float*>(h->chi_y), h->variant, h->bc, h->stream);
-                break;
-            default:
-                e = lbm::launch_step_bf16(src, dst, h->geo, h->k32, static_cast<const float*>(h->chi_x),
-                                          static_cast<const float*>(h->chi_y), h->variant, h->bc, h->stream);
-                break;
+    cudaError_t e = cudaSuccess;
+    const bool pdl = h->launch_mode != kLaunchPlain;
+    if (h->launch_mode == kLaunchGraph && nsteps >= kGraphChunk) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(h->stream, &cs);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
+        if (cs == cudaStreamCaptureStatusNone) {
+            e = ensure_graph(h, h->cur);
+            if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step graph build");
+            while (nsteps >= kGraphChunk) {
+                e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step graph launch");
+                h->time += kGraphChunk;  // an even chunk leaves cur unchanged
+                nsteps -= kGraphChunk;
+            }
         }
+    }
+    for (int t = 0; t < nsteps; ++t) {
+        e = launch_one_step(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl);
         if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step launch");
         h->cur = 1 - h->cur;
         ++h->time;
@@ -421,6 +508,8 @@ void lbm_destroy(lbm_handle h) {
     if (!h) return;
     DeviceGuard dg(h->device);
     cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     dev_free(h, h->buf[0], h->buf_bytes);
     dev_free(h, h->buf[1], h->buf_bytes);
     dev_free(h, h->chi_x, h->chi_bytes_x);

@@ -6,21 +6,31 @@ namespace lbm {
 
 namespace {
 
-__device__ __forceinline__ double weight(int i) { return i == 0 ? 4.0 / 9.0 : i < 5 ? 1.0 / 9.0 : 1.0 / 36.0; }
+template <typename CT>
+__device__ __forceinline__ CT weight(int i) {
+    return i == 0 ? CT(4) / CT(9) : i < 5 ? CT(1) / CT(9) : CT(1) / CT(36);
+}
 
-// f^eq_i(rho, u) - f^eq_i(rho0, u0) in FP64 (the second-order D2Q9 equilibrium).
-__device__ __forceinline__ double feq_dev(int i, double rho, double ux, double uy, const BaseState& b) {
-    const double cu = cx(i) * ux + cy(i) * uy;
-    const double cu0 = cx(i) * b.ux0 + cy(i) * b.uy0;
-    const double p = rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy));
-    const double p0 = b.rho0 * (1.0 + 3.0 * cu0 + 4.5 * cu0 * cu0 - 1.5 * (b.ux0 * b.ux0 + b.uy0 * b.uy0));
-    return weight(i) * (p - p0);
+// f^eq_i(rho, u) - f^eq_i(rho0, u0) of the second-order D2Q9 equilibrium, from
+// rho' = rho - rho0 and du = u - u0 without cancellation:
+//   w_i [rho' (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
+//        + rho0 (3 c.du + 9/2 (c.du)(c.u + c.u0) - 3/2 du.(u + u0))].
+template <typename CT>
+__device__ __forceinline__ CT feq_dev(int i, CT dr, CT ux, CT uy, CT dux, CT duy, CT rho0, CT ux0,
+                                      CT uy0) {
+    const CT cu = cx(i) * ux + cy(i) * uy;
+    const CT cu0 = cx(i) * ux0 + cy(i) * uy0;
+    const CT cdu = cx(i) * dux + cy(i) * duy;
+    const CT a = CT(1) + CT(3) * cu + CT(4.5) * cu * cu - CT(1.5) * (ux * ux + uy * uy);
+    const CT b = CT(3) * cdu + CT(4.5) * cdu * (cu + cu0) - CT(1.5) * (dux * (ux + ux0) + duy * (uy + uy0));
+    return weight<CT>(i) * (dr * a + rho0 * b);
 }
 
 template <typename T, int I>
-__device__ __forceinline__ void init_plane(T* dst, const Geometry& g, const BaseState& b,
-                                           const double* rho, const double* ux, const double* uy,
-                                           int bc, int x, int y) {
+__device__ __forceinline__ void init_plane(const PlanePtrs<T>& dst, const Geometry& g,
+                                           const BaseState& b, const double* rho, const double* ux,
+                                           const double* uy, int bc, int x, int y) {
+    using CT = typename Codec<T>::CT;
     // The pull at cell (x, y) + c_I reads this slot, so it holds f^eq there.
     int sx = x + cx(I), sy = y + cy(I);
     bool ok = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
@@ -29,18 +39,19 @@ __device__ __forceinline__ void init_plane(T* dst, const Geometry& g, const Base
         sy = (sy + g.ny) % g.ny;
         ok = true;
     }
-    double v = 0.0;
+    CT v = CT(0);
     if (ok) {
         const long long c = (long long)sy * g.nx + sx;
-        v = feq_dev(I, rho[c], ux[c], uy[c], b);
+        const double u = ux[c], w = uy[c];
+        v = feq_dev<CT>(I, CT(rho[c] - b.rho0), CT(u), CT(w), CT(u - b.ux0), CT(w - b.uy0),
+                        CT(b.rho0), CT(b.ux0), CT(b.uy0));
     }
-    using CT = typename Codec<T>::CT;
-    dst[I * g.plane + (long long)y * g.pitch + x] = Codec<T>::template enc<I>(static_cast<CT>(v));
+    dst.p[I][(long long)y * g.pitch + x] = Codec<T>::template enc<I>(v);
 }
 
 template <typename T>
-__global__ void init_kernel(T* dst, Geometry g, BaseState b, const double* rho, const double* ux,
-                            const double* uy, int bc) {
+__global__ void init_kernel(PlanePtrs<T> dst, Geometry g, BaseState b, const double* rho,
+                            const double* ux, const double* uy, int bc) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= g.nx || y >= g.ny) return;
@@ -55,40 +66,38 @@ __global__ void init_kernel(T* dst, Geometry g, BaseState b, const double* rho, 
     init_plane<T, 8>(dst, g, b, rho, ux, uy, bc, x, y);
 }
 
-// rho', j' of the pulled populations at (x, y), accumulated in FP64.
+// rho', j' of the pulled populations at (x, y), summed in the compute precision.
 template <typename T, int BC>
-__device__ __forceinline__ void cell_moments(const T* src, const Geometry& g, int x, int y,
-                                             double& r, double& jx, double& jy) {
+__device__ __forceinline__ void cell_moments(const PlanePtrs<T>& src, const Geometry& g, int x,
+                                             int y, typename Codec<T>::CT& r,
+                                             typename Codec<T>::CT& jx,
+                                             typename Codec<T>::CT& jy) {
     using CT = typename Codec<T>::CT;
     PullSites ps;
-    ps.init<BC>(x, y, g);
+    ps.edge<BC>(x, y, g.nx, g.ny, static_cast<int>(g.pitch));
     CT v[9];
-    pull_all<T, BC>(src, g.plane, (long long)y * g.pitch + x, ps, v);
-    r = 0.0;
-    jx = 0.0;
-    jy = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const double d = static_cast<double>(v[i]);
-        r += d;
-        jx += cx(i) * d;
-        jy += cy(i) * d;
-    }
+    pull_all<T, BC, true>(src, y * static_cast<int>(g.pitch) + x, ps, v);
+    CT m[9];
+    moments9(v, m);
+    r = m[0];
+    jx = m[1];
+    jy = m[2];
 }
 
 template <typename T, int BC>
-__global__ void moments_kernel(const T* src, Geometry g, BaseState b, double* rho_dev, double* ux,
-                               double* uy) {
+__global__ void moments_kernel(PlanePtrs<T> src, Geometry g, BaseState b, double* rho_dev,
+                               double* ux, double* uy) {
+    using CT = typename Codec<T>::CT;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= g.nx || y >= g.ny) return;
-    double r, jx, jy;
+    CT r, jx, jy;
     cell_moments<T, BC>(src, g, x, y, r, jx, jy);
     const long long c = (long long)y * g.nx + x;
-    const double rho = b.rho0 + r;
-    if (rho_dev) rho_dev[c] = r;
-    if (ux) ux[c] = (b.rho0 * b.ux0 + jx) / rho;
-    if (uy) uy[c] = (b.rho0 * b.uy0 + jy) / rho;
+    const double rho = b.rho0 + double(r);
+    if (rho_dev) rho_dev[c] = double(r);
+    if (ux) ux[c] = (b.rho0 * b.ux0 + double(jx)) / rho;
+    if (uy) uy[c] = (b.rho0 * b.uy0 + double(jy)) / rho;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -99,34 +108,36 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int kDiagThreads = 256;
 
-// First pass: each block strides over the region's cells in a fixed order and
-// writes its kDiag partial sums.
+// First pass: block (bx, by) of a gx x gy grid takes the rows y0 + by, + gy, ...
+// and the columns x0 + bx * 256 + t, + gx * 256, ... of the region, and writes
+// its kDiag sums (FP64) to partial[by * gx + bx].
 template <typename T, int BC>
 __global__ void __launch_bounds__(kDiagThreads)
-    diag_partial_kernel(const T* src, Geometry g, BaseState b, int x0, int y0, int x1, int y1,
+    diag_partial_kernel(PlanePtrs<T> src, Geometry g, BaseState b, int x0, int y0, int x1, int y1,
                         double* partial) {
-    const long long w = x1 - x0;
-    const long long ncell = w * (long long)(y1 - y0);
+    using CT = typename Codec<T>::CT;
     double acc[kDiag] = {0, 0, 0, 0, 0, 0};
-    const double cs2 = 1.0 / 3.0;
-    for (long long c = (long long)blockIdx.x * kDiagThreads + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * kDiagThreads) {
-        const int x = x0 + (int)(c % w);
-        const int y = y0 + (int)(c / w);
-        double r, jx, jy;
-        cell_moments<T, BC>(src, g, x, y, r, jx, jy);
-        const double rho = b.rho0 + r;
-        // u - u0 = (j' - rho' u0) / rho, with j' = j - rho0 u0
-        const double dux = (jx - r * b.ux0) / rho;
-        const double duy = (jy - r * b.uy0) / rho;
-        const double e = cs2 * r * r / (2.0 * b.rho0) + 0.5 * b.rho0 * (dux * dux + duy * duy);
-        const bool finite = isfinite(r) && isfinite(dux) && isfinite(duy);
-        acc[0] += r;
-        acc[1] += jx;
-        acc[2] += jy;
-        acc[3] += e;
-        acc[4] += r * r;
-        acc[5] += finite ? 0.0 : 1.0;
+    const CT rho0 = CT(b.rho0), ux0 = CT(b.ux0), uy0 = CT(b.uy0);
+    for (int y = y0 + blockIdx.y; y < y1; y += gridDim.y) {
+        for (int x = x0 + blockIdx.x * kDiagThreads + threadIdx.x; x < x1;
+             x += gridDim.x * kDiagThreads) {
+            CT r, jx, jy;
+            cell_moments<T, BC>(src, g, x, y, r, jx, jy);
+            // u - u0 = (j' - rho' u0) / rho, with j' = j - rho0 u0
+            const CT inv = CT(1) / (rho0 + r);
+            const CT dux = (jx - r * ux0) * inv;
+            const CT duy = (jy - r * uy0) * inv;
+            const double dr = double(r);
+            const double e = dr * dr / (6.0 * b.rho0) +
+                             0.5 * b.rho0 * (double(dux) * double(dux) + double(duy) * double(duy));
+            const bool finite = isfinite(r) && isfinite(dux) && isfinite(duy);
+            acc[0] += dr;
+            acc[1] += double(jx);
+            acc[2] += double(jy);
+            acc[3] += e;
+            acc[4] += dr * dr;
+            acc[5] += finite ? 0.0 : 1.0;
+        }
     }
     __shared__ double red[kDiag][kDiagThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(kDiagThreads)
     if (threadIdx.x < kDiag) {
         double s = 0.0;
         for (int k = 0; k < kDiagThreads / 32; ++k) s += red[threadIdx.x][k];
-        partial[(long long)blockIdx.x * kDiag + threadIdx.x] = s;
+        partial[(blockIdx.y * gridDim.x + blockIdx.x) * kDiag + threadIdx.x] = s;
     }
 }
 
@@ -150,7 +161,7 @@ __global__ void __launch_bounds__(kDiagThreads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = 0; q < kDiag; ++q) {
         double s = 0.0;
-        for (int k = threadIdx.x; k < blocks; k += kDiagThreads) s += partial[(long long)k * kDiag + q];
+        for (int k = threadIdx.x; k < blocks; k += kDiagThreads) s += partial[k * kDiag + q];
         s = warp_sum(s);
         if (lane == 0) red[q][warp] = s;
     }
@@ -166,7 +177,7 @@ template <typename T>
 cudaError_t init_t(void* dst, const Geometry& g, const BaseState& b, const double* rho,
                    const double* ux, const double* uy, int bc, cudaStream_t st) {
     const dim3 block(128, 2), grid((g.nx + 127) / 128, (g.ny + 1) / 2);
-    init_kernel<T><<<grid, block, 0, st>>>(static_cast<T*>(dst), g, b, rho, ux, uy, bc);
+    init_kernel<T><<<grid, block, 0, st>>>(plane_ptrs<T>(dst, g.plane), g, b, rho, ux, uy, bc);
     return cudaGetLastError();
 }
 
@@ -174,7 +185,7 @@ template <typename T>
 cudaError_t moments_t(const void* src, const Geometry& g, const BaseState& b, int bc, double* r,
                       double* ux, double* uy, cudaStream_t st) {
     const dim3 block(128, 2), grid((g.nx + 127) / 128, (g.ny + 1) / 2);
-    const T* s = static_cast<const T*>(src);
+    const PlanePtrs<T> s = plane_ptrs<T>(const_cast<void*>(src), g.plane);
     if (bc == kPeriodic)
         moments_kernel<T, kPeriodic><<<grid, block, 0, st>>>(s, g, b, r, ux, uy);
     else
@@ -185,14 +196,20 @@ cudaError_t moments_t(const void* src, const Geometry& g, const BaseState& b, in
 template <typename T>
 cudaError_t diag_t(const void* src, const Geometry& g, const BaseState& b, int bc, int x0, int y0,
                    int x1, int y1, double* partial, double* out, cudaStream_t st) {
-    const T* s = static_cast<const T*>(src);
+    const PlanePtrs<T> s = plane_ptrs<T>(const_cast<void*>(src), g.plane);
+    const int w = x1 - x0, h = y1 - y0;
+    const int gx = w <= 0 ? 1 : (w + kDiagThreads - 1) / kDiagThreads < 4 ? (w + kDiagThreads - 1) / kDiagThreads : 4;
+    int gy = kDiagBlocks / gx;
+    if (h > 0 && h < gy) gy = h;
+    if (gy < 1) gy = 1;
+    const dim3 grid(gx, gy);
     if (bc == kPeriodic)
-        diag_partial_kernel<T, kPeriodic><<<kDiagBlocks, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial);
+        diag_partial_kernel<T, kPeriodic><<<grid, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial);
     else
-        diag_partial_kernel<T, kDirichlet><<<kDiagBlocks, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial);
+        diag_partial_kernel<T, kDirichlet><<<grid, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    diag_final_kernel<<<1, kDiagThreads, 0, st>>>(partial, kDiagBlocks, out);
+    diag_final_kernel<<<1, kDiagThreads, 0, st>>>(partial, gx * gy, out);
     return cudaGetLastError();
 }
 

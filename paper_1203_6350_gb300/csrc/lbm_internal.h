@@ -32,24 +32,38 @@ struct StepConst {
     CT dmeq_ref[9];   // m^eq(rho_f, j_f) - m^eq(rho0, j0), evaluated in FP64 on the host
 };
 
+// Per-axis absorbing-layer coefficients: the strength chi and the Guo factors
+// 1/(1 + n chi), 1/(1 + m chi) (computed in FP64 on the host).  At a cell,
+// chi = max over the two axes and, since the factors fall with chi, the
+// factors are the min over the two axes.
+template <typename CT>
+struct alignas(4 * sizeof(CT)) AxisCoef {
+    CT chi, rn, rm, pad;
+};
+
 enum Storage { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum Variant { kNone = 0, kTypeI = 1, kTypeII = 2, kTypeIII = 3 };
 enum Bc { kDirichlet = 0, kPeriodic = 1 };
 
 // Step launchers, one translation unit per storage type.  src holds the
 // post-collision state of time t (pulled), dst receives that of time t + 1.
+// pdl != 0: launch as a programmatic dependent of the previous kernel.
 cudaError_t launch_step_f64(const void* src, void* dst, const Geometry& g,
-                            const StepConst<double>& k, const double* chi_x,
-                            const double* chi_y, int variant, int bc, cudaStream_t st);
+                            const StepConst<double>& k, const AxisCoef<double>* tx,
+                            const AxisCoef<double>* ty, int variant, int bc, cudaStream_t st,
+                            int pdl);
 cudaError_t launch_step_f32(const void* src, void* dst, const Geometry& g,
-                            const StepConst<float>& k, const float* chi_x, const float* chi_y,
-                            int variant, int bc, cudaStream_t st);
+                            const StepConst<float>& k, const AxisCoef<float>* tx,
+                            const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
+                            int pdl);
 cudaError_t launch_step_f16(const void* src, void* dst, const Geometry& g,
-                            const StepConst<float>& k, const float* chi_x, const float* chi_y,
-                            int variant, int bc, cudaStream_t st);
+                            const StepConst<float>& k, const AxisCoef<float>* tx,
+                            const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
+                            int pdl);
 cudaError_t launch_step_bf16(const void* src, void* dst, const Geometry& g,
-                             const StepConst<float>& k, const float* chi_x, const float* chi_y,
-                             int variant, int bc, cudaStream_t st);
+                             const StepConst<float>& k, const AxisCoef<float>* tx,
+                             const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
+                            int pdl);
 
 // Base-state parameters of the auxiliary kernels (always FP64).
 struct BaseState {

@@ -4,9 +4,9 @@
 namespace lbm {
 
 cudaError_t launch_step_f64(const void* src, void* dst, const Geometry& g,
-                        const StepConst<double>& k, const double* chi_x, const double* chi_y,
-                        int variant, int bc, cudaStream_t st) {
-    return launch_step_t<double>(src, dst, g, k, chi_x, chi_y, variant, bc, st);
+                        const StepConst<double>& k, const AxisCoef<double>* tx,
+                        const AxisCoef<double>* ty, int variant, int bc, cudaStream_t st, int pdl) {
+    return launch_step_t<double>(src, dst, g, k, tx, ty, variant, bc, st, pdl);
 }
 
 }  // namespace lbm
