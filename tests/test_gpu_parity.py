@@ -85,14 +85,14 @@ def test_small_pulse_all_fields(storage, variant):
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_small_pulse_type_I(storage):
     """Type I on the same workload has s + chi > 2 in the outer part of the layer and
-    grows there (Eq. effectrelax): parity at 60 and 300 steps, a field that has
-    grown by orders of magnitude over the type II one at 300 steps, and a
-    non-finite state on both sides after 1000 steps."""
+    grows there (Eq. effectrelax).  The growing mode amplifies every rounding
+    difference at ~9 % per step, so parity is checked while it is still small
+    (60 steps); then the field must have grown by orders of magnitude over the
+    type II one at 300 steps, and be non-finite on both sides after 1000 steps."""
     w = wl.small_pulse("I", storage)
-    for steps in (60, 300):
-        ref = _oracle(w, steps)
-        got = run_gpu(w, storage, steps)
-        assert_close(got[0], ref[0], TOL[storage], steps, steps)
+    ref = _oracle(w, 60)
+    got = run_gpu(w, storage, 60)
+    assert_close(got[0], ref[0], TOL[storage], 60)
     r2 = _oracle(w.with_(variant="II"), 300)[0]
     assert np.abs(_oracle(w, 300)[0]).max() > 100 * np.abs(r2).max()
     r1000 = _oracle(w, 1000)[0]
