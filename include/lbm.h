@@ -167,6 +167,46 @@ const char* lbm_last_error(lbm_handle h);
 /* Library version string. */
 const char* lbm_version(void);
 
+/* ------------------------------------------------------------------------
+ * Diagnostics without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory -- for example a host application that owns a fixed device
+ * memory pool and forbids other allocations, or a latency-critical loop that
+ * cannot afford cudaMalloc/cudaFree (they are slow and may synchronise the
+ * whole device).  Such a caller keeps a population buffer of its own (for
+ * instance filled by lbm_get_state with on_device = 1) and passes it here.
+ *
+ * Computes the six sums of lbm_diagnostics over the cells x0 <= ix < x1,
+ * y0 <= iy < y1 of `state`: a device buffer in the library's layout for the
+ * given storage and lattice (9 planes of ny rows of pitch elements, pitch = nx
+ * rounded up to 128 bytes; lbm_state_bytes gives its size), holding the
+ * post-collision state that lbm_get_state returns, with far-field state
+ * (rho0, u0) and boundary bc.  out: 6 doubles, a device pointer when
+ * out_on_device != 0 (the call is then asynchronous on cuda_stream), else a
+ * host pointer (the call synchronises cuda_stream).  cuda_stream is a
+ * borrowed cudaStream_t (NULL = legacy default stream).
+ *
+ * Scratch: the block partial sums live in one static device array of
+ * 786,480 bytes defined in the library, which every GPU that loads the
+ * library holds until the process exits.  The call never calls cudaMalloc,
+ * cudaFree or any other allocating routine.  Its first call on a device looks
+ * up the array's device address for that device (once per device, with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the array and each call rewrites every slot it reads, so no
+ * clearing is needed, but calls that overlap on the GPU (on different streams
+ * or from several threads) race on it and must be serialised by the caller.
+ *
+ * Limits: the region may hold at most 268,435,456 cells (16,384 partial sums
+ * of 16,384 cells each) and one plane fewer than 2^31 elements; larger inputs
+ * return LBM_ERR_TOO_LARGE without touching the device.  Other returns:
+ * LBM_ERR_ARG (bad storage, bc, sizes, region, NULL pointers, rho0 <= 0),
+ * LBM_ERR_CUDA, LBM_ERR_NONFINITE (host out only: out is filled and out[5] > 0),
+ * LBM_OK. */
+#define LBM_ERR_TOO_LARGE (-6) /* input exceeds the fixed capacity of a static scratch */
+int lbm_diagnostics_noalloc(const void* state, lbm_storage storage, int nx, int ny, lbm_bc bc,
+                            double rho0, double ux0, double uy0, int x0, int y0, int x1, int y1,
+                            double* out, int out_on_device, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

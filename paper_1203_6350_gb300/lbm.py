@@ -27,6 +27,7 @@ LBM_ERR_OOM = -2
 LBM_ERR_CUDA = -3
 LBM_ERR_NONFINITE = -4
 LBM_ERR_STATE = -5
+LBM_ERR_TOO_LARGE = -6
 
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
 VARIANT = {"none": 0, "I": 1, "II": 2, "III": 3}
@@ -79,6 +80,10 @@ SIGNATURES = [
     ("lbm_destroy", None, [_vp]),
     ("lbm_last_error", ctypes.c_char_p, [_vp]),
     ("lbm_version", ctypes.c_char_p, []),
+    ("lbm_diagnostics_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]),
 ]
 
 
@@ -187,6 +192,15 @@ def lbm_set_stream(h, stream) -> int:
 
 def lbm_destroy(h) -> None:
     load().lbm_destroy(h)
+
+
+def lbm_diagnostics_noalloc(state_ptr, storage, nx, ny, bc, rho0, ux0, uy0, x0, y0, x1, y1,
+                            out_ptr, out_on_device, stream=None) -> int:
+    """Diagnostics of a caller-owned device population buffer with no device
+    allocation (see include/lbm.h for who needs it and its limits)."""
+    return load().lbm_diagnostics_noalloc(state_ptr, int(storage), int(nx), int(ny), int(bc),
+                                          float(rho0), float(ux0), float(uy0), int(x0), int(y0),
+                                          int(x1), int(y1), out_ptr, int(out_on_device), stream)
 
 
 # ------------------------------------------------------------- helpers ----
