@@ -50,6 +50,8 @@ def parse():
                     help="time steps per solve (the workload's 5000 by default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256-lattice batched-versus-plain-loop measurement")
     return ap.parse_args()
 
 
@@ -319,6 +321,9 @@ def run_native(args):
     launches_total = args.steps * sum(w.steps + 1 + 4 for w in works)
     for lat in lats:
         lat.close()
+    batched = None
+    if not args.no_batched:
+        batched = run_batched()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -329,6 +334,7 @@ def run_native(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches_total,
             "reflected_energy": {k: refl.get(k) for k in VARIANTS},
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -382,6 +388,63 @@ def run_e2e(works, lats, stream, dev, steps):
     cells = sum(w.cells * w.steps for w in works) * steps
     return {"value": cells / t / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h}
+
+
+def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
+    """Batched workload: `count` independent lattices (sides log-uniform in
+    [64, 1024], seeded pulses, Mach in [0, 0.2], chi_max log-uniform in [1e-3, 1],
+    layer 8-64 cells, variants cycled), FP32, `steps` steps, one persistent launch
+    per step (autotuned tile shape, graph-replayed) against one launch per lattice
+    per step through the single-lattice API."""
+    import torch
+
+    from paper_1203_6350_gb300 import autotune, lbm
+    from paper_1203_6350_gb300.batch import Batch
+
+    works = wl.batch_of_lattices(seed=SEED, count=count, steps=steps + warmup, storage="f32")
+    shapes = [(w.nx, w.ny) for w in works]
+    tile = autotune.tuned_tiling(shapes, "f32")
+    cells = sum(w.cells for w in works)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = Batch("f32", stream=stream, tiling=tile)
+        for w in works:
+            with_warn(lambda: b.add_workload(w))
+        b.step(warmup)
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.step(steps)
+        z.record(stream)
+        z.synchronize()
+        t_batch = a.elapsed_time(z) / 1e3
+        b.close()
+        lats = []
+        for w in works:
+            lats.append(with_warn(lambda: lbm.Lattice.from_workload(w, stream=stream)))
+        hs = [lat.h for lat in lats]
+        step = lbm.load().lbm_step
+        for _ in range(4):
+            for h in hs:
+                step(h, 1)
+        a.record(stream)
+        for _ in range(steps):
+            for h in hs:
+                step(h, 1)
+        z.record(stream)
+        z.synchronize()
+        t_plain = a.elapsed_time(z) / 1e3
+        for lat in lats:
+            lat.close()
+    return {
+        "workload": f"{count} lattices, sides log-uniform in [64, 1024] (seed {SEED}), FP32, "
+                    f"variants cycled I/II/III, {steps} steps",
+        "lattices": count, "cells": cells, "steps": steps, "tile": list(tile),
+        "mlups": cells * steps / t_batch / 1e6,
+        "plain_loop_mlups": cells * steps / t_plain / 1e6,
+        "speedup_vs_plain_loop": t_plain / t_batch,
+        "launches_per_step": {"batched": 1, "plain_loop": count},
+    }
 
 
 def measured_peaks():

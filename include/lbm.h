@@ -168,6 +168,76 @@ const char* lbm_last_error(lbm_handle h);
 const char* lbm_version(void);
 
 /* ------------------------------------------------------------------------
+ * Batched stepping of many independent lattices (one persistent launch per
+ * time step over a tile table, replayed from captured CUDA graphs).
+ *
+ * Each instance is one problem in the sense of lbm_create + lbm_set_sponge
+ * (size, far field, rates, boundary, damping variant, absorbing profile,
+ * reference state) plus a step budget.  All instances of a batch share one
+ * storage type and one stream.  An instance becomes active at the global step
+ * at which it is initialised and stops after exactly its budget of steps, so
+ * instances admitted at different times or with different budgets run in the
+ * same launches and each takes exactly its own number of steps.  The per-cell
+ * arithmetic is that of lbm_step, so a lattice gives the same result alone and
+ * in a batch.  Calls on one batch must not overlap from several host threads.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch_ctx* lbm_batch;
+
+/* Device bytes lbm_batch_add allocates for an nx x ny instance (both
+ * population buffers and the per-axis absorbing tables), for admission
+ * control; 0 for invalid arguments. */
+size_t lbm_batch_instance_bytes(int nx, int ny, lbm_storage storage);
+
+/* Create an empty batch on cuda_stream (borrowed) with the given allocator
+ * (NULL = cudaMalloc).  Returns LBM_ERR_ARG, LBM_ERR_OOM or LBM_ERR_CUDA on
+ * failure. */
+int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator* alloc,
+                     lbm_batch* out);
+
+/* Tile shape of the batched launch: tile_x in {32, 64, 128, 256} cells along x,
+ * tile_y a multiple of 256 / tile_x up to 256 (a block of 256 threads covers
+ * the tile in rows).  Default 128 x 8. */
+int lbm_batch_set_tiling(lbm_batch b, int tile_x, int tile_y);
+
+/* Add an instance (arguments as lbm_create and lbm_set_sponge; chi arrays are
+ * host arrays, copied) with a budget of nsteps >= 0 steps.  Allocates its
+ * buffers; *id receives its handle.  It takes no steps until
+ * lbm_batch_init_equilibrium. */
+int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double uy0,
+                  const lbm_rates* rates, lbm_bc bc, lbm_variant variant, const double* chi_x,
+                  const double* chi_y, double rho_ref, double ux_ref, double uy_ref, int64_t nsteps,
+                  int* id);
+
+/* Time 0 of instance id from FP64 fields (as lbm_init_equilibrium); it becomes
+ * active from the batch's next step. */
+int lbm_batch_init_equilibrium(lbm_batch b, int id, const double* rho, const double* ux,
+                               const double* uy, int on_device);
+
+/* Advance the batch by nsteps global steps: every active instance takes a step
+ * in each of them until its budget is spent.  Asynchronous on the stream. */
+int lbm_batch_step(lbm_batch b, int nsteps);
+
+/* Steps instance id has taken (<= its budget), or -1 for an unknown id. */
+int64_t lbm_batch_time(lbm_batch b, int id);
+
+/* Fields and diagnostics of instance id at its current time, as lbm_moments
+ * and lbm_diagnostics. */
+int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* uy, int on_device);
+int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, double out[6]);
+
+/* Remove instance id and free its buffers (synchronises the stream). */
+int lbm_batch_remove(lbm_batch b, int id);
+
+/* Number of instances in the batch (-1 for NULL). */
+int lbm_batch_count(lbm_batch b);
+
+/* Message of the last error on b. */
+const char* lbm_batch_last_error(lbm_batch b);
+
+/* Free every instance and the batch.  NULL is allowed. */
+void lbm_batch_destroy(lbm_batch b);
+
+/* ------------------------------------------------------------------------
  * Diagnostics without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot let a library allocate
  * device memory -- for example a host application that owns a fixed device

@@ -1,0 +1,742 @@
+// Batched time step: many independent lattices advanced by one persistent
+// launch per step over a tile table, and the C ABI that manages the batch
+// (lbm_batch_* in include/lbm.h).
+//
+// Each instance is a lattice of its own (size, rates, damping variant,
+// boundary, reference state, absorbing profile) with its own double buffer.
+// It is active for the global steps start <= s < end, so instances admitted
+// at different times and with different step budgets share every launch and
+// each takes exactly its own number of steps.  The per-cell arithmetic is the
+// single-lattice kernel's (collide_cell, pull_all, store_all), so a lattice
+// gives the same result alone and in a batch.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+// Device descriptor of one instance.
+template <typename CT>
+struct BatchInst {
+    void* buf[2];
+    const AxisCoef<CT>* tx;
+    const AxisCoef<CT>* ty;
+    long long start, end;  // active for start <= step < end
+    long long plane;
+    int nx, ny, pitch, variant, bc, pad;
+    StepConst<CT> k;
+};
+
+struct BatchTile {
+    int inst, x0, y0, pad;
+};
+
+// One time step of every active instance.  Block b walks the tiles b, b + G,
+// ...; the tile's instance descriptor is copied to shared memory, then the
+// block covers the tile_x x tile_y cells with blockDim = (tile_x, 256/tile_x).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    batch_step_kernel(const BatchInst<typename Codec<T>::CT>* __restrict__ insts,
+                      const BatchTile* __restrict__ tiles, const int* __restrict__ ntiles_p,
+                      const long long* __restrict__ step_p, int k_in_chunk, int tile_y) {
+    using CT = typename Codec<T>::CT;
+    using Inst = BatchInst<CT>;
+    __shared__ __align__(16) unsigned char raw[sizeof(Inst)];
+    Inst& sd = *reinterpret_cast<Inst*>(raw);
+    constexpr int kWords = (int)(sizeof(Inst) / 4);
+    static_assert(sizeof(Inst) % 4 == 0, "descriptor must be word-sized");
+    // the previous step's grid must have finished before any buffer is touched
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const long long step = *step_p + k_in_chunk;
+    const int ntiles = *ntiles_p;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tile = tiles[t];
+        __syncthreads();  // everyone is done with the previous descriptor
+        const unsigned* srcw = reinterpret_cast<const unsigned*>(insts + tile.inst);
+        unsigned* dstw = reinterpret_cast<unsigned*>(raw);
+        for (int w = tid; w < kWords; w += nthr) dstw[w] = __ldg(srcw + w);
+        __syncthreads();
+        if (step < sd.start || step >= sd.end) continue;  // block-uniform
+        const int parity = (int)((step - sd.start) & 1);
+        const PlanePtrs<T> src = plane_ptrs<T>(sd.buf[parity], sd.plane);
+        const PlanePtrs<T> dst = plane_ptrs<T>(sd.buf[1 - parity], sd.plane);
+        const int nx = sd.nx, ny = sd.ny, pitch = sd.pitch;
+        const int x = tile.x0 + threadIdx.x;
+        const bool interior = tile.x0 > 0 && tile.y0 > 0 && tile.x0 + (int)blockDim.x < nx &&
+                              tile.y0 + tile_y < ny;
+        for (int ry = threadIdx.y; ry < tile_y; ry += blockDim.y) {
+            const int y = tile.y0 + ry;
+            if (x >= nx || y >= ny) continue;
+            const int o = y * pitch + x;
+            CT v[9];
+            PullSites ps;
+            if (interior) {
+                ps.interior(pitch);
+                pull_all<T, kDirichlet, false>(src, o, ps, v);
+            } else if (sd.bc == kPeriodic) {
+                ps.edge<kPeriodic>(x, y, nx, ny, pitch);
+                pull_all<T, kPeriodic, true>(src, o, ps, v);
+            } else {
+                ps.edge<kDirichlet>(x, y, nx, ny, pitch);
+                pull_all<T, kDirichlet, true>(src, o, ps, v);
+            }
+            switch (sd.variant) {
+                case kTypeI: collide_cell<CT, kTypeI>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                case kTypeII: collide_cell<CT, kTypeII>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                case kTypeIII: collide_cell<CT, kTypeIII>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                default: collide_cell<CT, kNone>(v, x, y, sd.k, sd.tx, sd.ty); break;
+            }
+            store_all<T>(dst, o, v);
+        }
+    }
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+__global__ void advance_step_kernel(long long* step_p, int by) { *step_p += by; }
+
+template <typename T>
+const void* batch_kernel_ptr() {
+    return reinterpret_cast<const void*>(&batch_step_kernel<T>);
+}
+
+template <typename T>
+cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int* ntiles,
+                           const long long* step, int k, int tile_x, int tile_y, int grid,
+                           cudaStream_t st, int pdl) {
+    using CT = typename Codec<T>::CT;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tile_x, 256 / tile_x);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel<T>,
+                              static_cast<const BatchInst<CT>*>(insts), tiles, ntiles, step, k,
+                              tile_y);
+}
+
+}  // namespace lbm
+
+using lbm::AxisCoef;
+using lbm::BatchInst;
+using lbm::BatchTile;
+using lbm::Geometry;
+using lbm::StepConst;
+
+namespace {
+
+constexpr int kBatchChunk = 32;  // steps per captured graph
+
+struct Instance {
+    int nx = 0, ny = 0;
+    double rho0 = 1, ux0 = 0, uy0 = 0;
+    double rho_f = 1, ux_f = 0, uy_f = 0;
+    lbm_rates rates{};
+    int variant = 0, bc = 0;
+    int64_t budget = 0;
+    int64_t start = INT64_MAX;  // global step at which it started (after init)
+    Geometry geo{};
+    size_t buf_bytes = 0, tab_bytes = 0;
+    void* buf[2] = {nullptr, nullptr};
+    void* tabs = nullptr;  // AxisCoef x table followed by y table
+    bool initialised = false;
+};
+
+}  // namespace
+
+struct lbm_batch_ctx {
+    int storage = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lbm_allocator alloc{};
+    bool custom_alloc = false;
+    std::map<int, Instance> insts;
+    int next_id = 0;
+    int64_t step = 0;  // global step (host mirror of *d_step)
+    int tile_x = 128, tile_y = 8;
+    int grid = 0;
+    // device tables
+    void* d_insts = nullptr;
+    size_t insts_cap = 0;  // bytes
+    BatchTile* d_tiles = nullptr;
+    size_t tiles_cap = 0;  // entries
+    int* d_ntiles = nullptr;
+    long long* d_step = nullptr;
+    double* d_diag = nullptr;
+    double* staging = nullptr;
+    size_t staging_bytes = 0;
+    std::vector<int> dense;  // dense index -> instance id
+    bool dirty = true;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int bfail(lbm_batch_ctx* b, int code, const std::string& msg) {
+    if (b) b->err = msg;
+    return code;
+}
+
+void* bd_alloc(lbm_batch_ctx* b, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (b->custom_alloc) return b->alloc.alloc(bytes, b->alloc.ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void bd_free(lbm_batch_ctx* b, void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (b->custom_alloc)
+        b->alloc.free(p, bytes, b->alloc.ctx);
+    else
+        cudaFree(p);
+}
+
+struct BDeviceGuard {
+    int prev = -1;
+    explicit BDeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~BDeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t storage_size(int storage) { return lbm::storage_bytes(storage); }
+
+Geometry geometry_of(int nx, int ny, int storage) {
+    const size_t es = storage_size(storage);
+    const long long per_row = (long long)((nx * es + 127) / 128 * 128 / es);
+    return Geometry{nx, ny, per_row, per_row * ny};
+}
+
+void moment_eq(double rho, double jx, double jy, double out[9]) {
+    const double q = (jx * jx + jy * jy) / rho;
+    out[0] = rho;
+    out[1] = jx;
+    out[2] = jy;
+    out[3] = -2.0 * rho + 3.0 * q;
+    out[4] = rho - 3.0 * q;
+    out[5] = -jx;
+    out[6] = -jy;
+    out[7] = (jx * jx - jy * jy) / rho;
+    out[8] = jx * jy / rho;
+}
+
+template <typename CT>
+StepConst<CT> consts_of(const Instance& in) {
+    StepConst<CT> k{};
+    for (int i = 0; i < 9; ++i) k.s[i] = static_cast<CT>(in.rates.s[i]);
+    k.n = static_cast<CT>(in.rates.n);
+    k.m = static_cast<CT>(in.rates.m);
+    const double jx0 = in.rho0 * in.ux0, jy0 = in.rho0 * in.uy0;
+    k.rho0 = static_cast<CT>(in.rho0);
+    k.jx0 = static_cast<CT>(jx0);
+    k.jy0 = static_cast<CT>(jy0);
+    k.jj0 = static_cast<CT>(jx0 * jx0 + jy0 * jy0);
+    k.jxy0 = static_cast<CT>(jx0 * jx0 - jy0 * jy0);
+    k.pxy0 = static_cast<CT>(jx0 * jy0);
+    const double jfx = in.rho_f * in.ux_f, jfy = in.rho_f * in.uy_f;
+    k.drf = static_cast<CT>(in.rho_f - in.rho0);
+    k.djfx = static_cast<CT>(jfx - jx0);
+    k.djfy = static_cast<CT>(jfy - jy0);
+    double mr[9], mb[9];
+    moment_eq(in.rho_f, jfx, jfy, mr);
+    moment_eq(in.rho0, jx0, jy0, mb);
+    for (int i = 0; i < 9; ++i) k.dmeq_ref[i] = static_cast<CT>(mr[i] - mb[i]);
+    return k;
+}
+
+template <typename CT>
+BatchInst<CT> desc_of(const Instance& in) {
+    BatchInst<CT> d{};
+    d.buf[0] = in.buf[0];
+    d.buf[1] = in.buf[1];
+    d.tx = static_cast<const AxisCoef<CT>*>(in.tabs);
+    d.ty = static_cast<const AxisCoef<CT>*>(in.tabs) + in.nx;
+    d.start = in.initialised ? in.start : LLONG_MAX;
+    d.end = in.initialised ? in.start + in.budget : LLONG_MAX;
+    d.plane = in.geo.plane;
+    d.nx = in.nx;
+    d.ny = in.ny;
+    d.pitch = static_cast<int>(in.geo.pitch);
+    d.variant = in.variant;
+    d.bc = in.bc;
+    d.k = consts_of<CT>(in);
+    return d;
+}
+
+size_t desc_size(int storage) {
+    return storage == LBM_F64 ? sizeof(BatchInst<double>) : sizeof(BatchInst<float>);
+}
+
+void drop_batch_graph(lbm_batch_ctx* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+cudaError_t launch_batch(lbm_batch_ctx* b, cudaStream_t st, int k, int pdl) {
+    switch (b->storage) {
+        case LBM_F64:
+            return lbm::launch_batch_t<double>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
+                                               b->tile_x, b->tile_y, b->grid, st, pdl);
+        case LBM_F32:
+            return lbm::launch_batch_t<float>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
+                                              b->tile_x, b->tile_y, b->grid, st, pdl);
+        case LBM_F16DEV:
+            return lbm::launch_batch_t<__half>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
+                                               b->tile_x, b->tile_y, b->grid, st, pdl);
+        default:
+            return lbm::launch_batch_t<__nv_bfloat16>(b->d_insts, b->d_tiles, b->d_ntiles,
+                                                      b->d_step, k, b->tile_x, b->tile_y,
+                                                      b->grid, st, pdl);
+    }
+}
+
+cudaError_t compute_grid(lbm_batch_ctx* b) {
+    const void* fn = nullptr;
+    switch (b->storage) {
+        case LBM_F64: fn = lbm::batch_kernel_ptr<double>(); break;
+        case LBM_F32: fn = lbm::batch_kernel_ptr<float>(); break;
+        case LBM_F16DEV: fn = lbm::batch_kernel_ptr<__half>(); break;
+        default: fn = lbm::batch_kernel_ptr<__nv_bfloat16>(); break;
+    }
+    int per_sm = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return e;
+    b->grid = std::max(1, per_sm * sms);
+    return cudaSuccess;
+}
+
+// Rebuild the descriptor array and the tile table on the device (stream-ordered).
+int sync_tables(lbm_batch_ctx* b) {
+    if (!b->dirty) return LBM_OK;
+    b->dense.clear();
+    std::vector<unsigned char> descs;
+    std::vector<BatchTile> tiles;
+    const size_t ds = desc_size(b->storage);
+    for (auto& kv : b->insts) {
+        const Instance& in = kv.second;
+        const int di = static_cast<int>(b->dense.size());
+        b->dense.push_back(kv.first);
+        const size_t off = descs.size();
+        descs.resize(off + ds);
+        if (b->storage == LBM_F64) {
+            const BatchInst<double> d = desc_of<double>(in);
+            std::memcpy(descs.data() + off, &d, ds);
+        } else {
+            const BatchInst<float> d = desc_of<float>(in);
+            std::memcpy(descs.data() + off, &d, ds);
+        }
+        if (!in.initialised) continue;
+        for (int y0 = 0; y0 < in.ny; y0 += b->tile_y)
+            for (int x0 = 0; x0 < in.nx; x0 += b->tile_x) tiles.push_back(BatchTile{di, x0, y0, 0});
+    }
+    bool realloc = false;
+    if (descs.size() > b->insts_cap) {
+        cudaStreamSynchronize(b->stream);
+        bd_free(b, b->d_insts, b->insts_cap);
+        b->insts_cap = std::max(descs.size(), 2 * b->insts_cap);
+        b->d_insts = bd_alloc(b, b->insts_cap);
+        if (!b->d_insts) return bfail(b, LBM_ERR_OOM, "descriptor table allocation failed");
+        realloc = true;
+    }
+    if (tiles.size() > b->tiles_cap) {
+        cudaStreamSynchronize(b->stream);
+        bd_free(b, b->d_tiles, b->tiles_cap * sizeof(BatchTile));
+        b->tiles_cap = std::max(tiles.size(), 2 * b->tiles_cap);
+        b->d_tiles = static_cast<BatchTile*>(bd_alloc(b, b->tiles_cap * sizeof(BatchTile)));
+        if (!b->d_tiles) return bfail(b, LBM_ERR_OOM, "tile table allocation failed");
+        realloc = true;
+    }
+    if (realloc) drop_batch_graph(b);
+    cudaError_t e = cudaSuccess;
+    if (!descs.empty())
+        e = cudaMemcpyAsync(b->d_insts, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile),
+                            cudaMemcpyHostToDevice, b->stream);
+    const int nt = static_cast<int>(tiles.size());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ntiles, &nt, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    // the host vectors die here: make sure the copies have consumed them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(e));
+    b->dirty = false;
+    return LBM_OK;
+}
+
+cudaError_t ensure_batch_graph(lbm_batch_ctx* b) {
+    if (b->graph) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!b->capture_stream) {
+        e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < kBatchChunk && e == cudaSuccess; ++k) e = launch_batch(b, b->capture_stream, k, k > 0);
+    if (e == cudaSuccess) {
+        lbm::advance_step_kernel<<<1, 1, 0, b->capture_stream>>>(b->d_step, kBatchChunk);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+Instance* find(lbm_batch_ctx* b, int id) {
+    auto it = b->insts.find(id);
+    return it == b->insts.end() ? nullptr : &it->second;
+}
+
+int64_t inst_time(const lbm_batch_ctx* b, const Instance& in) {
+    if (!in.initialised) return 0;
+    const int64_t t = b->step - in.start;
+    return t < 0 ? 0 : (t > in.budget ? in.budget : t);
+}
+
+int ensure_bstaging(lbm_batch_ctx* b, size_t need) {
+    if (b->staging && b->staging_bytes >= need) return LBM_OK;
+    cudaStreamSynchronize(b->stream);
+    bd_free(b, b->staging, b->staging_bytes);
+    b->staging = static_cast<double*>(bd_alloc(b, need));
+    b->staging_bytes = b->staging ? need : 0;
+    if (!b->staging) return bfail(b, LBM_ERR_OOM, "staging allocation failed");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_batch_instance_bytes(int nx, int ny, lbm_storage storage) {
+    if (nx < 1 || ny < 1 || storage < LBM_F64 || storage > LBM_BF16DEV) return 0;
+    const Geometry g = geometry_of(nx, ny, storage);
+    const size_t cts = storage == LBM_F64 ? 8 : 4;
+    return 2 * 9 * (size_t)g.plane * storage_size(storage) + 4 * cts * (size_t)(nx + ny);
+}
+
+int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator* alloc,
+                     lbm_batch* out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (storage < LBM_F64 || storage > LBM_BF16DEV) return LBM_ERR_ARG;
+    if (alloc && (!alloc->alloc || !alloc->free)) return LBM_ERR_ARG;
+    lbm_batch_ctx* b = new lbm_batch_ctx();
+    b->storage = storage;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (alloc) {
+        b->alloc = *alloc;
+        b->custom_alloc = true;
+    }
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = compute_grid(b);
+    if (e != cudaSuccess) {
+        delete b;
+        return LBM_ERR_CUDA;
+    }
+    b->d_ntiles = static_cast<int*>(bd_alloc(b, 256));
+    b->d_step = static_cast<long long*>(bd_alloc(b, 256));
+    b->d_diag = static_cast<double*>(bd_alloc(b, sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag)));
+    if (!b->d_ntiles || !b->d_step || !b->d_diag) {
+        lbm_batch_destroy(b);
+        return LBM_ERR_OOM;
+    }
+    e = cudaMemsetAsync(b->d_ntiles, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return LBM_ERR_CUDA;
+    }
+    if (const char* t = std::getenv("LBM_BATCH_TILE")) {
+        int tx = 0, ty = 0;
+        if (std::sscanf(t, "%dx%d", &tx, &ty) == 2) lbm_batch_set_tiling(b, tx, ty);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_tiling(lbm_batch b, int tile_x, int tile_y) {
+    if (!b) return LBM_ERR_ARG;
+    if (!(tile_x == 32 || tile_x == 64 || tile_x == 128 || tile_x == 256))
+        return bfail(b, LBM_ERR_ARG, "tile_x must be 32, 64, 128 or 256");
+    if (tile_y < 1 || tile_y > 256 || (tile_y % (256 / tile_x)) != 0)
+        return bfail(b, LBM_ERR_ARG, "tile_y must be a multiple of 256 / tile_x, at most 256");
+    b->tile_x = tile_x;
+    b->tile_y = tile_y;
+    b->dirty = true;
+    drop_batch_graph(b);
+    return LBM_OK;
+}
+
+int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double uy0,
+                  const lbm_rates* rates, lbm_bc bc, lbm_variant variant, const double* chi_x,
+                  const double* chi_y, double rho_ref, double ux_ref, double uy_ref, int64_t nsteps,
+                  int* id) {
+    if (!b) return LBM_ERR_ARG;
+    if (!id || !rates || !chi_x || !chi_y) return bfail(b, LBM_ERR_ARG, "NULL argument");
+    if (nx < 1 || ny < 1 || nsteps < 0) return bfail(b, LBM_ERR_ARG, "bad size or step budget");
+    if (bc != LBM_BC_DIRICHLET_EQ && bc != LBM_BC_PERIODIC) return bfail(b, LBM_ERR_ARG, "bad bc");
+    if (variant < LBM_SPONGE_NONE || variant > LBM_SPONGE_III) return bfail(b, LBM_ERR_ARG, "bad variant");
+    if (!(rho0 > 0) || !(rho_ref > 0) || !std::isfinite(ux0) || !std::isfinite(uy0) ||
+        !std::isfinite(ux_ref) || !std::isfinite(uy_ref))
+        return bfail(b, LBM_ERR_ARG, "bad far-field or reference state");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(rates->s[i])) return bfail(b, LBM_ERR_ARG, "non-finite rate");
+    if (!std::isfinite(rates->n) || !std::isfinite(rates->m) || rates->n < 0 || rates->m < 0)
+        return bfail(b, LBM_ERR_ARG, "bad Guo weights");
+    for (int i = 0; i < nx; ++i)
+        if (!(chi_x[i] >= 0) || !std::isfinite(chi_x[i])) return bfail(b, LBM_ERR_ARG, "bad chi_x");
+    for (int i = 0; i < ny; ++i)
+        if (!(chi_y[i] >= 0) || !std::isfinite(chi_y[i])) return bfail(b, LBM_ERR_ARG, "bad chi_y");
+    Instance in;
+    in.nx = nx;
+    in.ny = ny;
+    in.rho0 = rho0;
+    in.ux0 = ux0;
+    in.uy0 = uy0;
+    in.rho_f = rho_ref;
+    in.ux_f = ux_ref;
+    in.uy_f = uy_ref;
+    in.rates = *rates;
+    in.variant = variant;
+    in.bc = bc;
+    in.budget = nsteps;
+    in.geo = geometry_of(nx, ny, b->storage);
+    if (in.geo.plane > 2147483647LL) return bfail(b, LBM_ERR_ARG, "lattice too large");
+    in.buf_bytes = 9 * (size_t)in.geo.plane * storage_size(b->storage);
+    const size_t cts = b->storage == LBM_F64 ? 8 : 4;
+    in.tab_bytes = 4 * cts * (size_t)(nx + ny);
+    BDeviceGuard dg(b->device);
+    in.buf[0] = bd_alloc(b, in.buf_bytes);
+    in.buf[1] = bd_alloc(b, in.buf_bytes);
+    in.tabs = bd_alloc(b, in.tab_bytes);
+    if (!in.buf[0] || !in.buf[1] || !in.tabs) {
+        bd_free(b, in.buf[0], in.buf_bytes);
+        bd_free(b, in.buf[1], in.buf_bytes);
+        bd_free(b, in.tabs, in.tab_bytes);
+        return bfail(b, LBM_ERR_OOM, "instance allocation failed");
+    }
+    const double nn = rates->n, mm = rates->m;
+    cudaError_t e;
+    if (b->storage == LBM_F64) {
+        std::vector<double> t(4 * (size_t)(nx + ny));
+        for (int i = 0; i < nx + ny; ++i) {
+            const double c = i < nx ? chi_x[i] : chi_y[i - nx];
+            t[4 * i] = c;
+            t[4 * i + 1] = 1.0 / (1.0 + nn * c);
+            t[4 * i + 2] = 1.0 / (1.0 + mm * c);
+            t[4 * i + 3] = 0.0;
+        }
+        e = cudaMemcpyAsync(in.tabs, t.data(), in.tab_bytes, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    } else {
+        std::vector<float> t(4 * (size_t)(nx + ny));
+        for (int i = 0; i < nx + ny; ++i) {
+            const double c = i < nx ? chi_x[i] : chi_y[i - nx];
+            t[4 * i] = (float)c;
+            t[4 * i + 1] = (float)(1.0 / (1.0 + nn * c));
+            t[4 * i + 2] = (float)(1.0 / (1.0 + mm * c));
+            t[4 * i + 3] = 0.0f;
+        }
+        e = cudaMemcpyAsync(in.tabs, t.data(), in.tab_bytes, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    if (e != cudaSuccess) {
+        bd_free(b, in.buf[0], in.buf_bytes);
+        bd_free(b, in.buf[1], in.buf_bytes);
+        bd_free(b, in.tabs, in.tab_bytes);
+        return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_add: ") + cudaGetErrorString(e));
+    }
+    const int nid = b->next_id++;
+    b->insts[nid] = in;
+    b->dirty = true;
+    *id = nid;
+    return LBM_OK;
+}
+
+int lbm_batch_init_equilibrium(lbm_batch b, int id, const double* rho, const double* ux,
+                               const double* uy, int on_device) {
+    if (!b) return LBM_ERR_ARG;
+    Instance* in = find(b, id);
+    if (!in) return bfail(b, LBM_ERR_ARG, "unknown instance");
+    if (!rho || !ux || !uy) return bfail(b, LBM_ERR_ARG, "field pointer is NULL");
+    BDeviceGuard dg(b->device);
+    const double *dr = rho, *dx = ux, *dy = uy;
+    cudaError_t e = cudaSuccess;
+    const size_t n = (size_t)in->nx * in->ny;
+    if (!on_device) {
+        int rc = ensure_bstaging(b, 3 * n * sizeof(double));
+        if (rc) return rc;
+        e = cudaMemcpyAsync(b->staging, rho, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->staging + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->staging + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+        dr = b->staging;
+        dx = b->staging + n;
+        dy = b->staging + 2 * n;
+    }
+    if (e == cudaSuccess)
+        e = lbm::launch_init(b->storage, in->buf[0], in->geo, lbm::BaseState{in->rho0, in->ux0, in->uy0},
+                             dr, dx, dy, in->bc, b->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_init_equilibrium: ") + cudaGetErrorString(e));
+    in->initialised = true;
+    in->start = b->step;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int nsteps) {
+    if (!b) return LBM_ERR_ARG;
+    if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
+    BDeviceGuard dg(b->device);
+    int rc = sync_tables(b);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(b->stream, &cs);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "cudaStreamIsCapturing");
+    if (cs == cudaStreamCaptureStatusNone && nsteps >= kBatchChunk) {
+        e = ensure_batch_graph(b);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+        while (nsteps >= kBatchChunk) {
+            e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+            b->step += kBatchChunk;
+            nsteps -= kBatchChunk;
+        }
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        e = launch_batch(b, b->stream, k, k > 0);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    }
+    if (nsteps > 0) {
+        lbm::advance_step_kernel<<<1, 1, 0, b->stream>>>(b->d_step, nsteps);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch advance: ") + cudaGetErrorString(e));
+        b->step += nsteps;
+    }
+    return LBM_OK;
+}
+
+int64_t lbm_batch_time(lbm_batch b, int id) {
+    if (!b) return -1;
+    Instance* in = find(b, id);
+    return in ? inst_time(b, *in) : -1;
+}
+
+int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* uy, int on_device) {
+    if (!b) return LBM_ERR_ARG;
+    Instance* in = find(b, id);
+    if (!in) return bfail(b, LBM_ERR_ARG, "unknown instance");
+    if (!in->initialised) return bfail(b, LBM_ERR_STATE, "instance not initialised");
+    BDeviceGuard dg(b->device);
+    const size_t n = (size_t)in->nx * in->ny;
+    double *dr = rho_dev, *dx = ux, *dy = uy;
+    if (!on_device) {
+        int rc = ensure_bstaging(b, 3 * n * sizeof(double));
+        if (rc) return rc;
+        dr = rho_dev ? b->staging : nullptr;
+        dx = ux ? b->staging + n : nullptr;
+        dy = uy ? b->staging + 2 * n : nullptr;
+    }
+    const int cur = (int)(inst_time(b, *in) & 1);
+    cudaError_t e = lbm::launch_moments(b->storage, in->buf[cur], in->geo,
+                                        lbm::BaseState{in->rho0, in->ux0, in->uy0}, in->bc, dr, dx, dy,
+                                        b->stream);
+    if (e == cudaSuccess && !on_device) {
+        if (rho_dev) e = cudaMemcpyAsync(rho_dev, dr, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_moments: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, double out[6]) {
+    if (!b) return LBM_ERR_ARG;
+    Instance* in = find(b, id);
+    if (!in || !out) return bfail(b, LBM_ERR_ARG, "unknown instance or NULL out");
+    if (!in->initialised) return bfail(b, LBM_ERR_STATE, "instance not initialised");
+    if (x0 < 0 || y0 < 0 || x1 > in->nx || y1 > in->ny || x0 > x1 || y0 > y1)
+        return bfail(b, LBM_ERR_ARG, "region outside the lattice");
+    BDeviceGuard dg(b->device);
+    const int cur = (int)(inst_time(b, *in) & 1);
+    double* res = b->d_diag + lbm::kDiagBlocks * lbm::kDiag;
+    cudaError_t e = lbm::launch_diagnostics(b->storage, in->buf[cur], in->geo,
+                                            lbm::BaseState{in->rho0, in->ux0, in->uy0}, in->bc, x0,
+                                            y0, x1, y1, b->d_diag, res, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, lbm::kDiag * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_diagnostics: ") + cudaGetErrorString(e));
+    if (out[5] > 0) return bfail(b, LBM_ERR_NONFINITE, "the instance holds non-finite values");
+    return LBM_OK;
+}
+
+int lbm_batch_remove(lbm_batch b, int id) {
+    if (!b) return LBM_ERR_ARG;
+    Instance* in = find(b, id);
+    if (!in) return bfail(b, LBM_ERR_ARG, "unknown instance");
+    BDeviceGuard dg(b->device);
+    cudaStreamSynchronize(b->stream);  // no launch may still use its buffers
+    bd_free(b, in->buf[0], in->buf_bytes);
+    bd_free(b, in->buf[1], in->buf_bytes);
+    bd_free(b, in->tabs, in->tab_bytes);
+    b->insts.erase(id);
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_count(lbm_batch b) { return b ? static_cast<int>(b->insts.size()) : -1; }
+
+const char* lbm_batch_last_error(lbm_batch b) { return b ? b->err.c_str() : ""; }
+
+void lbm_batch_destroy(lbm_batch b) {
+    if (!b) return;
+    BDeviceGuard dg(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_batch_graph(b);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (auto& kv : b->insts) {
+        bd_free(b, kv.second.buf[0], kv.second.buf_bytes);
+        bd_free(b, kv.second.buf[1], kv.second.buf_bytes);
+        bd_free(b, kv.second.tabs, kv.second.tab_bytes);
+    }
+    bd_free(b, b->d_insts, b->insts_cap);
+    bd_free(b, b->d_tiles, b->tiles_cap * sizeof(BatchTile));
+    bd_free(b, b->d_ntiles, 256);
+    bd_free(b, b->d_step, 256);
+    bd_free(b, b->d_diag, sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag));
+    bd_free(b, b->staging, b->staging_bytes);
+    delete b;
+}
+
+}  // extern "C"

@@ -84,6 +84,25 @@ SIGNATURES = [
                                                ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]),
+    ("lbm_batch_instance_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("lbm_batch_create", ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(lbm_allocator),
+                                        ctypes.POINTER(_vp)]),
+    ("lbm_batch_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    ("lbm_batch_add", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.POINTER(lbm_rates),
+                                     ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, _i64,
+                                     ctypes.POINTER(ctypes.c_int)]),
+    ("lbm_batch_init_equilibrium", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]),
+    ("lbm_batch_step", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_batch_time", _i64, [_vp, ctypes.c_int]),
+    ("lbm_batch_moments", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]),
+    ("lbm_batch_diagnostics", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, _vp]),
+    ("lbm_batch_remove", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_batch_count", ctypes.c_int, [_vp]),
+    ("lbm_batch_last_error", ctypes.c_char_p, [_vp]),
+    ("lbm_batch_destroy", None, [_vp]),
 ]
 
 
@@ -201,6 +220,68 @@ def lbm_diagnostics_noalloc(state_ptr, storage, nx, ny, bc, rho0, ux0, uy0, x0, 
     return load().lbm_diagnostics_noalloc(state_ptr, int(storage), int(nx), int(ny), int(bc),
                                           float(rho0), float(ux0), float(uy0), int(x0), int(y0),
                                           int(x1), int(y1), out_ptr, int(out_on_device), stream)
+
+
+def lbm_batch_instance_bytes(nx, ny, storage) -> int:
+    return int(load().lbm_batch_instance_bytes(int(nx), int(ny), int(storage)))
+
+
+def lbm_batch_create(storage, stream=None, alloc: Optional[lbm_allocator] = None):
+    b = _vp()
+    rc = load().lbm_batch_create(int(storage), stream,
+                                 ctypes.byref(alloc) if alloc is not None else None,
+                                 ctypes.byref(b))
+    return rc, b
+
+
+def lbm_batch_set_tiling(b, tile_x, tile_y) -> int:
+    return load().lbm_batch_set_tiling(b, int(tile_x), int(tile_y))
+
+
+def lbm_batch_add(b, nx, ny, rho0, ux0, uy0, rates: lbm_rates, bc, variant, chi_x_ptr,
+                  chi_y_ptr, rho_ref, ux_ref, uy_ref, nsteps):
+    i = ctypes.c_int(-1)
+    rc = load().lbm_batch_add(b, int(nx), int(ny), float(rho0), float(ux0), float(uy0),
+                              ctypes.byref(rates), int(bc), int(variant), chi_x_ptr, chi_y_ptr,
+                              float(rho_ref), float(ux_ref), float(uy_ref), int(nsteps),
+                              ctypes.byref(i))
+    return rc, i.value
+
+
+def lbm_batch_init_equilibrium(b, i, rho_ptr, ux_ptr, uy_ptr, on_device) -> int:
+    return load().lbm_batch_init_equilibrium(b, int(i), rho_ptr, ux_ptr, uy_ptr, int(on_device))
+
+
+def lbm_batch_step(b, nsteps) -> int:
+    return load().lbm_batch_step(b, int(nsteps))
+
+
+def lbm_batch_time(b, i) -> int:
+    return int(load().lbm_batch_time(b, int(i)))
+
+
+def lbm_batch_moments(b, i, rho_ptr, ux_ptr, uy_ptr, on_device) -> int:
+    return load().lbm_batch_moments(b, int(i), rho_ptr, ux_ptr, uy_ptr, int(on_device))
+
+
+def lbm_batch_diagnostics(b, i, x0, y0, x1, y1, out_ptr) -> int:
+    return load().lbm_batch_diagnostics(b, int(i), int(x0), int(y0), int(x1), int(y1), out_ptr)
+
+
+def lbm_batch_remove(b, i) -> int:
+    return load().lbm_batch_remove(b, int(i))
+
+
+def lbm_batch_count(b) -> int:
+    return int(load().lbm_batch_count(b))
+
+
+def lbm_batch_last_error(b) -> str:
+    return (load().lbm_batch_last_error(b) or b"").decode()
+
+
+def lbm_batch_destroy(b) -> None:
+    load().lbm_batch_destroy(b)
 
 
 # ------------------------------------------------------------- helpers ----

@@ -1,0 +1,179 @@
+"""Continuous-batching server for lattice sweep jobs.
+
+Jobs (a lattice problem plus its number of steps) arrive over time.  The
+server keeps every admitted job's populations resident on the device, admits
+waiting jobs in arrival order whenever their device memory fits under the HBM
+budget, advances all resident jobs together (one batched launch per time step
+and storage type, replayed in chunks), and retires each job as soon as it has
+taken its own number of steps, which frees memory for the next ones.  A job
+added while others are running starts in the next chunk and shares their
+launches; each job still takes exactly its own steps, so its result is the
+same alone and in the mix.
+
+:func:`serial_loop` is the comparison: the same jobs one after another through
+the single-lattice API.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from . import lbm
+from .batch import Batch
+
+
+@dataclass
+class Job:
+    id: int
+    workload: object            # workloads.Workload (its storage field selects the format)
+    arrival: float = 0.0        # seconds after the start of the run
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    result: Optional[np.ndarray] = None   # lbm diagnostics over the layer-free interior
+    field: Optional[np.ndarray] = None    # final rho' (when the server keeps fields)
+
+    @property
+    def latency(self) -> Optional[float]:
+        return None if self.finished is None else self.finished - self.arrival
+
+    @property
+    def bytes(self) -> int:
+        w = self.workload
+        return lbm.lbm_batch_instance_bytes(w.nx, w.ny, lbm.STORAGE[w.storage])
+
+
+def interior(w):
+    W = w.width
+    return (W, W, w.nx - W, w.ny - W) if 2 * W < min(w.nx, w.ny) else (0, 0, w.nx, w.ny)
+
+
+class Server:
+    def __init__(self, hbm_budget: float = 150e9, chunk: int = 32, keep_fields: bool = False,
+                 tiling: Optional[tuple] = None, device: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.budget = float(hbm_budget)
+        self.chunk = int(chunk)
+        self.keep_fields = keep_fields
+        self.tiling = tiling
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        self.batches = {}
+        self.pending = deque()
+        self.resident = {}  # job id -> (storage, instance id, job)
+        self.used = 0
+        self.done = []
+        self.steps_run = 0
+
+    def _batch(self, storage) -> Batch:
+        if storage not in self.batches:
+            self.batches[storage] = Batch(storage, stream=self.stream, device=self.device,
+                                          tiling=self.tiling)
+        return self.batches[storage]
+
+    def submit(self, job: Job) -> None:
+        if job.bytes > self.budget:
+            raise ValueError(f"job {job.id} needs {job.bytes} bytes, more than the budget")
+        self.pending.append(job)
+
+    def admit(self, now: float) -> int:
+        n = 0
+        while self.pending and self.used + self.pending[0].bytes <= self.budget:
+            job = self.pending.popleft()
+            w = job.workload
+            b = self._batch(w.storage)
+            i = b.add_workload(w, steps=w.steps)
+            self.resident[job.id] = (w.storage, i, job)
+            self.used += job.bytes
+            job.admitted = now
+            n += 1
+        return n
+
+    def retire(self, clock) -> int:
+        n = 0
+        for jid, (st, i, job) in list(self.resident.items()):
+            b = self.batches[st]
+            if b.time(i) < job.workload.steps:
+                continue
+            job.result = b.diagnostics(i, interior(job.workload))
+            if self.keep_fields:
+                job.field = b.moments(i)[0]
+            b.remove(i)
+            self.used -= job.bytes
+            del self.resident[jid]
+            job.finished = clock()
+            self.done.append(job)
+            n += 1
+        return n
+
+    def advance(self) -> None:
+        with self.torch.cuda.stream(self.stream):
+            for st, b in self.batches.items():
+                if len(b):
+                    b.step(self.chunk)
+        self.steps_run += self.chunk
+
+    def run(self, jobs, realtime: bool = True):
+        """Serve `jobs` (sorted by arrival).  realtime: arrivals follow the wall
+        clock; otherwise every job is submitted at once in arrival order."""
+        jobs = sorted(jobs, key=lambda j: j.arrival)
+        t0 = time.perf_counter()
+
+        def clock():
+            return time.perf_counter() - t0
+
+        k = 0
+        while k < len(jobs) or self.pending or self.resident:
+            now = clock()
+            while k < len(jobs) and (not realtime or jobs[k].arrival <= now):
+                self.submit(jobs[k])
+                k += 1
+            self.admit(now)
+            if not self.resident:
+                if k < len(jobs) and realtime:
+                    time.sleep(max(0.0, jobs[k].arrival - clock()))
+                continue
+            self.advance()
+            self.retire(clock)
+        self.stream.synchronize()
+        return self.done
+
+    def close(self) -> None:
+        for b in self.batches.values():
+            b.close()
+        self.batches.clear()
+
+
+def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True):
+    """The same jobs one after another, in arrival order, through lbm_create /
+    lbm_step / lbm_diagnostics / lbm_destroy (one launch per step)."""
+    jobs = sorted(jobs, key=lambda j: j.arrival)
+    t0 = time.perf_counter()
+    for job in jobs:
+        if realtime:
+            time.sleep(max(0.0, job.arrival - (time.perf_counter() - t0)))
+        w = job.workload
+        job.admitted = time.perf_counter() - t0
+        with lbm.Lattice.from_workload(w) as lat:
+            lat.step(w.steps)
+            job.result = lat.diagnostics(interior(w))
+            if keep_fields:
+                job.field = lat.moments()[0]
+        job.finished = time.perf_counter() - t0
+    return jobs
+
+
+def summary(jobs, wall: float) -> dict:
+    lat = np.array([j.latency for j in jobs if j.latency is not None])
+    cells = sum(j.workload.cells * j.workload.steps for j in jobs)
+    return {
+        "jobs": len(jobs), "wall_s": wall, "solves_per_s": len(jobs) / wall if wall > 0 else None,
+        "mlups": cells / wall / 1e6 if wall > 0 else None,
+        "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+        "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+    }

@@ -1,0 +1,109 @@
+"""Batched stepping (lbm_batch_*): each lattice in a batch must give the result
+of the single-lattice path, whatever else is in the batch, whatever the tile
+shape, and whenever it was admitted.  The per-cell arithmetic is shared, so the
+comparisons are bit-exact."""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6350_gb300 import lbm
+
+    lbm.load()
+
+
+def _mixed_workloads(storage):
+    rng = np.random.default_rng(11)
+    mrt = np.array([1.7, 1.7, 1.7, 1.2, 1.4, 1.6, 1.6, 1.9, 1.9])
+    out = []
+    shapes = [(37, 53), (130, 64), (64, 257), (1, 1), (200, 9), (96, 96)]
+    variants = ["none", "I", "II", "III", "II", "III"]
+    for k, ((nx, ny), var) in enumerate(zip(shapes, variants)):
+        w = wl.pulse_workload(nx, ny, variant=var, storage=storage, eps=1e-3, b=3.0,
+                              width=max(0, min(nx, ny) // 5), chi_max=0.3,
+                              u0=(0.04 * (k % 3), 0.01), steps=40 + 17 * k,
+                              bc="periodic" if k % 2 else "dirichlet", name=f"mix-{k}")
+        if k % 2:
+            w = w.with_(s=mrt)
+        if nx * ny > 1:
+            w = w.with_(rho_dev=1e-3 * rng.standard_normal((ny, nx)))
+        out.append(w)
+    return out
+
+
+def _single(w, storage, steps):
+    from paper_1203_6350_gb300 import lbm
+
+    with lbm.Lattice.from_workload(w, storage=storage) as lat:
+        lat.step(steps)
+        return lat.moments()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16dev"])
+def test_batch_equals_single_lattice(storage):
+    from paper_1203_6350_gb300.batch import Batch
+
+    works = _mixed_workloads(storage)
+    with Batch(storage) as b:
+        ids = [b.add_workload(w) for w in works]
+        b.step(max(w.steps for w in works) + 5)
+        for i, w in zip(ids, works):
+            assert b.time(i) == w.steps
+            got = b.moments(i)
+            want = _single(w, storage, w.steps)
+            for a, c in zip(got, want):
+                np.testing.assert_array_equal(a, c)
+
+
+@pytest.mark.parametrize("tiling", [(32, 8), (64, 4), (128, 2), (128, 16), (256, 1), (256, 4)])
+def test_tile_shape_does_not_change_results(tiling):
+    from paper_1203_6350_gb300.batch import Batch
+
+    works = _mixed_workloads("f32")
+    with Batch("f32", tiling=tiling) as b:
+        ids = [b.add_workload(w) for w in works]
+        b.step(100)
+        res = [b.moments(i)[0] for i in ids]
+    for r, w in zip(res, works):
+        np.testing.assert_array_equal(r, _single(w, "f32", w.steps)[0])
+
+
+def test_staggered_admission_and_removal():
+    """Instances admitted at different global steps, with different budgets,
+    including one added while another is mid-run and one removed early."""
+    from paper_1203_6350_gb300.batch import Batch
+
+    works = _mixed_workloads("f32")
+    with Batch("f32") as b:
+        a = b.add_workload(works[2].with_(steps=90))
+        b.step(21)
+        c = b.add_workload(works[5].with_(steps=50))
+        d = b.add_workload(works[0].with_(steps=200))
+        b.step(33)  # 32-step graph chunk + 1 direct step
+        b.remove(d)
+        e = b.add_workload(works[1].with_(steps=7))
+        b.step(64)
+        assert b.time(a) == 90 and b.time(c) == 50 and b.time(e) == 7
+        for i, w, n in ((a, works[2], 90), (c, works[5], 50), (e, works[1], 7)):
+            np.testing.assert_array_equal(b.moments(i)[0], _single(w, "f32", n)[0])
+        assert len(b) == 3
+
+
+def test_batch_against_the_oracle():
+    from helpers import rel_l2, run_oracle
+    from paper_1203_6350_gb300.batch import Batch
+
+    w = wl.small_pulse("II", "f64")
+    with Batch("f64") as b:
+        i = b.add_workload(w.with_(steps=120))
+        b.step(200)
+        got = b.moments(i)[0]
+    assert rel_l2(got, run_oracle(w, 120)[0]) < 1e-9
