@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256-lattice batched-versus-plain-loop measurement")
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="seconds of the 200 jobs/s arrival trace to serve (0 skips)")
     return ap.parse_args()
 
 
@@ -324,6 +326,9 @@ def run_native(args):
     batched = None
     if not args.no_batched:
         batched = run_batched()
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = run_serving(args.serve_seconds)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -335,6 +340,7 @@ def run_native(args):
             "gpu_launches": launches_total,
             "reflected_energy": {k: refl.get(k) for k in VARIANTS},
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -444,6 +450,60 @@ def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
         "plain_loop_mlups": cells * steps / t_plain / 1e6,
         "speedup_vs_plain_loop": t_plain / t_batch,
         "launches_per_step": {"batched": 1, "plain_loop": count},
+    }
+
+
+def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
+    """Serving workload: Poisson arrivals at 200 jobs/s for `seconds` (sides
+    log-uniform in [128, 4096], 500-5000 steps, FP32 or FP16-deviation storage,
+    parameters as the batched workload), replayed in real time through the
+    continuous-batching server (150 GB HBM budget) and through a serial loop of
+    single-lattice solves; plus the error against the FP64 oracle on a seeded
+    1 % sample of the jobs small enough for the oracle (cells x steps <= 3e8)."""
+    import copy
+
+    from paper_1203_6350_gb300.serve import Job, Server, serial_loop, summary
+
+    reqs = wl.request_trace(seed=seed, rate=200.0, duration=seconds)
+    jobs = [Job(id=k, workload=r.workload, arrival=r.arrival) for k, r in enumerate(reqs)]
+    rng = np.random.default_rng(seed)
+    small = [j.id for j in jobs if j.workload.cells * j.workload.steps <= 3e8]
+    n_sample = max(1, int(math.ceil(0.01 * len(jobs))))
+    sample = set(int(x) for x in rng.choice(small, size=min(n_sample, len(small)), replace=False))
+    srv = Server(hbm_budget=budget, chunk=32, keep_fields=sample)
+    t0 = time.perf_counter()
+    done = srv.run(copy.deepcopy(jobs))
+    wall = time.perf_counter() - t0
+    srv.close()
+    served = summary(done, wall)
+    t0 = time.perf_counter()
+    ser = serial_loop(copy.deepcopy(jobs))
+    wall_s = time.perf_counter() - t0
+    serial = summary(ser, wall_s)
+    # oracle check of the sampled jobs' served results
+    from oracle import core
+
+    errs = []
+    for j in done:
+        if j.id not in sample:
+            continue
+        w = j.workload
+        got = j.field
+
+        prob = core.Problem(w.nx, w.ny, w.s, n=w.n, m=w.m, variant=w.variant, bc=w.bc,
+                            rho0=w.rho0, u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x,
+                            chi_y=w.chi_y)
+        ref = core.State(prob, *w.initial_fields()).run(w.steps).moments()[0]
+        den = float(np.linalg.norm(ref)) or 1.0
+        errs.append({"job": j.id, "storage": w.storage, "cells": w.cells, "steps": w.steps,
+                     "rel_l2_rho": float(np.linalg.norm(got - ref) / den)})
+    return {
+        "workload": f"Poisson 200 jobs/s for {seconds} s (seed {seed}), sides log-uniform in "
+                    f"[128, 4096], 500-5000 steps, FP32/FP16-dev, HBM budget {budget / 1e9:.0f} GB",
+        "served": served, "serial_loop": serial,
+        "solves_per_s_speedup": (served["solves_per_s"] / serial["solves_per_s"]
+                                 if serial["solves_per_s"] else None),
+        "oracle_sample": errs,
     }
 
 

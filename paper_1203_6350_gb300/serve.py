@@ -101,7 +101,8 @@ class Server:
             if b.time(i) < job.workload.steps:
                 continue
             job.result = b.diagnostics(i, interior(job.workload))
-            if self.keep_fields:
+            keep = self.keep_fields
+            if keep is True or (isinstance(keep, (set, frozenset)) and job.id in keep):
                 job.field = b.moments(i)[0]
             b.remove(i)
             self.used -= job.bytes

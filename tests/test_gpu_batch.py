@@ -1,7 +1,13 @@
 """Batched stepping (lbm_batch_*): each lattice in a batch must give the result
 of the single-lattice path, whatever else is in the batch, whatever the tile
-shape, and whenever it was admitted.  The per-cell arithmetic is shared, so the
-comparisons are bit-exact."""
+shape, and whenever it was admitted.
+
+Within the batched path the per-cell instruction sequence does not depend on
+the tile shape or on the other instances, so those comparisons are bit-exact.
+Against the single-lattice kernel the source arithmetic is shared but the
+compiler may contract multiply-adds differently in the two kernels: FP64 is
+bit-exact there, FP32 / FP16 agree to a few ulps (held to the parity
+tolerances)."""
 import numpy as np
 import pytest
 
@@ -28,7 +34,9 @@ def _mixed_workloads(storage):
     variants = ["none", "I", "II", "III", "II", "III"]
     for k, ((nx, ny), var) in enumerate(zip(shapes, variants)):
         w = wl.pulse_workload(nx, ny, variant=var, storage=storage, eps=1e-3, b=3.0,
-                              width=max(0, min(nx, ny) // 5), chi_max=0.3,
+                              width=max(0, min(nx, ny) // 5),
+                              # type I stays stable only while s + chi <= 2 (Eq. effectrelax)
+                              chi_max=0.08 if var == "I" else 0.3,
                               u0=(0.04 * (k % 3), 0.01), steps=40 + 17 * k,
                               bc="periodic" if k % 2 else "dirichlet", name=f"mix-{k}")
         if k % 2:
@@ -37,6 +45,19 @@ def _mixed_workloads(storage):
             w = w.with_(rho_dev=1e-3 * rng.standard_normal((ny, nx)))
         out.append(w)
     return out
+
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-2}
+
+
+def _close(a, b, tol):
+    if tol == 0:
+        np.testing.assert_array_equal(a, b)
+        return
+    fin = np.isfinite(b)
+    assert np.array_equal(np.isfinite(a), fin)
+    if fin.any():
+        assert np.linalg.norm(a[fin] - b[fin]) <= tol * np.linalg.norm(b[fin]) + 1e-300
 
 
 def _single(w, storage, steps):
@@ -60,20 +81,32 @@ def test_batch_equals_single_lattice(storage):
             got = b.moments(i)
             want = _single(w, storage, w.steps)
             for a, c in zip(got, want):
-                np.testing.assert_array_equal(a, c)
+                _close(a, c, 0 if storage == "f64" else TOL[storage])
+
+
+def _batch_run(works, storage, tiling=None, steps=100):
+    from paper_1203_6350_gb300.batch import Batch
+
+    with Batch(storage, tiling=tiling) as b:
+        ids = [b.add_workload(w) for w in works]
+        b.step(steps)
+        return [b.moments(i)[0] for i in ids]
 
 
 @pytest.mark.parametrize("tiling", [(32, 8), (64, 4), (128, 2), (128, 16), (256, 1), (256, 4)])
 def test_tile_shape_does_not_change_results(tiling):
-    from paper_1203_6350_gb300.batch import Batch
-
     works = _mixed_workloads("f32")
-    with Batch("f32", tiling=tiling) as b:
-        ids = [b.add_workload(w) for w in works]
-        b.step(100)
-        res = [b.moments(i)[0] for i in ids]
-    for r, w in zip(res, works):
-        np.testing.assert_array_equal(r, _single(w, "f32", w.steps)[0])
+    ref = _batch_run(works, "f32")
+    for r, q in zip(_batch_run(works, "f32", tiling), ref):
+        np.testing.assert_array_equal(r, q)
+
+
+def test_result_alone_equals_result_in_the_mix():
+    works = _mixed_workloads("f32")
+    mixed = _batch_run(works, "f32")
+    for w, m in zip(works, mixed):
+        (alone,) = _batch_run([w], "f32")
+        np.testing.assert_array_equal(alone, m)
 
 
 def test_staggered_admission_and_removal():
@@ -93,7 +126,9 @@ def test_staggered_admission_and_removal():
         b.step(64)
         assert b.time(a) == 90 and b.time(c) == 50 and b.time(e) == 7
         for i, w, n in ((a, works[2], 90), (c, works[5], 50), (e, works[1], 7)):
-            np.testing.assert_array_equal(b.moments(i)[0], _single(w, "f32", n)[0])
+            _close(b.moments(i)[0], _single(w, "f32", n)[0], TOL["f32"])
+            (alone,) = _batch_run([w.with_(steps=n)], "f32", steps=n + 3)
+            np.testing.assert_array_equal(b.moments(i)[0], alone)
         assert len(b) == 3
 
 
@@ -106,4 +141,7 @@ def test_batch_against_the_oracle():
         i = b.add_workload(w.with_(steps=120))
         b.step(200)
         got = b.moments(i)[0]
-    assert rel_l2(got, run_oracle(w, 120)[0]) < 1e-9
+    ref = run_oracle(w, 120)[0]
+    # 1e-10 relative plus the oracle's own FP64 rounding (~10 x 2^-53 per cell per step)
+    floor = 10 * 121 * 2.0**-53 * np.sqrt(ref.size)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref) + floor, rel_l2(got, ref)
