@@ -125,6 +125,14 @@ int lbm_set_sponge(lbm_handle h, lbm_variant variant, const double* chi_x, const
 int lbm_init_equilibrium(lbm_handle h, const double* rho, const double* ux, const double* uy,
                          int on_device);
 
+/* Time 0 of the 2-D acoustic pulse of Sec. 4.1 (Eqs. pulseprofile, 3:para0),
+ * built on the device with no input field: rho = rho0 + eps exp(-alpha r^2),
+ * alpha = ln 2 / half_width^2, r the distance of the cell (ix, iy) from
+ * (x0, y0), u = u0, f = f^eq(rho, u), then the boundary rule.  Asynchronous;
+ * resets the step counter.  LBM_ERR_ARG for non-finite input or
+ * half_width <= 0. */
+int lbm_init_pulse(lbm_handle h, double eps, double half_width, double x0, double y0);
+
 /* Advance nsteps >= 0 time steps: one fused kernel per step (pull-stream,
  * moments, rho* and j*, MRT relaxation, damping term, back-transform,
  * store), asynchronous on the handle's stream. */
@@ -212,6 +220,11 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
  * active from the batch's next step. */
 int lbm_batch_init_equilibrium(lbm_batch b, int id, const double* rho, const double* ux,
                                const double* uy, int on_device);
+
+/* Time 0 of instance id as the Gaussian pulse of lbm_init_pulse (built on the
+ * device); it becomes active from the batch's next step. */
+int lbm_batch_init_pulse(lbm_batch b, int id, double eps, double half_width, double x0,
+                         double y0);
 
 /* Advance the batch by nsteps global steps: every active instance takes a step
  * in each of them until its budget is spent.  Asynchronous on the stream. */

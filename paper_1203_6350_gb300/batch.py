@@ -57,14 +57,23 @@ class Batch:
         self.shapes[i] = (ny, nx)
         return i
 
-    def add_workload(self, w, steps: Optional[int] = None, init: bool = True) -> int:
+    def add_workload(self, w, steps: Optional[int] = None, init="fields") -> int:
         """Add a workloads.Workload (its own storage field is ignored: the batch's
-        storage applies) and optionally initialise it from its initial fields."""
+        storage applies).  init="fields" uploads its initial fields, "pulse"
+        builds its Gaussian pulse on the device, None leaves it uninitialised."""
         i = self.add(w.nx, w.ny, w.steps if steps is None else steps, w.s, w.n, w.m, w.rho0,
                      w.u0, w.bc, w.variant, w.chi_x, w.chi_y, w.rho_f, w.u_f)
-        if init:
+        if init == "pulse" and w.rho_dev is None:
+            mt = w.meta
+            self.init_pulse(i, mt.get("eps", 0.0), mt.get("b", 1.0), mt.get("x0", 0.0),
+                            mt.get("y0", 0.0))
+        elif init:
             self.init_equilibrium(i, *w.initial_fields())
         return i
+
+    def init_pulse(self, i, eps, half_width, x0, y0) -> None:
+        self._check(lbm.lbm_batch_init_pulse(self.b, i, eps, half_width, x0, y0),
+                    "lbm_batch_init_pulse")
 
     def init_equilibrium(self, i, rho, ux, uy) -> None:
         shp = self.shapes[i]

@@ -393,6 +393,21 @@ int lbm_init_equilibrium(lbm_handle h, const double* rho, const double* ux, cons
     return LBM_OK;
 }
 
+int lbm_init_pulse(lbm_handle h, double eps, double half_width, double x0, double y0) {
+    if (!h) return LBM_ERR_ARG;
+    if (!is_finite(eps) || !(half_width > 0) || !is_finite(half_width) || !is_finite(x0) ||
+        !is_finite(y0))
+        return fail(h, LBM_ERR_ARG, "pulse parameters must be finite with half_width > 0");
+    DeviceGuard dg(h->device);
+    h->cur = 0;
+    cudaError_t e = lbm::launch_init_pulse(h->storage, h->buf[0], h->geo, base_of(h), eps,
+                                           half_width, x0, y0, h->bc, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_init_pulse");
+    h->initialised = true;
+    h->time = 0;
+    return LBM_OK;
+}
+
 int lbm_step(lbm_handle h, int nsteps) {
     if (!h) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");

@@ -66,6 +66,55 @@ __global__ void init_kernel(PlanePtrs<T> dst, Geometry g, BaseState b, const dou
     init_plane<T, 8>(dst, g, b, rho, ux, uy, bc, x, y);
 }
 
+// Time 0 of the acoustic pulse of Sec. 4.1 (Eqs. pulseprofile, 3:para0) without
+// any input field: rho = rho0 + eps exp(-alpha |x - x_c|^2), u = u0 at every cell.
+template <typename T, int I>
+__device__ __forceinline__ void pulse_plane(const PlanePtrs<T>& dst, const Geometry& g,
+                                            const BaseState& b, double eps, double alpha,
+                                            double xc, double yc, int bc, int x, int y) {
+    using CT = typename Codec<T>::CT;
+    int sx = x + cx(I), sy = y + cy(I);
+    bool ok = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
+    if (!ok && bc == kPeriodic) {
+        sx = (sx + g.nx) % g.nx;
+        sy = (sy + g.ny) % g.ny;
+        ok = true;
+    }
+    CT v = CT(0);
+    if (ok) {
+        const double dx = sx - xc, dy = sy - yc;
+        const double dr = eps * exp(-alpha * (dx * dx + dy * dy));
+        v = feq_dev<CT>(I, CT(dr), CT(b.ux0), CT(b.uy0), CT(0), CT(0), CT(b.rho0), CT(b.ux0),
+                        CT(b.uy0));
+    }
+    dst.p[I][(long long)y * g.pitch + x] = Codec<T>::template enc<I>(v);
+}
+
+template <typename T>
+__global__ void pulse_kernel(PlanePtrs<T> dst, Geometry g, BaseState b, double eps, double alpha,
+                             double xc, double yc, int bc) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    pulse_plane<T, 0>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 1>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 2>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 3>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 4>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 5>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 6>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 7>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+    pulse_plane<T, 8>(dst, g, b, eps, alpha, xc, yc, bc, x, y);
+}
+
+template <typename T>
+cudaError_t pulse_t(void* dst, const Geometry& g, const BaseState& b, double eps, double alpha,
+                    double xc, double yc, int bc, cudaStream_t st) {
+    const dim3 block(128, 2), grid((g.nx + 127) / 128, (g.ny + 1) / 2);
+    pulse_kernel<T><<<grid, block, 0, st>>>(plane_ptrs<T>(dst, g.plane), g, b, eps, alpha, xc, yc, bc);
+    return cudaGetLastError();
+}
+
 // rho', j' of the pulled populations at (x, y), summed in the compute precision.
 template <typename T, int BC>
 __device__ __forceinline__ void cell_moments(const PlanePtrs<T>& src, const Geometry& g, int x,
@@ -223,6 +272,19 @@ cudaError_t launch_init(int storage, void* dst, const Geometry& g, const BaseSta
         case kF32: return init_t<float>(dst, g, b, rho, ux, uy, bc, st);
         case kF16: return init_t<__half>(dst, g, b, rho, ux, uy, bc, st);
         case kBF16: return init_t<__nv_bfloat16>(dst, g, b, rho, ux, uy, bc, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init_pulse(int storage, void* dst, const Geometry& g, const BaseState& b,
+                              double eps, double half_width, double xc, double yc, int bc,
+                              cudaStream_t st) {
+    const double alpha = 0.69314718055994530942 / (half_width * half_width);  // ln 2 / b^2
+    switch (storage) {
+        case kF64: return pulse_t<double>(dst, g, b, eps, alpha, xc, yc, bc, st);
+        case kF32: return pulse_t<float>(dst, g, b, eps, alpha, xc, yc, bc, st);
+        case kF16: return pulse_t<__half>(dst, g, b, eps, alpha, xc, yc, bc, st);
+        case kBF16: return pulse_t<__nv_bfloat16>(dst, g, b, eps, alpha, xc, yc, bc, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -613,6 +613,25 @@ int lbm_batch_init_equilibrium(lbm_batch b, int id, const double* rho, const dou
     return LBM_OK;
 }
 
+int lbm_batch_init_pulse(lbm_batch b, int id, double eps, double half_width, double x0,
+                         double y0) {
+    if (!b) return LBM_ERR_ARG;
+    Instance* in = find(b, id);
+    if (!in) return bfail(b, LBM_ERR_ARG, "unknown instance");
+    if (!std::isfinite(eps) || !(half_width > 0) || !std::isfinite(half_width) ||
+        !std::isfinite(x0) || !std::isfinite(y0))
+        return bfail(b, LBM_ERR_ARG, "pulse parameters must be finite with half_width > 0");
+    BDeviceGuard dg(b->device);
+    const cudaError_t e = lbm::launch_init_pulse(b->storage, in->buf[0], in->geo,
+                                                 lbm::BaseState{in->rho0, in->ux0, in->uy0}, eps,
+                                                 half_width, x0, y0, in->bc, b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_init_pulse: ") + cudaGetErrorString(e));
+    in->initialised = true;
+    in->start = b->step;
+    b->dirty = true;
+    return LBM_OK;
+}
+
 int lbm_batch_step(lbm_batch b, int nsteps) {
     if (!b) return LBM_ERR_ARG;
     if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");

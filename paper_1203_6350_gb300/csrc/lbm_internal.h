@@ -74,6 +74,11 @@ struct BaseState {
 cudaError_t launch_init(int storage, void* dst, const Geometry& g, const BaseState& b,
                         const double* rho, const double* ux, const double* uy, int bc,
                         cudaStream_t st);
+// Time-0 store of a Gaussian density pulse eps exp(-ln2 r^2 / b^2) centred at
+// (xc, yc) on the far-field state, computed in the kernel.
+cudaError_t launch_init_pulse(int storage, void* dst, const Geometry& g, const BaseState& b,
+                              double eps, double half_width, double xc, double yc, int bc,
+                              cudaStream_t st);
 // Fields of the current time (device outputs, any may be null).
 cudaError_t launch_moments(int storage, const void* src, const Geometry& g, const BaseState& b,
                            int bc, double* rho_dev, double* ux, double* uy, cudaStream_t st);

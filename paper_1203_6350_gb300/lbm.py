@@ -94,6 +94,8 @@ SIGNATURES = [
                                      ctypes.c_double, ctypes.c_double, _i64,
                                      ctypes.POINTER(ctypes.c_int)]),
     ("lbm_batch_init_equilibrium", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]),
+    ("lbm_batch_init_pulse", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.c_double] * 4),
+    ("lbm_init_pulse", ctypes.c_int, [_vp] + [ctypes.c_double] * 4),
     ("lbm_batch_step", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_batch_time", _i64, [_vp, ctypes.c_int]),
     ("lbm_batch_moments", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]),
@@ -252,6 +254,15 @@ def lbm_batch_init_equilibrium(b, i, rho_ptr, ux_ptr, uy_ptr, on_device) -> int:
     return load().lbm_batch_init_equilibrium(b, int(i), rho_ptr, ux_ptr, uy_ptr, int(on_device))
 
 
+def lbm_batch_init_pulse(b, i, eps, half_width, x0, y0) -> int:
+    return load().lbm_batch_init_pulse(b, int(i), float(eps), float(half_width), float(x0),
+                                       float(y0))
+
+
+def lbm_init_pulse(h, eps, half_width, x0, y0) -> int:
+    return load().lbm_init_pulse(h, float(eps), float(half_width), float(x0), float(y0))
+
+
 def lbm_batch_step(b, nsteps) -> int:
     return load().lbm_batch_step(b, int(nsteps))
 
@@ -356,11 +367,23 @@ class Lattice:
             warnings.warn(f"liblbm warning: {lbm_last_error(None)}", RuntimeWarning, stacklevel=2)
 
     @classmethod
-    def from_workload(cls, w, storage: Optional[str] = None, **kw) -> "Lattice":
+    def from_workload(cls, w, storage: Optional[str] = None, init: str = "fields",
+                      **kw) -> "Lattice":
+        """Lattice for a workloads.Workload.  init="fields" uploads its initial
+        fields; init="pulse" builds its Gaussian pulse on the device (workloads
+        whose initial state is a pulse described by eps, b, x0, y0)."""
         lat = cls(w.nx, w.ny, storage or w.storage, w.rho0, w.u0, w.s, w.n, w.m, w.bc, **kw)
         lat.set_sponge(w.variant, w.chi_x, w.chi_y, w.rho_f, w.u_f)
-        lat.init_equilibrium(*w.initial_fields())
+        if init == "pulse" and w.rho_dev is None:
+            mt = w.meta
+            lat.init_pulse(mt.get("eps", 0.0), mt.get("b", 1.0), mt.get("x0", 0.0),
+                           mt.get("y0", 0.0))
+        else:
+            lat.init_equilibrium(*w.initial_fields())
         return lat
+
+    def init_pulse(self, eps: float, half_width: float, x0: float, y0: float) -> None:
+        check(lbm_init_pulse(self.h, eps, half_width, x0, y0), self.h, "lbm_init_pulse")
 
     # ---- calls ----
     def set_sponge(self, variant: str, chi_x, chi_y, rho_ref: Optional[float] = None,

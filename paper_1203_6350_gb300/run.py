@@ -31,6 +31,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--width", type=int, default=128)
     ap.add_argument("--pulse", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="run this many copies of the lattice through the batched path")
+    ap.add_argument("--tile", default=None, help="batched tile shape, e.g. 128x16")
     args = ap.parse_args(argv)
 
     import torch
@@ -41,8 +44,16 @@ def main(argv=None):
     w = wl.quiescent(args.side, storage=args.storage, steps=args.steps, width=args.width,
                      variant=args.variant, pulse=args.pulse)
     stream = torch.cuda.Stream()
+    copies = max(1, args.batch)
     with torch.cuda.stream(stream):
-        lat = lbm.Lattice.from_workload(w, stream=stream)
+        if args.batch:
+            from paper_1203_6350_gb300.batch import Batch
+
+            tiling = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
+            lat = Batch(args.storage, stream=stream, tiling=tiling)
+            ids = [lat.add_workload(w, steps=1 << 40, init="pulse") for _ in range(copies)]
+        else:
+            lat = lbm.Lattice.from_workload(w, stream=stream, init="pulse")
         lat.step(args.warmup)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -51,16 +62,17 @@ def main(argv=None):
         b.record(stream)
     b.synchronize()
     t = a.elapsed_time(b) / 1e3
-    cells = w.cells * args.steps
+    cells = w.cells * args.steps * copies
     gbs = BYTES_PER_CELL[args.storage] * cells / t / 1e9
     peak = None
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         peak = float(json.load(open(p))["hbm_gbs"])
-    d = lat.diagnostics()
+    d = lat.diagnostics(ids[0]) if args.batch else lat.diagnostics()
     lat.close()
     print(json.dumps({
-        "case": f"{args.side}x{args.side} {args.storage} variant {args.variant} layer {args.width}",
+        "case": f"{copies} x {args.side}x{args.side} {args.storage} variant {args.variant} "
+                f"layer {args.width}" + (" (batched)" if args.batch else ""),
         "steps": args.steps, "mlups": cells / t / 1e6, "gbs": gbs,
         "frac_of_measured_hbm": gbs / peak if peak else None, "us_per_step": 1e6 * t / args.steps,
         "nonfinite_cells": d[5],

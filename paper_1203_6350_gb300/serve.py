@@ -52,11 +52,20 @@ def interior(w):
 
 
 class Server:
-    def __init__(self, hbm_budget: float = 150e9, chunk: int = 32, keep_fields: bool = False,
-                 tiling: Optional[tuple] = None, device: int = 0, stream=None):
+    def __init__(self, hbm_budget: float = 150e9, chunk: int = 32, keep_fields=False,
+                 tiling: Optional[tuple] = None, device: int = 0, stream=None,
+                 max_resident_cells: Optional[int] = 16 << 20, init: str = "pulse"):
+        """hbm_budget: device bytes the resident jobs may hold.  max_resident_cells:
+        slot limit -- jobs are admitted while the resident lattices hold fewer
+        cells than this (enough to keep the GPU's bandwidth busy; more only
+        stretches every job's latency), always at least one job.  init: "pulse"
+        builds each job's initial pulse on the device, "fields" uploads it."""
         import torch
 
         self.torch = torch
+        self.max_cells = max_resident_cells
+        self.init = init
+        self.cells = 0
         self.budget = float(hbm_budget)
         self.chunk = int(chunk)
         self.keep_fields = keep_fields
@@ -84,12 +93,16 @@ class Server:
     def admit(self, now: float) -> int:
         n = 0
         while self.pending and self.used + self.pending[0].bytes <= self.budget:
+            if (self.max_cells is not None and self.resident
+                    and self.cells >= self.max_cells):
+                break
             job = self.pending.popleft()
             w = job.workload
             b = self._batch(w.storage)
-            i = b.add_workload(w, steps=w.steps)
+            i = b.add_workload(w, steps=w.steps, init=self.init)
             self.resident[job.id] = (w.storage, i, job)
             self.used += job.bytes
+            self.cells += w.cells
             job.admitted = now
             n += 1
         return n
@@ -106,6 +119,7 @@ class Server:
                 job.field = b.moments(i)[0]
             b.remove(i)
             self.used -= job.bytes
+            self.cells -= job.workload.cells
             del self.resident[jid]
             job.finished = clock()
             self.done.append(job)
@@ -150,7 +164,7 @@ class Server:
         self.batches.clear()
 
 
-def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True):
+def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True, init: str = "pulse"):
     """The same jobs one after another, in arrival order, through lbm_create /
     lbm_step / lbm_diagnostics / lbm_destroy (one launch per step)."""
     jobs = sorted(jobs, key=lambda j: j.arrival)
@@ -160,7 +174,7 @@ def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True):
             time.sleep(max(0.0, job.arrival - (time.perf_counter() - t0)))
         w = job.workload
         job.admitted = time.perf_counter() - t0
-        with lbm.Lattice.from_workload(w) as lat:
+        with lbm.Lattice.from_workload(w, init=init) as lat:
             lat.step(w.steps)
             job.result = lat.diagnostics(interior(w))
             if keep_fields:

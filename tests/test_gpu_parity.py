@@ -320,3 +320,25 @@ def test_quiescent_lattice_stays_exactly_at_rest():
             lat.step(20)
             d = lat.diagnostics()
         assert d[0] == 0 and d[3] == 0 and d[4] == 0 and d[5] == 0
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_device_pulse_init_matches_field_init(storage):
+    """lbm_init_pulse builds the Gaussian pulse of Sec. 4.1 on the device; it must
+    agree with uploading the same pulse as fields (both at time 0 and after 50
+    steps), up to the last bit of the FP64 exponential."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.mean_flow_pulse(seed=1, variant="II", storage=storage, side=256, steps=50)
+    for steps in (0, 50):
+        with lbm.Lattice.from_workload(w, init="fields") as a:
+            a.step(steps)
+            fa = a.moments()
+        with lbm.Lattice.from_workload(w, init="pulse") as b:
+            b.step(steps)
+            fb = b.moments()
+        tol = 1e-12 if storage == "f64" else 1e-6  # one rounding of the stored value
+        for x, y in zip(fa, fb):
+            # scale: the field itself, or the pulse amplitude where a field is ~0 (u_y)
+            scale = np.linalg.norm(x) + 1e-3 * np.sqrt(x.size)
+            assert np.linalg.norm(x - y) <= tol * scale
