@@ -324,6 +324,47 @@ __device__ __forceinline__ void store_all(const PlanePtrs<T>& dst, int o,
     dst.p[8][o] = Codec<T>::template enc<8>(g[8]);
 }
 
+// The same pull and store addressed from one buffer base with 32-bit element
+// offsets I * plane + o (valid while 9 planes hold fewer than 2^31 elements);
+// keeps two pointers live instead of eighteen.
+template <typename T, int BC, bool CHECK, int I>
+__device__ __forceinline__ typename Codec<T>::CT pull_b(const T* __restrict__ base, int plane,
+                                                        int o, const PullSites& ps) {
+    using CT = typename Codec<T>::CT;
+    if (!CHECK || BC == kPeriodic || ps.inside<I>())
+        return Codec<T>::template dec<I>(
+            __ldg(base + static_cast<unsigned>(I * plane + o + ps.offset<I>())));
+    return CT(0);
+}
+
+template <typename T, int BC, bool CHECK>
+__device__ __forceinline__ void pull_all_b(const T* __restrict__ base, int plane, int o,
+                                           const PullSites& ps, typename Codec<T>::CT (&g)[9]) {
+    g[0] = pull_b<T, BC, CHECK, 0>(base, plane, o, ps);
+    g[1] = pull_b<T, BC, CHECK, 1>(base, plane, o, ps);
+    g[2] = pull_b<T, BC, CHECK, 2>(base, plane, o, ps);
+    g[3] = pull_b<T, BC, CHECK, 3>(base, plane, o, ps);
+    g[4] = pull_b<T, BC, CHECK, 4>(base, plane, o, ps);
+    g[5] = pull_b<T, BC, CHECK, 5>(base, plane, o, ps);
+    g[6] = pull_b<T, BC, CHECK, 6>(base, plane, o, ps);
+    g[7] = pull_b<T, BC, CHECK, 7>(base, plane, o, ps);
+    g[8] = pull_b<T, BC, CHECK, 8>(base, plane, o, ps);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_all_b(T* __restrict__ base, int plane, int o,
+                                            const typename Codec<T>::CT (&g)[9]) {
+    base[static_cast<unsigned>(o)] = Codec<T>::template enc<0>(g[0]);
+    base[static_cast<unsigned>(plane + o)] = Codec<T>::template enc<1>(g[1]);
+    base[static_cast<unsigned>(2 * plane + o)] = Codec<T>::template enc<2>(g[2]);
+    base[static_cast<unsigned>(3 * plane + o)] = Codec<T>::template enc<3>(g[3]);
+    base[static_cast<unsigned>(4 * plane + o)] = Codec<T>::template enc<4>(g[4]);
+    base[static_cast<unsigned>(5 * plane + o)] = Codec<T>::template enc<5>(g[5]);
+    base[static_cast<unsigned>(6 * plane + o)] = Codec<T>::template enc<6>(g[6]);
+    base[static_cast<unsigned>(7 * plane + o)] = Codec<T>::template enc<7>(g[7]);
+    base[static_cast<unsigned>(8 * plane + o)] = Codec<T>::template enc<8>(g[8]);
+}
+
 template <typename T>
 __host__ __device__ inline PlanePtrs<T> plane_ptrs(void* base, long long plane) {
     PlanePtrs<T> r;

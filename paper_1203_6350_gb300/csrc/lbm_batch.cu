@@ -69,8 +69,9 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
         if (step < sd.start || step >= sd.end) continue;  // block-uniform
         const int parity = (int)((step - sd.start) & 1);
-        const PlanePtrs<T> src = plane_ptrs<T>(sd.buf[parity], sd.plane);
-        const PlanePtrs<T> dst = plane_ptrs<T>(sd.buf[1 - parity], sd.plane);
+        const T* src = static_cast<const T*>(sd.buf[parity]);
+        T* dst = static_cast<T*>(sd.buf[1 - parity]);
+        const int plane = static_cast<int>(sd.plane);  // 9 * plane < 2^31 (checked on add)
         const int nx = sd.nx, ny = sd.ny, pitch = sd.pitch;
         const int x = tile.x0 + threadIdx.x;
         const bool interior = tile.x0 > 0 && tile.y0 > 0 && tile.x0 + (int)blockDim.x < nx &&
@@ -83,13 +84,13 @@ __global__ void __launch_bounds__(256)
             PullSites ps;
             if (interior) {
                 ps.interior(pitch);
-                pull_all<T, kDirichlet, false>(src, o, ps, v);
+                pull_all_b<T, kDirichlet, false>(src, plane, o, ps, v);
             } else if (sd.bc == kPeriodic) {
                 ps.edge<kPeriodic>(x, y, nx, ny, pitch);
-                pull_all<T, kPeriodic, true>(src, o, ps, v);
+                pull_all_b<T, kPeriodic, true>(src, plane, o, ps, v);
             } else {
                 ps.edge<kDirichlet>(x, y, nx, ny, pitch);
-                pull_all<T, kDirichlet, true>(src, o, ps, v);
+                pull_all_b<T, kDirichlet, true>(src, plane, o, ps, v);
             }
             switch (sd.variant) {
                 case kTypeI: collide_cell<CT, kTypeI>(v, x, y, sd.k, sd.tx, sd.ty); break;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256)
                 case kTypeIII: collide_cell<CT, kTypeIII>(v, x, y, sd.k, sd.tx, sd.ty); break;
                 default: collide_cell<CT, kNone>(v, x, y, sd.k, sd.tx, sd.ty); break;
             }
-            store_all<T>(dst, o, v);
+            store_all_b<T>(dst, plane, o, v);
         }
     }
     asm volatile("griddepcontrol.launch_dependents;");
@@ -530,7 +531,9 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
     in.bc = bc;
     in.budget = nsteps;
     in.geo = geometry_of(nx, ny, b->storage);
-    if (in.geo.plane > 2147483647LL) return bfail(b, LBM_ERR_ARG, "lattice too large");
+    if (9 * in.geo.plane > 2147483647LL)
+        return bfail(b, LBM_ERR_ARG, "lattice too large for the batched path (9 planes must hold "
+                                     "fewer than 2^31 elements)");
     in.buf_bytes = 9 * (size_t)in.geo.plane * storage_size(b->storage);
     const size_t cts = b->storage == LBM_F64 ? 8 : 4;
     in.tab_bytes = 4 * cts * (size_t)(nx + ny);

@@ -52,17 +52,24 @@ def interior(w):
 
 
 class Server:
-    def __init__(self, hbm_budget: float = 150e9, chunk: int = 32, keep_fields=False,
+    def __init__(self, hbm_budget: float = 150e9, chunk: int = 64, keep_fields=False,
                  tiling: Optional[tuple] = None, device: int = 0, stream=None,
-                 max_resident_cells: Optional[int] = 16 << 20, init: str = "pulse"):
+                 max_resident_cells: Optional[int] = 16 << 20, init: str = "pulse",
+                 solo_cells: Optional[int] = 4 << 20):
         """hbm_budget: device bytes the resident jobs may hold.  max_resident_cells:
         slot limit -- jobs are admitted while the resident lattices hold fewer
         cells than this (enough to keep the GPU's bandwidth busy; more only
         stretches every job's latency), always at least one job.  init: "pulse"
-        builds each job's initial pulse on the device, "fields" uploads it."""
+        builds each job's initial pulse on the device, "fields" uploads it.
+        solo_cells: a lattice this large fills the GPU on its own, so it runs
+        through the single-lattice kernel (chunk by chunk, interleaved on the
+        same stream with the batched launch of the smaller resident jobs); None
+        sends every job through the batch.  A job's path depends only on its
+        size, so its result does not depend on what else is resident."""
         import torch
 
         self.torch = torch
+        self.solo_cells = solo_cells
         self.max_cells = max_resident_cells
         self.init = init
         self.cells = 0
@@ -98,9 +105,14 @@ class Server:
                 break
             job = self.pending.popleft()
             w = job.workload
-            b = self._batch(w.storage)
-            i = b.add_workload(w, steps=w.steps, init=self.init)
-            self.resident[job.id] = (w.storage, i, job)
+            if self.solo_cells is not None and w.cells >= self.solo_cells:
+                lat = lbm.Lattice.from_workload(w, init=self.init, stream=self.stream,
+                                                device=self.device)
+                self.resident[job.id] = ("solo", lat, job)
+            else:
+                b = self._batch(w.storage)
+                i = b.add_workload(w, steps=w.steps, init=self.init)
+                self.resident[job.id] = (w.storage, i, job)
             self.used += job.bytes
             self.cells += w.cells
             job.admitted = now
@@ -110,14 +122,23 @@ class Server:
     def retire(self, clock) -> int:
         n = 0
         for jid, (st, i, job) in list(self.resident.items()):
-            b = self.batches[st]
-            if b.time(i) < job.workload.steps:
-                continue
-            job.result = b.diagnostics(i, interior(job.workload))
             keep = self.keep_fields
-            if keep is True or (isinstance(keep, (set, frozenset)) and job.id in keep):
-                job.field = b.moments(i)[0]
-            b.remove(i)
+            keep = keep is True or (isinstance(keep, (set, frozenset)) and job.id in keep)
+            if st == "solo":
+                if i.time < job.workload.steps:
+                    continue
+                job.result = i.diagnostics(interior(job.workload))
+                if keep:
+                    job.field = i.moments()[0]
+                i.close()
+            else:
+                b = self.batches[st]
+                if b.time(i) < job.workload.steps:
+                    continue
+                job.result = b.diagnostics(i, interior(job.workload))
+                if keep:
+                    job.field = b.moments(i)[0]
+                b.remove(i)
             self.used -= job.bytes
             self.cells -= job.workload.cells
             del self.resident[jid]
@@ -131,6 +152,11 @@ class Server:
             for st, b in self.batches.items():
                 if len(b):
                     b.step(self.chunk)
+            for st, lat, job in self.resident.values():
+                if st == "solo":
+                    n = min(self.chunk, job.workload.steps - lat.time)
+                    if n > 0:
+                        lat.step(n)
         self.steps_run += self.chunk
 
     def run(self, jobs, realtime: bool = True):
@@ -159,6 +185,10 @@ class Server:
         return self.done
 
     def close(self) -> None:
+        for st, h, _ in self.resident.values():
+            if st == "solo":
+                h.close()
+        self.resident.clear()
         for b in self.batches.values():
             b.close()
         self.batches.clear()

@@ -26,14 +26,18 @@ def _jobs():
     return [Job(id=k, workload=r.workload, arrival=0.004 * k) for k, r in enumerate(reqs)]
 
 
-def test_results_same_alone_in_the_mix_and_serial():
-    from paper_1203_6350_gb300 import lbm
+@pytest.mark.parametrize("solo_cells", [None, 12000])
+def test_results_same_alone_in_the_mix_and_serial(solo_cells):
+    """solo_cells=None: every job shares the batched launch.  12000: the larger
+    jobs run through the single-lattice kernel, interleaved with the batch."""
     from paper_1203_6350_gb300.serve import Server, serial_loop
 
     jobs = _jobs()
     assert {j.workload.storage for j in jobs} == {"f32", "f16dev"}
+    if solo_cells is not None:
+        assert 0 < sum(j.workload.cells >= solo_cells for j in jobs) < len(jobs)
     per_job = max(j.bytes for j in jobs)
-    srv = Server(hbm_budget=3.5 * per_job, chunk=16, keep_fields=True)
+    srv = Server(hbm_budget=3.5 * per_job, chunk=16, keep_fields=True, solo_cells=solo_cells)
     peak = []
     orig_admit = srv.admit
 
@@ -52,7 +56,7 @@ def test_results_same_alone_in_the_mix_and_serial():
     assert any(j.admitted > first_finish for j in mixed.values())
 
     for j in _jobs():
-        alone = Server(hbm_budget=1e12, chunk=16, keep_fields=True)
+        alone = Server(hbm_budget=1e12, chunk=16, keep_fields=True, solo_cells=solo_cells)
         (res,) = alone.run([j], realtime=False)
         alone.close()
         np.testing.assert_array_equal(res.field, mixed[j.id].field)
