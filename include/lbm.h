@@ -162,6 +162,14 @@ int lbm_set_state(lbm_handle h, const void* src, size_t bytes, int on_device, in
 /* Steps taken since lbm_init_equilibrium (or set by lbm_set_state). */
 int64_t lbm_time(lbm_handle h);
 
+/* How lbm_step issues its kernels: 0 one launch per step; 1 one launch per
+ * step, each a programmatic dependent of the previous (its launch overlaps
+ * the previous step's tail); 2 (default) replays of a captured graph of 64
+ * such launches, with single launches for the remainder.  All three compute
+ * identical results.  The environment variable LBM_LAUNCH=plain|pdl|graph
+ * sets the initial mode of new handles. */
+int lbm_set_launch_mode(lbm_handle h, int mode);
+
 /* Replace the handle's stream (borrowed; NULL = legacy default stream). */
 int lbm_set_stream(lbm_handle h, void* cuda_stream);
 

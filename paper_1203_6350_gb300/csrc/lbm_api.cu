@@ -513,6 +513,13 @@ int lbm_set_state(lbm_handle h, const void* src, size_t bytes, int on_device, in
 
 int64_t lbm_time(lbm_handle h) { return h ? h->time : -1; }
 
+int lbm_set_launch_mode(lbm_handle h, int mode) {
+    if (!h) return LBM_ERR_ARG;
+    if (mode < kLaunchPlain || mode > kLaunchGraph) return fail(h, LBM_ERR_ARG, "bad launch mode");
+    h->launch_mode = mode;
+    return LBM_OK;
+}
+
 int lbm_set_stream(lbm_handle h, void* cuda_stream) {
     if (!h) return LBM_ERR_ARG;
     h->stream = static_cast<cudaStream_t>(cuda_stream);

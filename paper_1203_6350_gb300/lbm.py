@@ -77,6 +77,7 @@ SIGNATURES = [
     ("lbm_set_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, _i64]),
     ("lbm_time", _i64, [_vp]),
     ("lbm_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("lbm_set_launch_mode", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_destroy", None, [_vp]),
     ("lbm_last_error", ctypes.c_char_p, [_vp]),
     ("lbm_version", ctypes.c_char_p, []),
@@ -209,6 +210,13 @@ def lbm_time(h) -> int:
 
 def lbm_set_stream(h, stream) -> int:
     return load().lbm_set_stream(h, stream)
+
+
+LAUNCH_MODES = {"plain": 0, "pdl": 1, "graph": 2}
+
+
+def lbm_set_launch_mode(h, mode) -> int:
+    return load().lbm_set_launch_mode(h, int(mode))
 
 
 def lbm_destroy(h) -> None:

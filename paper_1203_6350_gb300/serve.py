@@ -54,8 +54,8 @@ def interior(w):
 class Server:
     def __init__(self, hbm_budget: float = 150e9, chunk: int = 64, keep_fields=False,
                  tiling: Optional[tuple] = None, device: int = 0, stream=None,
-                 max_resident_cells: Optional[int] = 16 << 20, init: str = "pulse",
-                 solo_cells: Optional[int] = 4 << 20):
+                 max_resident_cells: Optional[int] = 4 << 20, init: str = "pulse",
+                 solo_cells: Optional[int] = 1 << 20):
         """hbm_budget: device bytes the resident jobs may hold.  max_resident_cells:
         slot limit -- jobs are admitted while the resident lattices hold fewer
         cells than this (enough to keep the GPU's bandwidth busy; more only
@@ -194,9 +194,11 @@ class Server:
         self.batches.clear()
 
 
-def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True, init: str = "pulse"):
+def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True, init: str = "pulse",
+                launch: str = "graph"):
     """The same jobs one after another, in arrival order, through lbm_create /
-    lbm_step / lbm_diagnostics / lbm_destroy (one launch per step)."""
+    lbm_step / lbm_diagnostics / lbm_destroy.  launch="plain": one kernel launch
+    per step; "graph" (the library default): graph-replayed dependent launches."""
     jobs = sorted(jobs, key=lambda j: j.arrival)
     t0 = time.perf_counter()
     for job in jobs:
@@ -205,6 +207,7 @@ def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True, init: st
         w = job.workload
         job.admitted = time.perf_counter() - t0
         with lbm.Lattice.from_workload(w, init=init) as lat:
+            lbm.check(lbm.lbm_set_launch_mode(lat.h, lbm.LAUNCH_MODES[launch]), lat.h, "launch")
             lat.step(w.steps)
             job.result = lat.diagnostics(interior(w))
             if keep_fields:
