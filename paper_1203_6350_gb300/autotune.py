@@ -15,8 +15,8 @@ from collections import Counter
 
 import numpy as np
 
-CANDIDATES = [(32, 8), (32, 16), (64, 4), (64, 8), (128, 2), (128, 8), (128, 16), (256, 1),
-              (256, 4)]
+CANDIDATES = [(32, 8), (32, 16), (64, 8), (64, 16), (128, 8), (128, 16), (128, 32), (128, 64),
+              (256, 4), (256, 8), (256, 16)]
 
 
 def cache_path() -> str:

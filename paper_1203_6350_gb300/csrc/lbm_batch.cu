@@ -40,11 +40,27 @@ struct BatchTile {
     int inst, x0, y0, pad;
 };
 
+// Blocks of 256 threads per SM the register allocation must allow: FP32 fits
+// 40 registers without spilling (6 blocks), the 16-bit formats 48 (5 blocks,
+// one register spilled outside the cell loop), FP64 80 (3 blocks).
+template <typename T>
+struct BatchMinBlocks {
+    static constexpr int value = 5;
+};
+template <>
+struct BatchMinBlocks<float> {
+    static constexpr int value = 6;
+};
+template <>
+struct BatchMinBlocks<double> {
+    static constexpr int value = 3;
+};
+
 // One time step of every active instance.  Block b walks the tiles b, b + G,
 // ...; the tile's instance descriptor is copied to shared memory, then the
 // block covers the tile_x x tile_y cells with blockDim = (tile_x, 256/tile_x).
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
     batch_step_kernel(const BatchInst<typename Codec<T>::CT>* __restrict__ insts,
                       const BatchTile* __restrict__ tiles, const int* __restrict__ ntiles_p,
                       const long long* __restrict__ step_p, int k_in_chunk, int tile_y) {
