@@ -40,12 +40,13 @@ struct BatchTile {
     int inst, x0, y0, pad;
 };
 
-// Blocks of 256 threads per SM the register allocation must allow: FP32 fits
-// 40 registers without spilling (6 blocks), the 16-bit formats 48 (5 blocks,
-// one register spilled outside the cell loop), FP64 80 (3 blocks).
+// Blocks of 256 threads per SM the register allocation must allow (0 leaves
+// it to the compiler): FP32 fits 40 registers without spilling (6 blocks),
+// FP64 80 (3 blocks); the 16-bit formats were fastest with the compiler's own
+// choice (48 registers).
 template <typename T>
 struct BatchMinBlocks {
-    static constexpr int value = 5;
+    static constexpr int value = 0;
 };
 template <>
 struct BatchMinBlocks<float> {
