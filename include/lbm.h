@@ -54,12 +54,17 @@ typedef struct lbm_ctx* lbm_handle;
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16DEV = 2, LBM_BF16DEV = 3 } lbm_storage;
 
 /* Damping term (Sec. 2.2): none, type I (Eq. app:newbgka), type II
- * (Eq. app:newbgka2), type III (Eq. app:bgk_no2ordor2). */
+ * (Eq. app:newbgka2), type III (Eq. app:bgk_no2ordor2).  LBM_SPONGE_VISCOUS
+ * is the comparison strategy of Sec. 4.1 ("viscosity absorbing"): no damping
+ * term; in the layer every non-conserved relaxation rate falls linearly from
+ * its value to 1, s_k' = s_k + (1 - s_k) r, where r in [0, 1] is the layer
+ * fraction taken from the same per-axis arrays as chi (r = max of the two). */
 typedef enum {
     LBM_SPONGE_NONE = 0,
     LBM_SPONGE_I = 1,
     LBM_SPONGE_II = 2,
-    LBM_SPONGE_III = 3
+    LBM_SPONGE_III = 3,
+    LBM_SPONGE_VISCOUS = 4
 } lbm_variant;
 
 typedef enum { LBM_BC_DIRICHLET_EQ = 0, LBM_BC_PERIODIC = 1 } lbm_bc;

@@ -20,7 +20,7 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblbm_oracle.so")
 
-VARIANTS = {"none": 0, "I": 1, "II": 2, "III": 3}
+VARIANTS = {"none": 0, "I": 1, "II": 2, "III": 3, "viscous": 4}
 BCS = {"dirichlet": 0, "periodic": 1}
 
 

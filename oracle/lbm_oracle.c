@@ -27,6 +27,9 @@
  *     type II  (Eq. app:newbgka2):      T_i = chi (f^eq_i(rho^f,u^f) - f^eq_i(rho*,u*))
  *     type III (Eq. app:bgk_no2ordor2): T_i = chi (f^Leq_i(rho^f,j^f) - f^Leq_i(rho*,j*))
  *     none:                             T_i = 0, and chi = 0 (no absorbing term at all)
+ *   The comparison strategy of Sec. 4.1 (viscosity sponge, variant 4) has no
+ *   damping term and relaxation rates that fall to 1 across the layer; see
+ *   oracle_collide_cell_viscous.
  *   f_i(x + c_i, t + 1) = fhat_i(x, t)                               (Eq. blbs)
  *
  * Readings of points the paper leaves open (each is listed in the design doc):
@@ -55,7 +58,7 @@
 typedef struct {
     int nx, ny;
     int bc;        /* 0: Dirichlet far-field equilibrium, 1: periodic */
-    int variant;   /* 0: none, 1: type I, 2: type II, 3: type III */
+    int variant;   /* 0: none, 1: type I, 2: type II, 3: type III, 4: viscosity sponge */
     double rho0, ux0, uy0;    /* far-field state of the boundary */
     double rho_f, ux_f, uy_f; /* reference state q_ref of the absorbing term */
     double s[9];   /* diagonal of S in the row order of M */
@@ -194,6 +197,34 @@ void oracle_collide_cell(const oracle_params* p, const double* lam, double chi, 
     }
 }
 
+/* The comparison strategy of Sec. 4.1 ("viscosity absorbing"): no damping
+ * term; in the layer the relaxation frequency falls linearly from its
+ * physical value to 1.  With the layer fraction r in [0, 1] (0 at the inner
+ * edge, 1 at the wall) every non-conserved rate becomes
+ * s_k' = s_k + (1 - s_k) r, so Lambda' = (1 - r) Lambda + r Lambda1 with
+ * Lambda1 = M^{-1} diag(s_0, s_1, s_2, 1, ..., 1) M.  rho, j are unchanged by
+ * the collision (no forcing, rho* = rho). */
+void oracle_collide_cell_viscous(const oracle_params* p, const double* lam, const double* lam1,
+                                 double r, const double* f, double* fhat) {
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        rho += f[i];
+        jx += CX[i] * f[i];
+        jy += CY[i] * f[i];
+    }
+    double fs[9];
+    oracle_feq(rho, jx / rho, jy / rho, fs);
+    (void)p;
+    for (int i = 0; i < 9; ++i) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < 9; ++j) {
+            a += lam[i * 9 + j] * (fs[j] - f[j]);
+            b += lam1[i * 9 + j] * (fs[j] - f[j]);
+        }
+        fhat[i] = f[i] + (1.0 - r) * a + r * b;
+    }
+}
+
 static inline size_t idx(const oracle_params* p, int i, int iy, int ix) {
     return ((size_t)i * p->ny + iy) * p->nx + ix;
 }
@@ -227,8 +258,10 @@ int oracle_run(const oracle_params* p, const double* chi_x, const double* chi_y,
                int nsteps, int nthreads) {
     const int nx = p->nx, ny = p->ny;
     if (nx <= 0 || ny <= 0 || nsteps < 0) return -1;
-    double lam[81];
+    double lam[81], lam1[81], s1[9];
     if (oracle_lambda(p->s, lam) != 0) return -2;
+    for (int k = 0; k < 9; ++k) s1[k] = k < 3 ? p->s[k] : 1.0;
+    if (oracle_lambda(s1, lam1) != 0) return -2;
     double fb[9];
     oracle_feq(p->rho0, p->ux0, p->uy0, fb);
     const size_t ncell = (size_t)nx * ny;
@@ -249,7 +282,10 @@ int oracle_run(const oracle_params* p, const double* chi_x, const double* chi_y,
                 double fc[9], fh[9];
                 for (int i = 0; i < 9; ++i) fc[i] = f[idx(p, i, iy, ix)];
                 const double chi = chi_x[ix] > chi_y[iy] ? chi_x[ix] : chi_y[iy];
-                oracle_collide_cell(p, lam, chi, fc, fh);
+                if (p->variant == 4)  /* the arrays carry the layer fraction r */
+                    oracle_collide_cell_viscous(p, lam, lam1, chi, fc, fh);
+                else
+                    oracle_collide_cell(p, lam, chi, fc, fh);
                 for (int i = 0; i < 9; ++i) post[idx(p, i, iy, ix)] = fh[i];
             }
         }

@@ -69,6 +69,23 @@ def step(f, chi, s, variant="II", n=0.5, m=0.5, rho_f=1.0, u_f=(0.0, 0.0), bc="d
          rho0=1.0, u0=(0.0, 0.0)):
     """One time step of the scheme.  f: [9, ny, nx]; chi: [ny, nx]."""
     lam = np.linalg.inv(M) @ np.diag(s) @ M
+    if variant == "viscous":
+        # Sec. 4.1 comparison: no damping term, the non-conserved rates fall
+        # linearly to 1 across the layer; chi carries the layer fraction r.
+        r = chi
+        rho = f.sum(0)
+        jx = np.tensordot(C[:, 0], f, 1)
+        jy = np.tensordot(C[:, 1], f, 1)
+        fs = feq(rho, jx / rho, jy / rho)
+        out_post = np.empty_like(f)
+        minv = np.linalg.inv(M)
+        for iy in range(f.shape[1]):
+            for ix in range(f.shape[2]):
+                sk = np.array(s, dtype=np.float64)
+                sk[3:] = sk[3:] + (1.0 - sk[3:]) * r[iy, ix]
+                lam_c = minv @ np.diag(sk) @ M
+                out_post[:, iy, ix] = f[:, iy, ix] + lam_c @ (fs[:, iy, ix] - f[:, iy, ix])
+        return _stream(out_post, bc, rho0, u0)
     if variant == "none":  # no absorbing term: F = 0, so rho* = rho and j* = j
         chi = np.zeros_like(chi)
     rho = f.sum(0)
@@ -89,6 +106,12 @@ def step(f, chi, s, variant="II", n=0.5, m=0.5, rho_f=1.0, u_f=(0.0, 0.0), bc="d
     else:
         t = 0.0
     post = f + coll + t
+    return _stream(post, bc, rho0, u0)
+
+
+def _stream(post, bc, rho0, u0):
+    """Pull streaming f_i(x) = fhat_i(x - c_i) with the boundary rule."""
+    f = post
     out = np.empty_like(f)
     if bc == "periodic":
         for i in range(9):

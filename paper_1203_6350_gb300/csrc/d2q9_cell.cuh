@@ -183,6 +183,31 @@ __device__ __forceinline__ void collide_bulk(CT (&g)[9], const StepConst<CT>& k)
     back9(mp, g);
 }
 
+// The comparison sponge of Sec. 4.1 ("viscosity absorbing"): no damping term,
+// and in the layer every non-conserved rate falls linearly toward 1,
+// s_k' = s_k + (1 - s_k) r, with r in [0, 1] the layer fraction of the cell.
+template <typename CT>
+__device__ __forceinline__ void collide_viscous(CT (&g)[9], CT r, const StepConst<CT>& k) {
+    CT m[9];
+    moments9(g, m);
+    CT e3, e4, e7, e8;
+    quad_eq(m[0], m[1], m[2], k, e3, e4, e7, e8);
+    CT sk[9];
+#pragma unroll
+    for (int i = 3; i < 9; ++i) sk[i] = k.s[i] + (CT(1) - k.s[i]) * r;
+    CT mp[9];
+    mp[0] = m[0];
+    mp[1] = m[1];
+    mp[2] = m[2];
+    mp[3] = m[3] + sk[3] * (e3 - m[3]);
+    mp[4] = m[4] + sk[4] * (e4 - m[4]);
+    mp[5] = m[5] + sk[5] * (-m[1] - m[5]);
+    mp[6] = m[6] + sk[6] * (-m[2] - m[6]);
+    mp[7] = m[7] + sk[7] * (e7 - m[7]);
+    mp[8] = m[8] + sk[8] * (e8 - m[8]);
+    back9(mp, g);
+}
+
 // Collision with an absorbing strength chi > 0 and its Guo factors rn, rm.
 template <typename CT, int VAR>
 __device__ __forceinline__ void collide_layer(CT (&g)[9], CT chi, CT rn, CT rm,

@@ -303,7 +303,13 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
 int lbm_set_sponge(lbm_handle h, lbm_variant variant, const double* chi_x, const double* chi_y,
                    double rho_ref, double ux_ref, double uy_ref) {
     if (!h) return LBM_ERR_ARG;
-    if (variant < LBM_SPONGE_NONE || variant > LBM_SPONGE_III) return fail(h, LBM_ERR_ARG, "bad variant");
+    if (variant < LBM_SPONGE_NONE || variant > LBM_SPONGE_VISCOUS) return fail(h, LBM_ERR_ARG, "bad variant");
+    if (variant == LBM_SPONGE_VISCOUS && chi_x && chi_y) {
+        for (int i = 0; i < h->nx; ++i)
+            if (chi_x[i] > 1.0) return fail(h, LBM_ERR_ARG, "viscous sponge: layer fraction above 1");
+        for (int i = 0; i < h->ny; ++i)
+            if (chi_y[i] > 1.0) return fail(h, LBM_ERR_ARG, "viscous sponge: layer fraction above 1");
+    }
     if (!chi_x || !chi_y) return fail(h, LBM_ERR_ARG, "chi arrays are NULL");
     if (!(rho_ref > 0) || !is_finite(rho_ref) || !is_finite(ux_ref) || !is_finite(uy_ref))
         return fail(h, LBM_ERR_ARG, "reference state must be finite with rho_ref > 0");

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
                 case kTypeI: collide_cell<CT, kTypeI>(v, x, y, sd.k, sd.tx, sd.ty); break;
                 case kTypeII: collide_cell<CT, kTypeII>(v, x, y, sd.k, sd.tx, sd.ty); break;
                 case kTypeIII: collide_cell<CT, kTypeIII>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                case kViscous: collide_cell<CT, kViscous>(v, x, y, sd.k, sd.tx, sd.ty); break;
                 default: collide_cell<CT, kNone>(v, x, y, sd.k, sd.tx, sd.ty); break;
             }
             store_all_b<T>(dst, plane, o, v);
@@ -522,7 +523,13 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
     if (!id || !rates || !chi_x || !chi_y) return bfail(b, LBM_ERR_ARG, "NULL argument");
     if (nx < 1 || ny < 1 || nsteps < 0) return bfail(b, LBM_ERR_ARG, "bad size or step budget");
     if (bc != LBM_BC_DIRICHLET_EQ && bc != LBM_BC_PERIODIC) return bfail(b, LBM_ERR_ARG, "bad bc");
-    if (variant < LBM_SPONGE_NONE || variant > LBM_SPONGE_III) return bfail(b, LBM_ERR_ARG, "bad variant");
+    if (variant < LBM_SPONGE_NONE || variant > LBM_SPONGE_VISCOUS) return bfail(b, LBM_ERR_ARG, "bad variant");
+    if (variant == LBM_SPONGE_VISCOUS && chi_x && chi_y) {
+        for (int i = 0; i < nx; ++i)
+            if (chi_x[i] > 1.0) return bfail(b, LBM_ERR_ARG, "viscous sponge: layer fraction above 1");
+        for (int i = 0; i < ny; ++i)
+            if (chi_y[i] > 1.0) return bfail(b, LBM_ERR_ARG, "viscous sponge: layer fraction above 1");
+    }
     if (!(rho0 > 0) || !(rho_ref > 0) || !std::isfinite(ux0) || !std::isfinite(uy0) ||
         !std::isfinite(ux_ref) || !std::isfinite(uy_ref))
         return bfail(b, LBM_ERR_ARG, "bad far-field or reference state");

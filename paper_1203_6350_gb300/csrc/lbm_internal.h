@@ -42,7 +42,7 @@ struct alignas(4 * sizeof(CT)) AxisCoef {
 };
 
 enum Storage { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
-enum Variant { kNone = 0, kTypeI = 1, kTypeII = 2, kTypeIII = 3 };
+enum Variant { kNone = 0, kTypeI = 1, kTypeII = 2, kTypeIII = 3, kViscous = 4 };
 enum Bc { kDirichlet = 0, kPeriodic = 1 };
 
 // Step launchers, one translation unit per storage type.  src holds the

@@ -30,6 +30,12 @@ __device__ __forceinline__ void collide_cell(CT (&v)[9], int x, int y, const Ste
                                              const AxisCoef<CT>* tx, const AxisCoef<CT>* ty) {
     if (VAR == kNone) {
         collide_bulk(v, k);
+    } else if (VAR == kViscous) {  // the tables' chi slot holds the layer fraction r
+        const CT r = fmax(load_coef(tx, x).chi, load_coef(ty, y).chi);
+        if (r > CT(0))
+            collide_viscous(v, r, k);
+        else
+            collide_bulk(v, k);
     } else {
         const AxisCoef<CT> ax = load_coef(tx, x), ay = load_coef(ty, y);
         const CT chi = fmax(ax.chi, ay.chi);
@@ -104,10 +110,12 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geometry& g,
     LBM_STEP_CASE(kTypeI, kDirichlet)
     LBM_STEP_CASE(kTypeII, kDirichlet)
     LBM_STEP_CASE(kTypeIII, kDirichlet)
+    LBM_STEP_CASE(kViscous, kDirichlet)
     LBM_STEP_CASE(kNone, kPeriodic)
     LBM_STEP_CASE(kTypeI, kPeriodic)
     LBM_STEP_CASE(kTypeII, kPeriodic)
     LBM_STEP_CASE(kTypeIII, kPeriodic)
+    LBM_STEP_CASE(kViscous, kPeriodic)
 #undef LBM_STEP_CASE
     return cudaErrorInvalidValue;
 }

@@ -30,7 +30,7 @@ LBM_ERR_STATE = -5
 LBM_ERR_TOO_LARGE = -6
 
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
-VARIANT = {"none": 0, "I": 1, "II": 2, "III": 3}
+VARIANT = {"none": 0, "I": 1, "II": 2, "III": 3, "viscous": 4}
 BC = {"dirichlet": 0, "periodic": 1}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 

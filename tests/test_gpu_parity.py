@@ -139,7 +139,7 @@ def _rand_workload(nx, ny, bc, variant, seed, mrt=True):
 
 @pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 7), (130, 3), (257, 129), (33, 64)])
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
-@pytest.mark.parametrize("variant", ["none", "I", "II", "III"])
+@pytest.mark.parametrize("variant", ["none", "I", "II", "III", "viscous"])
 def test_ragged_and_tiny_lattices(shape, bc, variant):
     """Tiles of 128 x 2 cells with ragged edges, 1-cell lattices, periodic wrap,
     distinct MRT rates, mean flow, q_ref different from the far field, random
@@ -342,3 +342,40 @@ def test_device_pulse_init_matches_field_init(storage):
             # scale: the field itself, or the pulse amplitude where a field is ~0 (u_y)
             scale = np.linalg.norm(x) + 1e-3 * np.sqrt(x.size)
             assert np.linalg.norm(x - y) <= tol * scale
+
+
+def test_paper_strategy_comparison_on_the_gpu():
+    """The Sec. 4.1 comparison run by the CUDA path (FP32): type II with the Orszag
+    profile, the viscosity sponge and no layer on the 200 x 200 pulse; the E_L2
+    history of each matches the oracle's and the type II layer ends an order of
+    magnitude below the other two."""
+    from oracle import core
+    from oracle import diagnostics as dg
+    from paper_1203_6350_gb300 import lbm
+
+    hist = {}
+    for variant in ("none", "viscous", "II"):
+        w = wl.pulse_workload(200, 200, variant="II", storage="f32", b=10.0, width=40,
+                              chi_max=0.0, nu=1e-5)
+        s = w.s[0]
+        if variant == "II":
+            c = wl.orszag_profile(200, 40, 4 / s - 0.001)
+            w = w.with_(chi_x=c, chi_y=c)
+        elif variant == "viscous":
+            r = wl.viscous_ramp(200, 40)
+            w = w.with_(variant="viscous", chi_x=r, chi_y=r)
+        else:
+            w = w.with_(variant="none")
+        prob = core.Problem(w.nx, w.ny, w.s, variant=w.variant, u0=w.u0, u_f=w.u_f,
+                            chi_x=w.chi_x, chi_y=w.chi_y)
+        st = core.State(prob, *w.initial_fields())
+        g_hist, o_hist = [], []
+        with lbm.Lattice.from_workload(w) as lat:
+            for _ in range(12):
+                lat.step(50)
+                st.run(50)
+                g_hist.append(dg.e_l2(lat.moments()[0]))
+                o_hist.append(dg.e_l2(st.moments()[0]))
+        np.testing.assert_allclose(g_hist, o_hist, rtol=1e-3)
+        hist[variant] = np.array(g_hist)
+    assert hist["II"][-1] < 0.1 * hist["viscous"][-1] < 0.1 * hist["none"][-1] * 1.0e1

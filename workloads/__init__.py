@@ -50,6 +50,15 @@ def ramp_profile(n: int, width: int, chi_max: float, power: float = 2.0) -> np.n
     return chi_max * (layer_depth(n, width) / width) ** power
 
 
+def viscous_ramp(n: int, width: int) -> np.ndarray:
+    """Layer fraction r = d / width in [0, 1] for the viscosity sponge of Sec. 4.1
+    (the relaxation frequency falls linearly from its physical value at the
+    inner edge of the layer, r = 0, to 1 at the wall, r = 1)."""
+    if width <= 0:
+        return np.zeros(n)
+    return layer_depth(n, width) / width
+
+
 def orszag_profile(n: int, width: int, chi: float) -> np.ndarray:
     """sigma = chi * sigma~ with the normalised A = n = 4 profile of
     Eq. (normalizedsigma), sigma~(x) = 3125 (L - x)(x - x0)^4 / (256 (L - x0)^5),
