@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256-lattice batched-versus-plain-loop measurement")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the 2048^2-16384^2 storage-format roofline sweep")
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="seconds of the 200 jobs/s arrival trace to serve (0 skips)")
     return ap.parse_args()
@@ -319,6 +321,7 @@ def run_native(args):
                            "algorithmic rate can exceed the HBM copy peak; see roofline_large "
                            "for the same kernel on a 4096x4096 lattice, larger than L2"}
     roof_large = roofline_large(peaks)
+    sweep = None if args.no_sweep else run_roofline_sweep(peaks)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -345,6 +348,7 @@ def run_native(args):
             "clocks": clocks,
             "gpu_launches": launches_total,
             "reflected_energy": {k: refl.get(k) for k in VARIANTS},
+            "roofline_sweep": sweep,
             "batched": batched,
             "serving": serving,
         }
@@ -415,6 +419,56 @@ def roofline_large(peaks, side: int = 4096, steps: int = 100):
             "frac": achieved / peaks["hbm_gbs"], "case": f"{side}x{side} FP32, 128-cell layer",
             "avg_launch_us": per_launch * 1e6, "mlups": w.cells / per_launch / 1e6,
             "traffic_profile": "profiles/step_kernel_f32_4096x4096_full.md"}
+
+
+def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", "f16dev",
+                                                                         "bf16dev"),
+                       steps: int = 50, error_steps: int = 200):
+    """Roofline sweep: square lattices at rest with a 128-cell ramped layer, each
+    storage format, MLUPS and algorithmic GB/s over `steps` steps (after warm-up);
+    plus the relative L2 error of rho' against the FP64 oracle on the 2048^2 case
+    with a centred eps = 1e-3, b = 5 pulse after `error_steps` steps."""
+    import torch
+
+    from paper_1203_6350_gb300 import lbm
+
+    rows = []
+    stream = torch.cuda.Stream()
+    for side in sides:
+        for st in storages:
+            w = wl.quiescent(side, storage=st, steps=steps, width=128)
+            with torch.cuda.stream(stream):
+                lat = with_warn(lambda: lbm.Lattice.from_workload(w, stream=stream, init="pulse"))
+                lat.step(10)
+                a = torch.cuda.Event(enable_timing=True)
+                z = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lat.step(steps)
+                z.record(stream)
+                z.synchronize()
+                lat.close()
+            t = a.elapsed_time(z) / 1e3
+            gbs = BYTES_PER_CELL[st] * w.cells * steps / t / 1e9
+            rows.append({"side": side, "storage": st, "bytes_per_cell_step": BYTES_PER_CELL[st],
+                         "mlups": w.cells * steps / t / 1e6, "gbs": gbs,
+                         "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]})
+            torch.cuda.empty_cache()
+    # error of each storage format against the oracle on the 2048^2 pulse
+    from oracle import core
+
+    w = wl.quiescent(2048, storage="f32", steps=error_steps, width=128, pulse=True)
+    prob = core.Problem(w.nx, w.ny, w.s, n=w.n, m=w.m, variant=w.variant, bc=w.bc, rho0=w.rho0,
+                        u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x, chi_y=w.chi_y)
+    ref = core.State(prob, *w.initial_fields()).run(error_steps).moments()[0]
+    errors = {}
+    for st in storages:
+        with with_warn(lambda: lbm.Lattice.from_workload(w, storage=st)) as lat:
+            lat.step(error_steps)
+            got = lat.moments()[0]
+        errors[st] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"cases": rows, "rel_l2_rho_2048_vs_oracle": errors, "error_steps": error_steps,
+            "workload": "square lattices at rest, 128-cell quadratic layer chi_max 0.1, type II; "
+                        "error case adds a centred eps=1e-3, b=5 pulse"}
 
 
 def job_value(cells_per_step: float, steps: int, t_job: float, world: int) -> float:
