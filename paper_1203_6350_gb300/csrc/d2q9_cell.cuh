@@ -139,14 +139,11 @@ __device__ __forceinline__ void quad_eq(CT drs, CT djx, CT djy, const StepConst<
     e8 = (k.rho0 * (djx * k.jy0 + k.jx0 * djy + djx * djy) - k.pxy0 * drs) * inv;
 }
 
-// g = M^T D^-1 m^+ for the post-collision moments.
+// g = M^T a for a = D^-1 m^+ (the post-collision moments already scaled).
 template <typename CT>
-__device__ __forceinline__ void back9(const CT (&mp)[9], CT (&g)[9]) {
-    const CT a0 = mp[0] * (CT(1) / CT(9));
-    const CT a1 = mp[1] * (CT(1) / CT(6)), a2 = mp[2] * (CT(1) / CT(6));
-    const CT a3 = mp[3] * (CT(1) / CT(36)), a4 = mp[4] * (CT(1) / CT(36));
-    const CT a5 = mp[5] * (CT(1) / CT(12)), a6 = mp[6] * (CT(1) / CT(12));
-    const CT a7 = mp[7] * CT(0.25), a8 = mp[8] * CT(0.25);
+__device__ __forceinline__ void back9_scaled(const CT (&a)[9], CT (&g)[9]) {
+    const CT a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3], a4 = a[4];
+    const CT a5 = a[5], a6 = a[6], a7 = a[7], a8 = a[8];
     const CT e1 = a0 - a3 - CT(2) * a4;  // shared by the axis populations
     const CT e5 = a0 + CT(2) * a3 + a4;  // shared by the diagonal populations
     const CT x1 = a1 - CT(2) * a5, y1 = a2 - CT(2) * a6;
@@ -163,24 +160,25 @@ __device__ __forceinline__ void back9(const CT (&mp)[9], CT (&g)[9]) {
 }
 
 // Collision where chi = 0: rho* = rho, j* = j, no damping term.  The
-// conserved rows are unchanged; the other six relax toward m^eq(rho, j).
+// conserved rows are unchanged; the other six relax toward m^eq(rho, j):
+// D^-1 m_k^+ = ((1 - s_k)/D_k) m_k + (s_k/D_k) m_k^eq.
 template <typename CT>
 __device__ __forceinline__ void collide_bulk(CT (&g)[9], const StepConst<CT>& k) {
     CT m[9];
     moments9(g, m);
     CT e3, e4, e7, e8;
     quad_eq(m[0], m[1], m[2], k, e3, e4, e7, e8);
-    CT mp[9];
-    mp[0] = m[0];
-    mp[1] = m[1];
-    mp[2] = m[2];
-    mp[3] = m[3] + k.s[3] * (e3 - m[3]);
-    mp[4] = m[4] + k.s[4] * (e4 - m[4]);
-    mp[5] = m[5] + k.s[5] * (-m[1] - m[5]);
-    mp[6] = m[6] + k.s[6] * (-m[2] - m[6]);
-    mp[7] = m[7] + k.s[7] * (e7 - m[7]);
-    mp[8] = m[8] + k.s[8] * (e8 - m[8]);
-    back9(mp, g);
+    CT a[9];
+    a[0] = m[0] * k.dinv[0];
+    a[1] = m[1] * k.dinv[1];
+    a[2] = m[2] * k.dinv[2];
+    a[3] = k.keep[3] * m[3] + k.take[3] * e3;
+    a[4] = k.keep[4] * m[4] + k.take[4] * e4;
+    a[5] = k.keep[5] * m[5] - k.take[5] * m[1];
+    a[6] = k.keep[6] * m[6] - k.take[6] * m[2];
+    a[7] = k.keep[7] * m[7] + k.take[7] * e7;
+    a[8] = k.keep[8] * m[8] + k.take[8] * e8;
+    back9_scaled(a, g);
 }
 
 // The comparison sponge of Sec. 4.1 ("viscosity absorbing"): no damping term,
@@ -195,17 +193,17 @@ __device__ __forceinline__ void collide_viscous(CT (&g)[9], CT r, const StepCons
     CT sk[9];
 #pragma unroll
     for (int i = 3; i < 9; ++i) sk[i] = k.s[i] + (CT(1) - k.s[i]) * r;
-    CT mp[9];
-    mp[0] = m[0];
-    mp[1] = m[1];
-    mp[2] = m[2];
-    mp[3] = m[3] + sk[3] * (e3 - m[3]);
-    mp[4] = m[4] + sk[4] * (e4 - m[4]);
-    mp[5] = m[5] + sk[5] * (-m[1] - m[5]);
-    mp[6] = m[6] + sk[6] * (-m[2] - m[6]);
-    mp[7] = m[7] + sk[7] * (e7 - m[7]);
-    mp[8] = m[8] + sk[8] * (e8 - m[8]);
-    back9(mp, g);
+    CT a[9];
+    a[0] = m[0] * k.dinv[0];
+    a[1] = m[1] * k.dinv[1];
+    a[2] = m[2] * k.dinv[2];
+    a[3] = (m[3] + sk[3] * (e3 - m[3])) * k.dinv[3];
+    a[4] = (m[4] + sk[4] * (e4 - m[4])) * k.dinv[4];
+    a[5] = (m[5] + sk[5] * (-m[1] - m[5])) * k.dinv[5];
+    a[6] = (m[6] + sk[6] * (-m[2] - m[6])) * k.dinv[6];
+    a[7] = (m[7] + sk[7] * (e7 - m[7])) * k.dinv[7];
+    a[8] = (m[8] + sk[8] * (e8 - m[8])) * k.dinv[8];
+    back9_scaled(a, g);
 }
 
 // Collision with an absorbing strength chi > 0 and its Guo factors rn, rm.
@@ -246,10 +244,11 @@ __device__ __forceinline__ void collide_layer(CT (&g)[9], CT chi, CT rn, CT rm,
         t[7] = CT(0);
         t[8] = CT(0);
     }
-    CT mp[9];
+    // D^-1 m_k^+ = ((1 - s_k)/D_k) m_k + (s_k/D_k) m_k^eq + chi T_k / D_k
+    CT a[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) mp[i] = m[i] + k.s[i] * (meq[i] - m[i]) + chi * t[i];
-    back9(mp, g);
+    for (int i = 0; i < 9; ++i) a[i] = k.keep[i] * m[i] + k.take[i] * meq[i] + (chi * k.dinv[i]) * t[i];
+    back9_scaled(a, g);
 }
 
 // Per-plane base pointers of one population buffer.

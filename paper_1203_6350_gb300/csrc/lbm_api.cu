@@ -36,6 +36,7 @@ struct lbm_ctx {
     size_t staging_bytes = 0;
     int variant = 0;
     double rho_f = 1, ux_f = 0, uy_f = 0;
+    int bulk[4] = {0, 0, 0, 0};  // rectangle [x0, x1) x [y0, y1) where chi = 0
     StepConst<double> k64{};
     StepConst<float> k32{};
     bool initialised = false;
@@ -135,6 +136,11 @@ void fill_const(const lbm_ctx* h, StepConst<CT>& k) {
     meq(h->rho_f, jfx, jfy, mr);
     meq(h->rho0, jx0, jy0, mb);
     for (int i = 0; i < 9; ++i) k.dmeq_ref[i] = static_cast<CT>(mr[i] - mb[i]);
+    lbm::fill_relax(k, h->rates.s);
+    k.bulk_x0 = h->bulk[0];
+    k.bulk_x1 = h->bulk[1];
+    k.bulk_y0 = h->bulk[2];
+    k.bulk_y1 = h->bulk[3];
 }
 
 void refresh_consts(lbm_ctx* h) {
@@ -253,6 +259,10 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     h->rho_f = rho0;
     h->ux_f = ux0;
     h->uy_f = uy0;
+    h->bulk[0] = 0;  // no layer until lbm_set_sponge
+    h->bulk[1] = nx;
+    h->bulk[2] = 0;
+    h->bulk[3] = ny;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) {
         delete h;
@@ -361,6 +371,8 @@ int lbm_set_sponge(lbm_handle h, lbm_variant variant, const double* chi_x, const
     h->rho_f = rho_ref;
     h->ux_f = ux_ref;
     h->uy_f = uy_ref;
+    lbm::zero_run(chi_x, h->nx, h->bulk[0], h->bulk[1]);
+    lbm::zero_run(chi_y, h->ny, h->bulk[2], h->bulk[3]);
     refresh_consts(h);
     const double s_nu = h->rates.s[7];
     if ((variant == LBM_SPONGE_II || variant == LBM_SPONGE_III) && chi_max > 4.0 / s_nu)

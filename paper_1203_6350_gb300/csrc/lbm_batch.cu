@@ -172,6 +172,7 @@ struct Instance {
     size_t buf_bytes = 0, tab_bytes = 0;
     void* buf[2] = {nullptr, nullptr};
     void* tabs = nullptr;  // AxisCoef x table followed by y table
+    int bulk[4] = {0, 0, 0, 0};  // rectangle [x0, x1) x [y0, y1) where chi = 0
     bool initialised = false;
 };
 
@@ -285,6 +286,11 @@ StepConst<CT> consts_of(const Instance& in) {
     moment_eq(in.rho_f, jfx, jfy, mr);
     moment_eq(in.rho0, jx0, jy0, mb);
     for (int i = 0; i < 9; ++i) k.dmeq_ref[i] = static_cast<CT>(mr[i] - mb[i]);
+    lbm::fill_relax(k, in.rates.s);
+    k.bulk_x0 = in.bulk[0];
+    k.bulk_x1 = in.bulk[1];
+    k.bulk_y0 = in.bulk[2];
+    k.bulk_y1 = in.bulk[3];
     return k;
 }
 
@@ -554,6 +560,8 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
     in.variant = variant;
     in.bc = bc;
     in.budget = nsteps;
+    lbm::zero_run(chi_x, nx, in.bulk[0], in.bulk[1]);
+    lbm::zero_run(chi_y, ny, in.bulk[2], in.bulk[3]);
     in.geo = geometry_of(nx, ny, b->storage);
     if (9 * in.geo.plane > 2147483647LL)
         return bfail(b, LBM_ERR_ARG, "lattice too large for the batched path (9 planes must hold "

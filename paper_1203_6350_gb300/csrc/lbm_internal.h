@@ -30,6 +30,10 @@ struct StepConst {
     CT pxy0;          // jx0 * jy0
     CT drf, djfx, djfy;  // reference state minus base: rho_f - rho0, j_f - j0
     CT dmeq_ref[9];   // m^eq(rho_f, j_f) - m^eq(rho0, j0), evaluated in FP64 on the host
+    CT keep[9];       // (1 - s_k) / D_k: relaxation with the D^-1 of the back-transform folded in
+    CT take[9];       // s_k / D_k
+    CT dinv[9];       // 1 / D_k, D = diag(9, 6, 6, 36, 36, 12, 12, 4, 4)
+    int bulk_x0, bulk_x1, bulk_y0, bulk_y1;  // chi = 0 for bulk_x0 <= x < bulk_x1 and bulk_y0 <= y < bulk_y1
 };
 
 // Per-axis absorbing-layer coefficients: the strength chi and the Guo factors
@@ -40,6 +44,35 @@ template <typename CT>
 struct alignas(4 * sizeof(CT)) AxisCoef {
     CT chi, rn, rm, pad;
 };
+
+// Host-side: the relaxation constants of StepConst for the nine rates s.
+template <typename CT>
+inline void fill_relax(StepConst<CT>& k, const double* s) {
+    const double D[9] = {9, 6, 6, 36, 36, 12, 12, 4, 4};
+    for (int i = 0; i < 9; ++i) {
+        k.keep[i] = static_cast<CT>((1.0 - s[i]) / D[i]);
+        k.take[i] = static_cast<CT>(s[i] / D[i]);
+        k.dinv[i] = static_cast<CT>(1.0 / D[i]);
+    }
+}
+
+// Host-side: the longest run [lo, hi) of zeros in a[0..n) ([0, 0) if none).
+inline void zero_run(const double* a, int n, int& lo, int& hi) {
+    lo = hi = 0;
+    for (int i = 0; i < n;) {
+        if (a[i] != 0.0) {
+            ++i;
+            continue;
+        }
+        int j = i;
+        while (j < n && a[j] == 0.0) ++j;
+        if (j - i > hi - lo) {
+            lo = i;
+            hi = j;
+        }
+        i = j;
+    }
+}
 
 enum Storage { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum Variant { kNone = 0, kTypeI = 1, kTypeII = 2, kTypeIII = 3, kViscous = 4 };

@@ -28,8 +28,8 @@ __device__ __forceinline__ AxisCoef<double> load_coef(const AxisCoef<double>* t,
 template <typename CT, int VAR>
 __device__ __forceinline__ void collide_cell(CT (&v)[9], int x, int y, const StepConst<CT>& k,
                                              const AxisCoef<CT>* tx, const AxisCoef<CT>* ty) {
-    if (VAR == kNone) {
-        collide_bulk(v, k);
+    if (VAR == kNone || (x >= k.bulk_x0 && x < k.bulk_x1 && y >= k.bulk_y0 && y < k.bulk_y1)) {
+        collide_bulk(v, k);  // no layer here: skip the per-axis tables
     } else if (VAR == kViscous) {  // the tables' chi slot holds the layer fraction r
         const CT r = fmax(load_coef(tx, x).chi, load_coef(ty, y).chi);
         if (r > CT(0))
