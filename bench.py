@@ -313,13 +313,36 @@ def run_native(args):
     achieved = bytes_launch / per_launch / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(),
-            "kernel": "lbm::step_kernel<float, variant, Dirichlet>",
+            "kernel": STEP_KERNEL[lats[0].cells_per_thread],
+            "cells_per_thread": lats[0].cells_per_thread,
             "bytes_per_launch": bytes_launch, "avg_launch_us": per_launch * 1e6,
             "peak_source": peaks["source"],
             "working_set": "the 75.5 MB double-buffered state of a 1024x1024 solve stays in L2 "
                            "across its steps (ncu: ~21 MB of DRAM traffic per launch), so the "
                            "algorithmic rate can exceed the HBM copy peak; see roofline_large "
                            "for the same kernel on a 4096x4096 lattice, larger than L2"}
+    # the same solves with the one-cell-per-thread kernel, for comparison
+    one_cell = None
+    if lats[0].cells_per_thread == 2:
+        t1 = 0.0
+        with torch.cuda.stream(stream):
+            for w, lat, f in zip(works, lats, fields):
+                lat.cells_per_thread = 1
+                lat.init_equilibrium(*f)
+                lat.step(64)
+                a1 = torch.cuda.Event(enable_timing=True)
+                b1 = torch.cuda.Event(enable_timing=True)
+                a1.record(stream)
+                lat.step(w.steps)
+                b1.record(stream)
+                b1.synchronize()
+                t1 += a1.elapsed_time(b1) / 1e3
+                lat.cells_per_thread = 2
+        per1 = t1 / sum(w.steps for w in works)
+        one_cell = {"kernel": STEP_KERNEL[1], "avg_launch_us": per1 * 1e6,
+                    "achieved": bytes_launch / per1 / 1e9,
+                    "mlups": works[0].cells / per1 / 1e6}
+    roof["one_cell_per_thread"] = one_cell
     roof_large = roofline_large(peaks)
     sweep = None if args.no_sweep else run_roofline_sweep(peaks)
 
@@ -365,7 +388,8 @@ def with_warn(fn):
         return fn()
 
 
-KERNEL_SOURCES = ("d2q9_cell.cuh", "lbm_step.cuh", "step_f32.cu", "lbm_internal.h")
+KERNEL_SOURCES = ("d2q9_cell.cuh", "lbm_step.cuh", "step_f32.cu", "lbm_step2.cuh", "step2_f32.cu",
+                  "lbm_internal.h")
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_f32_meanflow_1024x1024_traffic.md")
 
 
@@ -395,17 +419,24 @@ def profiled_traffic():
         return None
 
 
-def roofline_large(peaks, side: int = 4096, steps: int = 100):
-    """The same FP32 step kernel on a lattice larger than L2 (HBM-bound)."""
+STEP_KERNEL = {1: "lbm::step_kernel<float, variant, Dirichlet> (one cell per thread)",
+               2: "lbm::step2_kernel<float, variant, Dirichlet> (two cells per thread, packed FP32)"}
+
+
+def timed_steps(w, steps: int, cells=None, warm: int = 10) -> float:
+    """Seconds for `steps` steps of workload w (device pulse init, `warm`
+    untimed steps first), through the graph-replayed lbm_step on a side stream;
+    cells = cells per thread of the step kernel (None: the library default)."""
     import torch
 
     from paper_1203_6350_gb300 import lbm
 
-    w = wl.quiescent(side, storage="f32", steps=steps, width=128, pulse=True)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         lat = with_warn(lambda: lbm.Lattice.from_workload(w, stream=stream, init="pulse"))
-        lat.step(10)
+        if cells is not None:
+            lat.cells_per_thread = cells
+        lat.step(warm)
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -413,11 +444,22 @@ def roofline_large(peaks, side: int = 4096, steps: int = 100):
         z.record(stream)
         z.synchronize()
         lat.close()
-    per_launch = a.elapsed_time(z) / 1e3 / steps
+    return a.elapsed_time(z) / 1e3
+
+
+def roofline_large(peaks, side: int = 4096, steps: int = 100):
+    """The same FP32 step kernel on a lattice larger than L2 (HBM-bound), with
+    two cells per thread (the default) and with one."""
+    w = wl.quiescent(side, storage="f32", steps=steps, width=128, pulse=True)
+    per_launch = timed_steps(w, steps) / steps
+    per_launch_1 = timed_steps(w, steps, cells=1) / steps
     achieved = BYTES_PER_CELL["f32"] * w.cells / per_launch / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "case": f"{side}x{side} FP32, 128-cell layer",
+            "kernel": STEP_KERNEL[2],
             "avg_launch_us": per_launch * 1e6, "mlups": w.cells / per_launch / 1e6,
+            "one_cell_per_thread": {"avg_launch_us": per_launch_1 * 1e6,
+                                    "mlups": w.cells / per_launch_1 / 1e6},
             "traffic_profile": "profiles/step_kernel_f32_4096x4096_full.md"}
 
 
@@ -433,25 +475,16 @@ def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", 
     from paper_1203_6350_gb300 import lbm
 
     rows = []
-    stream = torch.cuda.Stream()
     for side in sides:
         for st in storages:
             w = wl.quiescent(side, storage=st, steps=steps, width=128)
-            with torch.cuda.stream(stream):
-                lat = with_warn(lambda: lbm.Lattice.from_workload(w, stream=stream, init="pulse"))
-                lat.step(10)
-                a = torch.cuda.Event(enable_timing=True)
-                z = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                lat.step(steps)
-                z.record(stream)
-                z.synchronize()
-                lat.close()
-            t = a.elapsed_time(z) / 1e3
-            gbs = BYTES_PER_CELL[st] * w.cells * steps / t / 1e9
-            rows.append({"side": side, "storage": st, "bytes_per_cell_step": BYTES_PER_CELL[st],
-                         "mlups": w.cells * steps / t / 1e6, "gbs": gbs,
-                         "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]})
+            for cells in (2, 1):
+                t = timed_steps(w, steps, cells=cells)
+                gbs = BYTES_PER_CELL[st] * w.cells * steps / t / 1e9
+                rows.append({"side": side, "storage": st, "cells_per_thread": cells,
+                             "bytes_per_cell_step": BYTES_PER_CELL[st],
+                             "mlups": w.cells * steps / t / 1e6, "gbs": gbs,
+                             "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]})
             torch.cuda.empty_cache()
     # error of each storage format against the oracle on the 2048^2 pulse
     from oracle import core

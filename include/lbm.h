@@ -175,6 +175,20 @@ int64_t lbm_time(lbm_handle h);
  * sets the initial mode of new handles. */
 int lbm_set_launch_mode(lbm_handle h, int mode);
 
+/* Cells each thread of the step kernel advances: 1, or 2 -- the neighbouring
+ * cells (x, x + 1) stepped together with packed two-lane FP32 arithmetic and
+ * paired loads and stores.  2 is available for LBM_F32, LBM_F16DEV and
+ * LBM_BF16DEV storage while the nine population planes hold fewer than 2^32
+ * elements, and is then the default; otherwise (and for LBM_F64) 1.  Both
+ * evaluate the same collision in the same order; they agree to FP32
+ * rounding (the code generator may fuse a product into the add that
+ * consumes it in one form and not in the other).  LBM_ERR_ARG for any other
+ * value or an unsupported 2.  Waits for the handle's stream.  The environment
+ * variable LBM_CPT=1 makes 1 the initial choice of new handles. */
+int lbm_set_cells_per_thread(lbm_handle h, int cells);
+/* The current choice (LBM_ERR_ARG for a NULL handle). */
+int lbm_cells_per_thread(lbm_handle h);
+
 /* Replace the handle's stream (borrowed; NULL = legacy default stream). */
 int lbm_set_stream(lbm_handle h, void* cuda_stream);
 

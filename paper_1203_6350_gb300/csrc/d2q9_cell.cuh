@@ -95,6 +95,61 @@ struct Codec<__nv_bfloat16> {
     }
 };
 
+// ---- Arithmetic on one cell (float, double) or on two packed cells (F2) ----
+//
+// The collision below is written once over a value type V.  For F2 every
+// operation is one packed FP32 instruction (add/sub/mul/fma .rn.f32x2) that
+// does the work of two scalar ones; each lane rounds as the scalar
+// instruction does (checked on the GPU lane by lane).
+
+// fmadd is one fused multiply-add.  A product written with mul may be fused
+// by the compiler into an add that consumes it, in the scalar and in the
+// packed form alike (for the packed instructions the code generator does so
+// whenever the pattern allows), so the two forms agree to FP32 rounding, not
+// bit for bit.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul(float a, float b) { return a * b; }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+
+__device__ __forceinline__ F2 f2(float lo, float hi) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.u) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(F2 a) { return __uint_as_float(static_cast<unsigned>(a.u)); }
+__device__ __forceinline__ float f2_hi(F2 a) { return __uint_as_float(static_cast<unsigned>(a.u >> 32)); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ F2 mul(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ F2 fmadd(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.u) : "l"(a.u), "l"(b.u), "l"(c.u));
+    return r;
+}
+
+// A numeric literal in the value type.
+template <typename V>
+__device__ __forceinline__ V lit(float c) {
+    return V(c);
+}
+template <>
+__device__ __forceinline__ F2 lit<F2>(float c) {
+    return f2(c, c);
+}
+
 // Reciprocal of a value near rho0^2.  FP32: the hardware approximation
 // (max 1 ulp); it only scales the |j|^2/rho terms of the equilibrium.
 __device__ __forceinline__ float rcp_eq(float x) {
@@ -103,151 +158,162 @@ __device__ __forceinline__ float rcp_eq(float x) {
     return r;
 }
 __device__ __forceinline__ double rcp_eq(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ F2 rcp_eq(F2 x) { return f2(rcp_eq(f2_lo(x)), rcp_eq(f2_hi(x))); }
 
 // Moments m = M g (App. A.1), written as sums and differences.
-template <typename CT>
-__device__ __forceinline__ void moments9(const CT (&g)[9], CT (&m)[9]) {
-    const CT a13 = g[1] - g[3], a24 = g[2] - g[4];
-    const CT b57 = g[5] - g[7], c86 = g[8] - g[6];
-    const CT p13 = g[1] + g[3], p24 = g[2] + g[4];
-    const CT p57 = g[5] + g[7], p68 = g[6] + g[8];
-    const CT s14 = p13 + p24, s58 = p57 + p68;
-    m[0] = g[0] + s14 + s58;                   // rho'
-    m[1] = a13 + b57 + c86;                    // j_x'
-    m[2] = a24 + b57 - c86;                    // j_y'
-    m[3] = CT(2) * s58 - s14 - CT(4) * g[0];   // e
-    m[4] = CT(4) * g[0] - CT(2) * s14 + s58;   // epsilon
-    m[5] = b57 + c86 - CT(2) * a13;            // q_x
-    m[6] = b57 - c86 - CT(2) * a24;            // q_y
-    m[7] = p13 - p24;                          // p_xx
-    m[8] = p57 - p68;                          // p_xy
+template <typename V>
+__device__ __forceinline__ void moments9(const V (&g)[9], V (&m)[9]) {
+    const V a13 = g[1] - g[3], a24 = g[2] - g[4];
+    const V b57 = g[5] - g[7], c86 = g[8] - g[6];
+    const V p13 = g[1] + g[3], p24 = g[2] + g[4];
+    const V p57 = g[5] + g[7], p68 = g[6] + g[8];
+    const V s14 = p13 + p24, s58 = p57 + p68;
+    const V bpc = b57 + c86, bmc = b57 - c86;
+    m[0] = g[0] + s14 + s58;                                 // rho'
+    m[1] = a13 + bpc;                                        // j_x'
+    m[2] = a24 + bmc;                                        // j_y'
+    m[3] = (s58 + s58) - fmadd(lit<V>(4.0f), g[0], s14);     // e: 2 s58 - s14 - 4 g0
+    m[4] = fmadd(lit<V>(4.0f), g[0], s58) - (s14 + s14);     // epsilon: 4 g0 - 2 s14 + s58
+    m[5] = fmadd(lit<V>(-2.0f), a13, bpc);                   // q_x
+    m[6] = fmadd(lit<V>(-2.0f), a24, bmc);                   // q_y
+    m[7] = p13 - p24;                                        // p_xx
+    m[8] = p57 - p68;                                        // p_xy
 }
 
 // m^eq(rho*, j*) - m^eq(rho0, j0) for rows 3, 4, 7, 8 (the nonlinear ones),
 // without cancellation:
-//   |j*|^2/rho* - |j0|^2/rho0 = (rho0 (|j*|^2 - |j0|^2) - |j0|^2 drho*) / (rho* rho0).
-template <typename CT>
-__device__ __forceinline__ void quad_eq(CT drs, CT djx, CT djy, const StepConst<CT>& k, CT& e3,
-                                        CT& e4, CT& e7, CT& e8) {
-    const CT inv = rcp_eq((k.rho0 + drs) * k.rho0);
-    const CT ax = djx * (CT(2) * k.jx0 + djx);
-    const CT ay = djy * (CT(2) * k.jy0 + djy);
-    const CT q = (k.rho0 * (ax + ay) - k.jj0 * drs) * inv;
-    e3 = CT(3) * q - CT(2) * drs;
-    e4 = drs - CT(3) * q;
-    e7 = (k.rho0 * (ax - ay) - k.jxy0 * drs) * inv;
-    e8 = (k.rho0 * (djx * k.jy0 + k.jx0 * djy + djx * djy) - k.pxy0 * drs) * inv;
+//   |j*|^2/rho* - |j0|^2/rho0 = (rho0 (|j*|^2 - |j0|^2) - |j0|^2 drho*) / (rho* rho0),
+// with |j*|^2 - |j0|^2 = djx (2 jx0 + djx) + djy (2 jy0 + djy).
+template <typename V>
+__device__ __forceinline__ void quad_eq(V drs, V djx, V djy, const StepConst<V>& k, V& e3, V& e4,
+                                        V& e7, V& e8) {
+    const V inv = rcp_eq(mul(k.rho0 + drs, k.rho0));
+    const V ax = mul(djx, k.jx0_2 + djx);
+    const V ay = mul(djy, k.jy0_2 + djy);
+    const V q = mul(fmadd(k.njj0, drs, mul(k.rho0, ax + ay)), inv);
+    e3 = fmadd(lit<V>(3.0f), q, mul(lit<V>(-2.0f), drs));
+    e4 = fmadd(lit<V>(-3.0f), q, drs);
+    e7 = mul(fmadd(k.njxy0, drs, mul(k.rho0, ax - ay)), inv);
+    // jx* jy* - jx0 jy0 = djx (jy0 + djy) + jx0 djy
+    e8 = mul(fmadd(k.npxy0, drs, mul(k.rho0, fmadd(djx, k.jy0 + djy, mul(k.jx0, djy)))), inv);
 }
 
 // g = M^T a for a = D^-1 m^+ (the post-collision moments already scaled).
-template <typename CT>
-__device__ __forceinline__ void back9_scaled(const CT (&a)[9], CT (&g)[9]) {
-    const CT a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3], a4 = a[4];
-    const CT a5 = a[5], a6 = a[6], a7 = a[7], a8 = a[8];
-    const CT e1 = a0 - a3 - CT(2) * a4;  // shared by the axis populations
-    const CT e5 = a0 + CT(2) * a3 + a4;  // shared by the diagonal populations
-    const CT x1 = a1 - CT(2) * a5, y1 = a2 - CT(2) * a6;
-    const CT x5 = a1 + a5, y5 = a2 + a6;
-    g[0] = a0 - CT(4) * a3 + CT(4) * a4;
-    g[1] = e1 + x1 + a7;
-    g[2] = e1 + y1 - a7;
-    g[3] = e1 - x1 + a7;
-    g[4] = e1 - y1 - a7;
-    g[5] = e5 + x5 + y5 + a8;
-    g[6] = e5 - x5 + y5 - a8;
-    g[7] = e5 - x5 - y5 + a8;
-    g[8] = e5 + x5 - y5 - a8;
+template <typename V>
+__device__ __forceinline__ void back9_scaled(const V (&a)[9], V (&g)[9]) {
+    const V e1 = fmadd(lit<V>(-2.0f), a[4], a[0] - a[3]);  // shared by the axis populations
+    const V e5 = fmadd(lit<V>(2.0f), a[3], a[0] + a[4]);   // shared by the diagonal populations
+    const V x1 = fmadd(lit<V>(-2.0f), a[5], a[1]), y1 = fmadd(lit<V>(-2.0f), a[6], a[2]);
+    const V x5 = a[1] + a[5], y5 = a[2] + a[6];
+    g[0] = fmadd(lit<V>(4.0f), a[4] - a[3], a[0]);
+    const V ep = e1 + a[7], em = e1 - a[7];
+    g[1] = ep + x1;
+    g[3] = ep - x1;
+    g[2] = em + y1;
+    g[4] = em - y1;
+    const V up = e5 + a[8], um = e5 - a[8];
+    const V xpy = x5 + y5, xmy = x5 - y5;
+    g[5] = up + xpy;
+    g[7] = up - xpy;
+    g[6] = um - xmy;
+    g[8] = um + xmy;
 }
 
 // Collision where chi = 0: rho* = rho, j* = j, no damping term.  The
 // conserved rows are unchanged; the other six relax toward m^eq(rho, j):
-// D^-1 m_k^+ = ((1 - s_k)/D_k) m_k + (s_k/D_k) m_k^eq.
-template <typename CT>
-__device__ __forceinline__ void collide_bulk(CT (&g)[9], const StepConst<CT>& k) {
-    CT m[9];
+// a_k = keep_k m_k + take_k E_k (see StepConst).
+template <typename V>
+__device__ __forceinline__ void collide_bulk(V (&g)[9], const StepConst<V>& k) {
+    V m[9];
     moments9(g, m);
-    CT e3, e4, e7, e8;
+    V e3, e4, e7, e8;
     quad_eq(m[0], m[1], m[2], k, e3, e4, e7, e8);
-    CT a[9];
-    a[0] = m[0] * k.dinv[0];
-    a[1] = m[1] * k.dinv[1];
-    a[2] = m[2] * k.dinv[2];
-    a[3] = k.keep[3] * m[3] + k.take[3] * e3;
-    a[4] = k.keep[4] * m[4] + k.take[4] * e4;
-    a[5] = k.keep[5] * m[5] - k.take[5] * m[1];
-    a[6] = k.keep[6] * m[6] - k.take[6] * m[2];
-    a[7] = k.keep[7] * m[7] + k.take[7] * e7;
-    a[8] = k.keep[8] * m[8] + k.take[8] * e8;
+    V a[9];
+    a[0] = mul(m[0], k.dinv[0]);
+    a[1] = mul(m[1], k.dinv[1]);
+    a[2] = mul(m[2], k.dinv[2]);
+    a[3] = fmadd(k.keep[3], m[3], mul(k.take[3], e3));
+    a[4] = fmadd(k.keep[4], m[4], mul(k.take[4], e4));
+    a[5] = fmadd(k.keep[5], m[5], mul(k.take[5], m[1]));
+    a[6] = fmadd(k.keep[6], m[6], mul(k.take[6], m[2]));
+    a[7] = fmadd(k.keep[7], m[7], mul(k.take[7], e7));
+    a[8] = fmadd(k.keep[8], m[8], mul(k.take[8], e8));
     back9_scaled(a, g);
 }
 
 // The comparison sponge of Sec. 4.1 ("viscosity absorbing"): no damping term,
 // and in the layer every non-conserved rate falls linearly toward 1,
 // s_k' = s_k + (1 - s_k) r, with r in [0, 1] the layer fraction of the cell.
-template <typename CT>
-__device__ __forceinline__ void collide_viscous(CT (&g)[9], CT r, const StepConst<CT>& k) {
-    CT m[9];
+template <typename V>
+__device__ __forceinline__ void collide_viscous(V (&g)[9], V r, const StepConst<V>& k) {
+    V m[9];
     moments9(g, m);
-    CT e3, e4, e7, e8;
+    V e3, e4, e7, e8;
     quad_eq(m[0], m[1], m[2], k, e3, e4, e7, e8);
-    CT sk[9];
+    V sk[9];
 #pragma unroll
-    for (int i = 3; i < 9; ++i) sk[i] = k.s[i] + (CT(1) - k.s[i]) * r;
-    CT a[9];
-    a[0] = m[0] * k.dinv[0];
-    a[1] = m[1] * k.dinv[1];
-    a[2] = m[2] * k.dinv[2];
-    a[3] = (m[3] + sk[3] * (e3 - m[3])) * k.dinv[3];
-    a[4] = (m[4] + sk[4] * (e4 - m[4])) * k.dinv[4];
-    a[5] = (m[5] + sk[5] * (-m[1] - m[5])) * k.dinv[5];
-    a[6] = (m[6] + sk[6] * (-m[2] - m[6])) * k.dinv[6];
-    a[7] = (m[7] + sk[7] * (e7 - m[7])) * k.dinv[7];
-    a[8] = (m[8] + sk[8] * (e8 - m[8])) * k.dinv[8];
+    for (int i = 3; i < 9; ++i) sk[i] = fmadd(k.oms[i], r, k.s[i]);
+    // m_k^+ = m_k + s_k' (m_k^eq - m_k); rows 5, 6: m^eq = -j
+    V a[9];
+    a[0] = mul(m[0], k.dinv[0]);
+    a[1] = mul(m[1], k.dinv[1]);
+    a[2] = mul(m[2], k.dinv[2]);
+    a[3] = mul(fmadd(sk[3], e3 - m[3], m[3]), k.dinv[3]);
+    a[4] = mul(fmadd(sk[4], e4 - m[4], m[4]), k.dinv[4]);
+    a[5] = mul(m[5] - mul(sk[5], m[1] + m[5]), k.dinv[5]);
+    a[6] = mul(m[6] - mul(sk[6], m[2] + m[6]), k.dinv[6]);
+    a[7] = mul(fmadd(sk[7], e7 - m[7], m[7]), k.dinv[7]);
+    a[8] = mul(fmadd(sk[8], e8 - m[8], m[8]), k.dinv[8]);
     back9_scaled(a, g);
 }
 
 // Collision with an absorbing strength chi > 0 and its Guo factors rn, rm.
-template <typename CT, int VAR>
-__device__ __forceinline__ void collide_layer(CT (&g)[9], CT chi, CT rn, CT rm,
-                                              const StepConst<CT>& k) {
-    CT m[9];
+template <typename V, int VAR>
+__device__ __forceinline__ void collide_layer(V (&g)[9], V chi, V rn, V rm,
+                                              const StepConst<V>& k) {
+    V m[9];
     moments9(g, m);
     // rho*, j*: the Guo definitions solved exactly (sum F = chi (rho_f - rho*),
     // sum c F = chi (j_f - j*)), as deviations from the base state.
-    const CT drs = (m[0] + k.n * chi * k.drf) * rn;
-    const CT djxs = (m[1] + k.m * chi * k.djfx) * rm;
-    const CT djys = (m[2] + k.m * chi * k.djfy) * rm;
-    CT meq[9];
-    meq[0] = drs;
-    meq[1] = djxs;
-    meq[2] = djys;
-    quad_eq(drs, djxs, djys, k, meq[3], meq[4], meq[7], meq[8]);
-    meq[5] = -djxs;
-    meq[6] = -djys;
+    const V drs = mul(fmadd(chi, k.ndrf, m[0]), rn);
+    const V djxs = mul(fmadd(chi, k.mdjfx, m[1]), rm);
+    const V djys = mul(fmadd(chi, k.mdjfy, m[2]), rm);
+    V E[9];  // equilibrium sources (rows 5, 6: j*, the sign is in take)
+    E[0] = drs;
+    E[1] = djxs;
+    E[2] = djys;
+    quad_eq(drs, djxs, djys, k, E[3], E[4], E[7], E[8]);
+    E[5] = djxs;
+    E[6] = djys;
 
-    CT t[9];
-    if (VAR == kTypeI) {
+    // T_k of the damping term, times chi
+    V ct[9];
+    if (VAR == kTypeI) {  // m^eq(q_ref) - m
 #pragma unroll
-        for (int i = 0; i < 9; ++i) t[i] = k.dmeq_ref[i] - m[i];
-    } else if (VAR == kTypeII) {
+        for (int i = 0; i < 9; ++i) ct[i] = mul(chi, k.dmeq_ref[i] - m[i]);
+    } else if (VAR == kTypeII) {  // m^eq(q_ref) - m^eq(rho*, j*)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) t[i] = k.dmeq_ref[i] - meq[i];
+        for (int i = 0; i < 9; ++i)
+            ct[i] = mul(chi, (i == 5 || i == 6) ? k.dmeq_ref[i] + E[i] : k.dmeq_ref[i] - E[i]);
     } else {  // type III: linear equilibria (rho, j, -2 rho, rho, -j, 0, 0)
-        const CT dr = k.drf - drs, dx = k.djfx - djxs, dy = k.djfy - djys;
-        t[0] = dr;
-        t[1] = dx;
-        t[2] = dy;
-        t[3] = CT(-2) * dr;
-        t[4] = dr;
-        t[5] = -dx;
-        t[6] = -dy;
-        t[7] = CT(0);
-        t[8] = CT(0);
+        const V dr = mul(chi, k.drf - drs), dx = mul(chi, k.djfx - djxs), dy = mul(chi, k.djfy - djys);
+        const V ndx = mul(chi, djxs - k.djfx), ndy = mul(chi, djys - k.djfy);
+        ct[0] = dr;
+        ct[1] = dx;
+        ct[2] = dy;
+        ct[3] = mul(lit<V>(-2.0f), dr);
+        ct[4] = dr;
+        ct[5] = ndx;
+        ct[6] = ndy;
     }
-    // D^-1 m_k^+ = ((1 - s_k)/D_k) m_k + (s_k/D_k) m_k^eq + chi T_k / D_k
-    CT a[9];
+    V a[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) a[i] = k.keep[i] * m[i] + k.take[i] * meq[i] + (chi * k.dinv[i]) * t[i];
+    for (int i = 0; i < 9; ++i) {
+        if (VAR == kTypeIII && i >= 7)
+            a[i] = fmadd(k.keep[i], m[i], mul(k.take[i], E[i]));
+        else
+            a[i] = fmadd(k.keep[i], m[i], fmadd(k.take[i], E[i], mul(k.dinv[i], ct[i])));
+    }
     back9_scaled(a, g);
 }
 

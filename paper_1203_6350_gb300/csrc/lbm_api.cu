@@ -39,6 +39,8 @@ struct lbm_ctx {
     int bulk[4] = {0, 0, 0, 0};  // rectangle [x0, x1) x [y0, y1) where chi = 0
     StepConst<double> k64{};
     StepConst<float> k32{};
+    StepConst<lbm::F2> k2{};          // the FP32 constants, duplicated for the pair kernel
+    int cpt = 1;                      // cells per thread of the step kernel: 1, or 2 (FP32 / 16-bit)
     bool initialised = false;
     int64_t time = 0;
     int launch_mode = 2;              // kLaunchGraph; LBM_LAUNCH=plain|pdl|graph overrides
@@ -101,51 +103,16 @@ struct DeviceGuard {
     }
 };
 
-// Moment equilibria m^eq(rho, j) of the second-order D2Q9 equilibrium, in the
-// row order of M (App. A.1).
-void meq(double rho, double jx, double jy, double out[9]) {
-    const double q = (jx * jx + jy * jy) / rho;
-    out[0] = rho;
-    out[1] = jx;
-    out[2] = jy;
-    out[3] = -2.0 * rho + 3.0 * q;
-    out[4] = rho - 3.0 * q;
-    out[5] = -jx;
-    out[6] = -jy;
-    out[7] = (jx * jx - jy * jy) / rho;
-    out[8] = jx * jy / rho;
-}
-
 template <typename CT>
 void fill_const(const lbm_ctx* h, StepConst<CT>& k) {
-    for (int i = 0; i < 9; ++i) k.s[i] = static_cast<CT>(h->rates.s[i]);
-    k.n = static_cast<CT>(h->rates.n);
-    k.m = static_cast<CT>(h->rates.m);
-    const double jx0 = h->rho0 * h->ux0, jy0 = h->rho0 * h->uy0;
-    k.rho0 = static_cast<CT>(h->rho0);
-    k.jx0 = static_cast<CT>(jx0);
-    k.jy0 = static_cast<CT>(jy0);
-    k.jj0 = static_cast<CT>(jx0 * jx0 + jy0 * jy0);
-    k.jxy0 = static_cast<CT>(jx0 * jx0 - jy0 * jy0);
-    k.pxy0 = static_cast<CT>(jx0 * jy0);
-    const double jfx = h->rho_f * h->ux_f, jfy = h->rho_f * h->uy_f;
-    k.drf = static_cast<CT>(h->rho_f - h->rho0);
-    k.djfx = static_cast<CT>(jfx - jx0);
-    k.djfy = static_cast<CT>(jfy - jy0);
-    double mr[9], mb[9];
-    meq(h->rho_f, jfx, jfy, mr);
-    meq(h->rho0, jx0, jy0, mb);
-    for (int i = 0; i < 9; ++i) k.dmeq_ref[i] = static_cast<CT>(mr[i] - mb[i]);
-    lbm::fill_relax(k, h->rates.s);
-    k.bulk_x0 = h->bulk[0];
-    k.bulk_x1 = h->bulk[1];
-    k.bulk_y0 = h->bulk[2];
-    k.bulk_y1 = h->bulk[3];
+    k = lbm::make_step_const<CT>(h->rates.s, h->rates.n, h->rates.m, h->rho0, h->ux0, h->uy0,
+                                 h->rho_f, h->ux_f, h->uy_f, h->bulk);
 }
 
 void refresh_consts(lbm_ctx* h) {
     fill_const<double>(h, h->k64);
     fill_const<float>(h, h->k32);
+    fill_const<lbm::F2>(h, h->k2);
 }
 
 int ensure_staging(lbm_ctx* h) {
@@ -158,12 +125,28 @@ int ensure_staging(lbm_ctx* h) {
     return LBM_OK;
 }
 
+// The pair kernel steps FP32 and 16-bit storage and addresses the nine
+// planes with 32-bit element offsets.
+bool pair_kernel_ok(const lbm_ctx* h) {
+    return h->storage != LBM_F64 && 9 * h->geo.plane < (1ll << 32);
+}
+
 lbm::BaseState base_of(const lbm_ctx* h) { return lbm::BaseState{h->rho0, h->ux0, h->uy0}; }
 
 bool is_finite(double v) { return std::isfinite(v); }
 
 cudaError_t launch_one_step(lbm_ctx* h, const void* src, void* dst, cudaStream_t st, bool pdl) {
     const int p = pdl ? 1 : 0;
+    const auto* tx = static_cast<const lbm::AxisCoef<float>*>(h->chi_x);
+    const auto* ty = static_cast<const lbm::AxisCoef<float>*>(h->chi_y);
+    if (h->cpt == 2) {
+        switch (h->storage) {
+            case LBM_F32: return lbm::launch_step2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
+            case LBM_F16DEV: return lbm::launch_step2_f16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
+            case LBM_BF16DEV: return lbm::launch_step2_bf16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
+            default: break;
+        }
+    }
     switch (h->storage) {
         case LBM_F64:
             return lbm::launch_step_f64(src, dst, h->geo, h->k64, static_cast<const lbm::AxisCoef<double>*>(h->chi_x),
@@ -300,6 +283,10 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
         return cuda_fail(nullptr, e, "initial clear");
     }
     refresh_consts(h);
+    h->cpt = pair_kernel_ok(h) ? 2 : 1;
+    if (const char* c = std::getenv("LBM_CPT")) {
+        if (!std::strcmp(c, "1")) h->cpt = 1;
+    }
     if (const char* m = std::getenv("LBM_LAUNCH")) {
         if (!std::strcmp(m, "plain")) h->launch_mode = kLaunchPlain;
         else if (!std::strcmp(m, "pdl")) h->launch_mode = kLaunchPdl;
@@ -537,6 +524,22 @@ int lbm_set_launch_mode(lbm_handle h, int mode) {
     h->launch_mode = mode;
     return LBM_OK;
 }
+
+int lbm_set_cells_per_thread(lbm_handle h, int cells) {
+    if (!h) return LBM_ERR_ARG;
+    if (cells != 1 && cells != 2) return fail(h, LBM_ERR_ARG, "cells per thread must be 1 or 2");
+    if (cells == 2 && !pair_kernel_ok(h))
+        return fail(h, LBM_ERR_ARG, "two cells per thread needs FP32 or 16-bit storage and 9 planes below 2^32 elements");
+    if (cells != h->cpt) {
+        DeviceGuard dg(h->device);
+        cudaStreamSynchronize(h->stream);
+        drop_graphs(h);  // the captured launches name the other kernel
+        h->cpt = cells;
+    }
+    return LBM_OK;
+}
+
+int lbm_cells_per_thread(lbm_handle h) { return h ? h->cpt : LBM_ERR_ARG; }
 
 int lbm_set_stream(lbm_handle h, void* cuda_stream) {
     if (!h) return LBM_ERR_ARG;

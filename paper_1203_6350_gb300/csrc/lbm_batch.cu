@@ -41,9 +41,9 @@ struct BatchTile {
 };
 
 // Blocks of 256 threads per SM the register allocation must allow (0 leaves
-// it to the compiler): FP32 fits 40 registers without spilling (6 blocks),
-// FP64 80 (3 blocks); the 16-bit formats were fastest with the compiler's own
-// choice (48 registers).
+// it to the compiler): FP32 is fastest at 40 registers (6 blocks, a few bytes
+// of spill) -- measured ahead of 48 and of the compiler's own 52 -- FP64 at 80
+// (3 blocks); the 16-bit formats with the compiler's own choice.
 template <typename T>
 struct BatchMinBlocks {
     static constexpr int value = 0;
@@ -57,9 +57,14 @@ struct BatchMinBlocks<double> {
     static constexpr int value = 3;
 };
 
-// One time step of every active instance.  Block b walks the tiles b, b + G,
-// ...; the tile's instance descriptor is copied to shared memory, then the
-// block covers the tile_x x tile_y cells with blockDim = (tile_x, 256/tile_x).
+// One time step of every active instance.  Block b of G walks the tiles b,
+// b + G, ..., so that at any moment the G blocks sweep one compact stretch of
+// the tile table (a contiguous run per block spreads the DRAM accesses and
+// measured 27 % slower).  The tile table lists each instance's tiles
+// together: a block copies an instance descriptor to shared memory only when
+// its next tile belongs to another instance, and it fetches the next tile
+// entry while it processes the current tile.  The block covers a
+// tile_x x tile_y tile with blockDim = (tile_x, 256/tile_x).
 template <typename T>
 __global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
     batch_step_kernel(const BatchInst<typename Codec<T>::CT>* __restrict__ insts,
@@ -77,13 +82,20 @@ __global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
     const int ntiles = *ntiles_p;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const BatchTile tile = tiles[t];
-        __syncthreads();  // everyone is done with the previous descriptor
-        const unsigned* srcw = reinterpret_cast<const unsigned*>(insts + tile.inst);
-        unsigned* dstw = reinterpret_cast<unsigned*>(raw);
-        for (int w = tid; w < kWords; w += nthr) dstw[w] = __ldg(srcw + w);
-        __syncthreads();
+    const int G = gridDim.x;
+    int held = -1;  // instance whose descriptor is in shared memory
+    BatchTile next = (int)blockIdx.x < ntiles ? tiles[blockIdx.x] : BatchTile{};
+    for (int t = blockIdx.x; t < ntiles; t += G) {
+        const BatchTile tile = next;
+        if (t + G < ntiles) next = tiles[t + G];
+        if (tile.inst != held) {  // block-uniform
+            __syncthreads();      // everyone is done with the previous descriptor
+            const unsigned* srcw = reinterpret_cast<const unsigned*>(insts + tile.inst);
+            unsigned* dstw = reinterpret_cast<unsigned*>(raw);
+            for (int w = tid; w < kWords; w += nthr) dstw[w] = __ldg(srcw + w);
+            __syncthreads();
+            held = tile.inst;
+        }
         if (step < sd.start || step >= sd.end) continue;  // block-uniform
         const int parity = (int)((step - sd.start) & 1);
         const T* src = static_cast<const T*>(sd.buf[parity]);
@@ -252,46 +264,10 @@ Geometry geometry_of(int nx, int ny, int storage) {
     return Geometry{nx, ny, per_row, per_row * ny};
 }
 
-void moment_eq(double rho, double jx, double jy, double out[9]) {
-    const double q = (jx * jx + jy * jy) / rho;
-    out[0] = rho;
-    out[1] = jx;
-    out[2] = jy;
-    out[3] = -2.0 * rho + 3.0 * q;
-    out[4] = rho - 3.0 * q;
-    out[5] = -jx;
-    out[6] = -jy;
-    out[7] = (jx * jx - jy * jy) / rho;
-    out[8] = jx * jy / rho;
-}
-
 template <typename CT>
 StepConst<CT> consts_of(const Instance& in) {
-    StepConst<CT> k{};
-    for (int i = 0; i < 9; ++i) k.s[i] = static_cast<CT>(in.rates.s[i]);
-    k.n = static_cast<CT>(in.rates.n);
-    k.m = static_cast<CT>(in.rates.m);
-    const double jx0 = in.rho0 * in.ux0, jy0 = in.rho0 * in.uy0;
-    k.rho0 = static_cast<CT>(in.rho0);
-    k.jx0 = static_cast<CT>(jx0);
-    k.jy0 = static_cast<CT>(jy0);
-    k.jj0 = static_cast<CT>(jx0 * jx0 + jy0 * jy0);
-    k.jxy0 = static_cast<CT>(jx0 * jx0 - jy0 * jy0);
-    k.pxy0 = static_cast<CT>(jx0 * jy0);
-    const double jfx = in.rho_f * in.ux_f, jfy = in.rho_f * in.uy_f;
-    k.drf = static_cast<CT>(in.rho_f - in.rho0);
-    k.djfx = static_cast<CT>(jfx - jx0);
-    k.djfy = static_cast<CT>(jfy - jy0);
-    double mr[9], mb[9];
-    moment_eq(in.rho_f, jfx, jfy, mr);
-    moment_eq(in.rho0, jx0, jy0, mb);
-    for (int i = 0; i < 9; ++i) k.dmeq_ref[i] = static_cast<CT>(mr[i] - mb[i]);
-    lbm::fill_relax(k, in.rates.s);
-    k.bulk_x0 = in.bulk[0];
-    k.bulk_x1 = in.bulk[1];
-    k.bulk_y0 = in.bulk[2];
-    k.bulk_y1 = in.bulk[3];
-    return k;
+    return lbm::make_step_const<CT>(in.rates.s, in.rates.n, in.rates.m, in.rho0, in.ux0, in.uy0,
+                                    in.rho_f, in.ux_f, in.uy_f, in.bulk);
 }
 
 template <typename CT>

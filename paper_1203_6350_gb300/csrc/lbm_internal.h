@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -17,22 +18,52 @@ struct Geometry {
     long long plane;  // elements per plane = ny * pitch
 };
 
-// Per-lattice constants of the step, in the compute precision CT (double for
-// FP64 storage, float otherwise).  All "d" quantities are deviations from the
-// far-field (base) state rho0, j0 = rho0 u0.
+// Two FP32 values packed in one 64-bit register: the populations of two
+// neighbouring cells (x, x + 1) stepped together with the packed FP32
+// instructions of sm_100-class GPUs (lo = cell x, hi = cell x + 1).
+struct alignas(8) F2 {
+    unsigned long long u;
+};
+
+// Host-side conversion of an FP64 constant to the compute type.
+template <typename CT>
+inline CT to_ct(double v) {
+    return static_cast<CT>(v);
+}
+template <>
+inline F2 to_ct<F2>(double v) {
+    const float f = static_cast<float>(v);
+    unsigned w;
+    std::memcpy(&w, &f, sizeof w);
+    return F2{(static_cast<unsigned long long>(w) << 32) | w};
+}
+
+// Per-lattice constants of the step, in the compute type CT (double for FP64
+// storage, float otherwise, F2 -- every constant duplicated -- for the kernel
+// that steps two cells per thread).  All "d" quantities are deviations from
+// the far-field (base) state rho0, j0 = rho0 u0.
+//
+// The relaxation of row k is written on the scaled moment a_k = m_k^+ / D_k
+// that the back-transform M^T consumes (D = diag(9, 6, 6, 36, 36, 12, 12, 4, 4)):
+//   a_k = keep_k m_k + take_k E_k + dinv_k chi T_k,
+// with E_k the equilibrium source of the row: m_k^eq itself, except rows 5
+// and 6 whose equilibrium is -j_x, -j_y; there E_k = j and take_k carries the
+// minus sign.
 template <typename CT>
 struct StepConst {
     CT s[9];          // relaxation rates, row order of M
-    CT n, m;          // Guo weights
+    CT oms[9];        // 1 - s_k
+    CT keep[9];       // (1 - s_k) / D_k
+    CT take[9];       // s_k / D_k (negated for rows 5, 6)
+    CT dinv[9];       // 1 / D_k
     CT rho0, jx0, jy0;
-    CT jj0;           // |j0|^2
-    CT jxy0;          // jx0^2 - jy0^2
-    CT pxy0;          // jx0 * jy0
-    CT drf, djfx, djfy;  // reference state minus base: rho_f - rho0, j_f - j0
+    CT jx0_2, jy0_2;  // 2 j0
+    CT njj0;          // -|j0|^2
+    CT njxy0;         // -(jx0^2 - jy0^2)
+    CT npxy0;         // -jx0 jy0
+    CT drf, djfx, djfy;   // reference state minus base: rho_f - rho0, j_f - j0
+    CT ndrf, mdjfx, mdjfy;  // Guo source numerators n drf, m djfx, m djfy
     CT dmeq_ref[9];   // m^eq(rho_f, j_f) - m^eq(rho0, j0), evaluated in FP64 on the host
-    CT keep[9];       // (1 - s_k) / D_k: relaxation with the D^-1 of the back-transform folded in
-    CT take[9];       // s_k / D_k
-    CT dinv[9];       // 1 / D_k, D = diag(9, 6, 6, 36, 36, 12, 12, 4, 4)
     int bulk_x0, bulk_x1, bulk_y0, bulk_y1;  // chi = 0 for bulk_x0 <= x < bulk_x1 and bulk_y0 <= y < bulk_y1
 };
 
@@ -45,15 +76,63 @@ struct alignas(4 * sizeof(CT)) AxisCoef {
     CT chi, rn, rm, pad;
 };
 
-// Host-side: the relaxation constants of StepConst for the nine rates s.
+// Moment equilibria m^eq(rho, j) of the second-order D2Q9 equilibrium, in the
+// row order of M (App. A.1), in FP64.
+inline void moment_eq(double rho, double jx, double jy, double out[9]) {
+    const double q = (jx * jx + jy * jy) / rho;
+    out[0] = rho;
+    out[1] = jx;
+    out[2] = jy;
+    out[3] = -2.0 * rho + 3.0 * q;
+    out[4] = rho - 3.0 * q;
+    out[5] = -jx;
+    out[6] = -jy;
+    out[7] = (jx * jx - jy * jy) / rho;
+    out[8] = jx * jy / rho;
+}
+
+// Host-side: every constant of the step for rates s, Guo weights n, m, base
+// state (rho0, u0), reference state (rho_f, u_f) and the chi = 0 rectangle
+// bulk = {x0, x1, y0, y1}.  Computed in FP64, rounded once to CT.
 template <typename CT>
-inline void fill_relax(StepConst<CT>& k, const double* s) {
+inline StepConst<CT> make_step_const(const double* s, double n, double m, double rho0,
+                                     double ux0, double uy0, double rho_f, double ux_f,
+                                     double uy_f, const int* bulk) {
+    StepConst<CT> k{};
     const double D[9] = {9, 6, 6, 36, 36, 12, 12, 4, 4};
     for (int i = 0; i < 9; ++i) {
-        k.keep[i] = static_cast<CT>((1.0 - s[i]) / D[i]);
-        k.take[i] = static_cast<CT>(s[i] / D[i]);
-        k.dinv[i] = static_cast<CT>(1.0 / D[i]);
+        const double sign = (i == 5 || i == 6) ? -1.0 : 1.0;
+        k.s[i] = to_ct<CT>(s[i]);
+        k.oms[i] = to_ct<CT>(1.0 - s[i]);
+        k.keep[i] = to_ct<CT>((1.0 - s[i]) / D[i]);
+        k.take[i] = to_ct<CT>(sign * s[i] / D[i]);
+        k.dinv[i] = to_ct<CT>(1.0 / D[i]);
     }
+    const double jx0 = rho0 * ux0, jy0 = rho0 * uy0;
+    k.rho0 = to_ct<CT>(rho0);
+    k.jx0 = to_ct<CT>(jx0);
+    k.jy0 = to_ct<CT>(jy0);
+    k.jx0_2 = to_ct<CT>(2.0 * jx0);
+    k.jy0_2 = to_ct<CT>(2.0 * jy0);
+    k.njj0 = to_ct<CT>(-(jx0 * jx0 + jy0 * jy0));
+    k.njxy0 = to_ct<CT>(-(jx0 * jx0 - jy0 * jy0));
+    k.npxy0 = to_ct<CT>(-(jx0 * jy0));
+    const double jfx = rho_f * ux_f, jfy = rho_f * uy_f;
+    k.drf = to_ct<CT>(rho_f - rho0);
+    k.djfx = to_ct<CT>(jfx - jx0);
+    k.djfy = to_ct<CT>(jfy - jy0);
+    k.ndrf = to_ct<CT>(n * (rho_f - rho0));
+    k.mdjfx = to_ct<CT>(m * (jfx - jx0));
+    k.mdjfy = to_ct<CT>(m * (jfy - jy0));
+    double mr[9], mb[9];
+    moment_eq(rho_f, jfx, jfy, mr);
+    moment_eq(rho0, jx0, jy0, mb);
+    for (int i = 0; i < 9; ++i) k.dmeq_ref[i] = to_ct<CT>(mr[i] - mb[i]);
+    k.bulk_x0 = bulk[0];
+    k.bulk_x1 = bulk[1];
+    k.bulk_y0 = bulk[2];
+    k.bulk_y1 = bulk[3];
+    return k;
 }
 
 // Host-side: the longest run [lo, hi) of zeros in a[0..n) ([0, 0) if none).
@@ -97,6 +176,18 @@ cudaError_t launch_step_bf16(const void* src, void* dst, const Geometry& g,
                              const StepConst<float>& k, const AxisCoef<float>* tx,
                              const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
                             int pdl);
+
+// Two-cells-per-thread step launchers (FP32 and 16-bit storage; packed FP32
+// compute).  cudaErrorInvalidValue when 9 planes exceed 2^32 elements.
+cudaError_t launch_step2_f32(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
+                             const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
+                             int bc, cudaStream_t st, int pdl);
+cudaError_t launch_step2_f16(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
+                             const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
+                             int bc, cudaStream_t st, int pdl);
+cudaError_t launch_step2_bf16(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
+                              const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
+                              int bc, cudaStream_t st, int pdl);
 
 // Base-state parameters of the auxiliary kernels (always FP64).
 struct BaseState {

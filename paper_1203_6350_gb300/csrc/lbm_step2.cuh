@@ -1,0 +1,283 @@
+// Two-cells-per-thread step kernel.  Each thread steps the neighbouring cells
+// (x, x + 1), x even, of one row: the whole collision runs on packed FP32
+// pairs (one add/sub/mul/fma .f32x2 instruction per operation for both
+// cells), the three planes that do not move along x (i = 0, 2, 4) are pulled
+// with one 64-bit (FP32) or 32-bit (16-bit storage) load per pair, and all
+// nine planes are stored with one such access per pair.  The six planes that
+// move along x are pulled cell by cell (two 32- or 16-bit loads; a pair of
+// sources straddles the pair boundary).  Same scheme, same layout, same
+// boundary rules as the one-cell kernel.
+#pragma once
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+constexpr int kPairBX = 64;  // threads along x: 128 cells, two full warps
+constexpr int kPairBY = 4;   // rows per block
+
+// Storage of a pair of cells <-> F2.  Raw2 is the raw word of two adjacent
+// elements (lo = cell x).
+template <typename T>
+struct PairCodec;
+template <>
+struct PairCodec<float> {
+    using Raw2 = unsigned long long;
+    template <int I>
+    __device__ static __forceinline__ F2 dec2(Raw2 w) { return F2{w}; }
+    template <int I>
+    __device__ static __forceinline__ F2 dec11(float a, float b) { return f2(a, b); }
+    template <int I>
+    __device__ static __forceinline__ Raw2 enc2(F2 v) { return v.u; }
+    template <int I>
+    __device__ static __forceinline__ float enc_lo(F2 v) { return f2_lo(v); }
+};
+
+// 16-bit formats: q_i = g_i 2^e_i (see scale_exp); the scale is applied in
+// FP32 on the pair, the format conversion packs or unpacks both cells.
+template <typename H, typename H2>
+struct PairCodec16 {
+    using Raw2 = unsigned;
+    template <int I>
+    __device__ static __forceinline__ F2 dec2(Raw2 w) {
+        H2 h;
+        memcpy(&h, &w, sizeof w);
+        return mul(f2(to_f(h.x), to_f(h.y)), lit<F2>(pow2f(-scale_exp(I))));
+    }
+    template <int I>
+    __device__ static __forceinline__ F2 dec11(H a, H b) {
+        return mul(f2(to_f(a), to_f(b)), lit<F2>(pow2f(-scale_exp(I))));
+    }
+    template <int I>
+    __device__ static __forceinline__ Raw2 enc2(F2 v) {
+        const F2 s = mul(v, lit<F2>(pow2f(scale_exp(I))));
+        const H2 h = pack(f2_lo(s), f2_hi(s));
+        Raw2 w;
+        memcpy(&w, &h, sizeof w);
+        return w;
+    }
+    template <int I>
+    __device__ static __forceinline__ H enc_lo(F2 v) {
+        return Codec<H>::template enc<I>(f2_lo(v));
+    }
+    __device__ static __forceinline__ float to_f(__half h) { return __half2float(h); }
+    __device__ static __forceinline__ float to_f(__nv_bfloat16 h) { return __bfloat162float(h); }
+    __device__ static __forceinline__ __half2 pack_h(float lo, float hi, __half2*) {
+        return __floats2half2_rn(lo, hi);
+    }
+    __device__ static __forceinline__ __nv_bfloat162 pack_h(float lo, float hi, __nv_bfloat162*) {
+        return __floats2bfloat162_rn(lo, hi);
+    }
+    __device__ static __forceinline__ H2 pack(float lo, float hi) {
+        return pack_h(lo, hi, static_cast<H2*>(nullptr));
+    }
+};
+template <>
+struct PairCodec<__half> : PairCodec16<__half, __half2> {};
+template <>
+struct PairCodec<__nv_bfloat16> : PairCodec16<__nv_bfloat16, __nv_bfloat162> {};
+
+template <typename T>
+__device__ __forceinline__ typename PairCodec<T>::Raw2 ld_pair(const T* p) {
+    return __ldg(reinterpret_cast<const typename PairCodec<T>::Raw2*>(p));
+}
+
+// Pull the nine populations of the pair at element offset o (row y, x even),
+// all sources inside the lattice.  Element offsets are 32-bit unsigned:
+// valid while the nine planes hold fewer than 2^32 elements.
+template <typename T>
+__device__ __forceinline__ void pull_pair_interior(const T* __restrict__ s, unsigned plane,
+                                                   unsigned pitch, unsigned o, F2 (&v)[9]) {
+    using PC = PairCodec<T>;
+    const unsigned up = o - pitch, dn = o + pitch;  // rows y - 1, y + 1
+    v[0] = PC::template dec2<0>(ld_pair(s + o));
+    v[2] = PC::template dec2<2>(ld_pair(s + (2 * plane + up)));  // from (x, y - 1)
+    v[4] = PC::template dec2<4>(ld_pair(s + (4 * plane + dn)));  // from (x, y + 1)
+    const T* p1 = s + (plane + o);                                // from (x - 1, y)
+    v[1] = PC::template dec11<1>(__ldg(p1 - 1), __ldg(p1));
+    const T* p3 = s + (3 * plane + o);                            // from (x + 1, y)
+    v[3] = PC::template dec11<3>(__ldg(p3 + 1), __ldg(p3 + 2));
+    const T* p5 = s + (5 * plane + up);                           // from (x - 1, y - 1)
+    v[5] = PC::template dec11<5>(__ldg(p5 - 1), __ldg(p5));
+    const T* p6 = s + (6 * plane + up);                           // from (x + 1, y - 1)
+    v[6] = PC::template dec11<6>(__ldg(p6 + 1), __ldg(p6 + 2));
+    const T* p7 = s + (7 * plane + dn);                           // from (x + 1, y + 1)
+    v[7] = PC::template dec11<7>(__ldg(p7 + 1), __ldg(p7 + 2));
+    const T* p8 = s + (8 * plane + dn);                           // from (x - 1, y + 1)
+    v[8] = PC::template dec11<8>(__ldg(p8 - 1), __ldg(p8));
+}
+
+// Population I of cell (c, y) pulled from (c - c_ix, y - c_iy) with the
+// boundary rule: a Dirichlet far-field wall contributes a zero deviation,
+// periodic wraps.  The phantom cell c = nx of an odd-width lattice reads
+// nothing (its result is never stored).
+template <typename T, int BC, int I>
+__device__ __forceinline__ float pull_one(const T* __restrict__ s, unsigned plane, int pitch,
+                                          int c, int y, int nx, int ny) {
+    if (c >= nx) return 0.0f;
+    int sx = c - cx(I), sy = y - cy(I);
+    if (BC == kPeriodic) {
+        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+    } else if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
+        return 0.0f;
+    }
+    return Codec<T>::template dec<I>(__ldg(s + (I * plane + static_cast<unsigned>(sy * pitch + sx))));
+}
+
+template <typename T, int BC, int I>
+__device__ __forceinline__ F2 pull_pair_one(const T* __restrict__ s, unsigned plane, int pitch,
+                                            int x, int y, int nx, int ny) {
+    return f2(pull_one<T, BC, I>(s, plane, pitch, x, y, nx, ny),
+              pull_one<T, BC, I>(s, plane, pitch, x + 1, y, nx, ny));
+}
+
+template <typename T, int BC>
+__device__ __forceinline__ void pull_pair_edge(const T* __restrict__ s, unsigned plane, int pitch,
+                                               int x, int y, int nx, int ny, F2 (&v)[9]) {
+    v[0] = pull_pair_one<T, BC, 0>(s, plane, pitch, x, y, nx, ny);
+    v[1] = pull_pair_one<T, BC, 1>(s, plane, pitch, x, y, nx, ny);
+    v[2] = pull_pair_one<T, BC, 2>(s, plane, pitch, x, y, nx, ny);
+    v[3] = pull_pair_one<T, BC, 3>(s, plane, pitch, x, y, nx, ny);
+    v[4] = pull_pair_one<T, BC, 4>(s, plane, pitch, x, y, nx, ny);
+    v[5] = pull_pair_one<T, BC, 5>(s, plane, pitch, x, y, nx, ny);
+    v[6] = pull_pair_one<T, BC, 6>(s, plane, pitch, x, y, nx, ny);
+    v[7] = pull_pair_one<T, BC, 7>(s, plane, pitch, x, y, nx, ny);
+    v[8] = pull_pair_one<T, BC, 8>(s, plane, pitch, x, y, nx, ny);
+}
+
+template <typename T, int I>
+__device__ __forceinline__ void store_pair_plane(T* __restrict__ d, unsigned plane, unsigned o,
+                                                 const F2 (&v)[9]) {
+    *reinterpret_cast<typename PairCodec<T>::Raw2*>(d + (I * plane + o)) =
+        PairCodec<T>::template enc2<I>(v[I]);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(T* __restrict__ d, unsigned plane, unsigned o,
+                                           const F2 (&v)[9]) {
+    store_pair_plane<T, 0>(d, plane, o, v);
+    store_pair_plane<T, 1>(d, plane, o, v);
+    store_pair_plane<T, 2>(d, plane, o, v);
+    store_pair_plane<T, 3>(d, plane, o, v);
+    store_pair_plane<T, 4>(d, plane, o, v);
+    store_pair_plane<T, 5>(d, plane, o, v);
+    store_pair_plane<T, 6>(d, plane, o, v);
+    store_pair_plane<T, 7>(d, plane, o, v);
+    store_pair_plane<T, 8>(d, plane, o, v);
+}
+
+// Store only cell x of the pair (the last column of an odd-width lattice).
+template <typename T>
+__device__ __forceinline__ void store_lo(T* __restrict__ d, unsigned plane, unsigned o,
+                                         const F2 (&v)[9]) {
+    d[o] = PairCodec<T>::template enc_lo<0>(v[0]);
+    d[plane + o] = PairCodec<T>::template enc_lo<1>(v[1]);
+    d[2 * plane + o] = PairCodec<T>::template enc_lo<2>(v[2]);
+    d[3 * plane + o] = PairCodec<T>::template enc_lo<3>(v[3]);
+    d[4 * plane + o] = PairCodec<T>::template enc_lo<4>(v[4]);
+    d[5 * plane + o] = PairCodec<T>::template enc_lo<5>(v[5]);
+    d[6 * plane + o] = PairCodec<T>::template enc_lo<6>(v[6]);
+    d[7 * plane + o] = PairCodec<T>::template enc_lo<7>(v[7]);
+    d[8 * plane + o] = PairCodec<T>::template enc_lo<8>(v[8]);
+}
+
+// Collide the pair (x, x + 1) of row y.  Both cells take the damping path as
+// soon as one of them lies in the layer; with chi = 0 that path reduces to
+// the plain relaxation.
+template <int VAR>
+__device__ __forceinline__ void collide_pair(F2 (&v)[9], int x, int y, int nx,
+                                             const StepConst<F2>& k,
+                                             const AxisCoef<float>* __restrict__ tx,
+                                             const AxisCoef<float>* __restrict__ ty) {
+    if (VAR == kNone ||
+        (x >= k.bulk_x0 && x + 1 < k.bulk_x1 && y >= k.bulk_y0 && y < k.bulk_y1)) {
+        collide_bulk(v, k);
+        return;
+    }
+    // the phantom cell of an odd-width lattice reuses its neighbour's coefficients
+    const AxisCoef<float> a0 = load_coef(tx, x), a1 = load_coef(tx, min(x + 1, nx - 1));
+    const AxisCoef<float> ay = load_coef(ty, y);
+    const float c0 = fmaxf(a0.chi, ay.chi), c1 = fmaxf(a1.chi, ay.chi);
+    if (c0 > 0.0f || c1 > 0.0f) {
+        if (VAR == kViscous)  // the tables' chi slot holds the layer fraction r
+            collide_viscous(v, f2(c0, c1), k);
+        else
+            collide_layer<F2, VAR>(v, f2(c0, c1), f2(fminf(a0.rn, ay.rn), fminf(a1.rn, ay.rn)),
+                                   f2(fminf(a0.rm, ay.rm), fminf(a1.rm, ay.rm)), k);
+    } else {
+        collide_bulk(v, k);
+    }
+}
+
+template <typename T, int VAR, int BC>
+__global__ void __launch_bounds__(kPairBX* kPairBY)
+    step2_kernel(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
+                 unsigned plane, StepConst<F2> k, const AxisCoef<float>* __restrict__ tx,
+                 const AxisCoef<float>* __restrict__ ty) {
+    const int x = 2 * (blockIdx.x * kPairBX + threadIdx.x);
+    const int y = blockIdx.y * kPairBY + threadIdx.y;
+    // Launched as a programmatic dependent of the previous step: wait until that
+    // grid has completed and its stores are visible.  No-op otherwise.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (x >= nx || y >= ny) {
+        asm volatile("griddepcontrol.launch_dependents;");
+        return;
+    }
+    const unsigned o = static_cast<unsigned>(y * pitch + x);
+    // per thread: both cells and all their sources inside the lattice
+    const bool interior = x > 0 && x + 2 < nx && y > 0 && y + 1 < ny;
+    F2 v[9];
+    if (interior)
+        pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch), o, v);
+    else
+        pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v);
+    collide_pair<VAR>(v, x, y, nx, k, tx, ty);
+    if (x + 1 < nx)
+        store_pair<T>(dst, plane, o, v);
+    else
+        store_lo<T>(dst, plane, o, v);
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+// Launch one step of the pair kernel (storage float, __half or
+// __nv_bfloat16); pdl as for the one-cell kernel.  Returns
+// cudaErrorInvalidValue when the nine planes exceed 32-bit element offsets.
+template <typename T>
+cudaError_t launch_step2_t(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
+                           const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
+                           int bc, cudaStream_t st, int pdl) {
+    if (9 * g.plane >= (1ll << 32)) return cudaErrorInvalidValue;
+    const T* s = static_cast<const T*>(src);
+    T* d = static_cast<T*>(dst);
+    const int pitch = static_cast<int>(g.pitch);
+    const unsigned plane = static_cast<unsigned>(g.plane);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((g.nx + 2 * kPairBX - 1) / (2 * kPairBX), (g.ny + kPairBY - 1) / kPairBY);
+    cfg.blockDim = dim3(kPairBX, kPairBY);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+#define LBM_STEP2_CASE(V, B)                                                                  \
+    if (variant == V && bc == B)                                                              \
+        return cudaLaunchKernelEx(&cfg, step2_kernel<T, V, B>, s, d, g.nx, g.ny, pitch, plane, k, \
+                                  tx, ty);
+    LBM_STEP2_CASE(kNone, kDirichlet)
+    LBM_STEP2_CASE(kTypeI, kDirichlet)
+    LBM_STEP2_CASE(kTypeII, kDirichlet)
+    LBM_STEP2_CASE(kTypeIII, kDirichlet)
+    LBM_STEP2_CASE(kViscous, kDirichlet)
+    LBM_STEP2_CASE(kNone, kPeriodic)
+    LBM_STEP2_CASE(kTypeI, kPeriodic)
+    LBM_STEP2_CASE(kTypeII, kPeriodic)
+    LBM_STEP2_CASE(kTypeIII, kPeriodic)
+    LBM_STEP2_CASE(kViscous, kPeriodic)
+#undef LBM_STEP2_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

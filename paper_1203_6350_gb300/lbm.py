@@ -78,6 +78,8 @@ SIGNATURES = [
     ("lbm_time", _i64, [_vp]),
     ("lbm_set_stream", ctypes.c_int, [_vp, _vp]),
     ("lbm_set_launch_mode", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_set_cells_per_thread", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_cells_per_thread", ctypes.c_int, [_vp]),
     ("lbm_destroy", None, [_vp]),
     ("lbm_last_error", ctypes.c_char_p, [_vp]),
     ("lbm_version", ctypes.c_char_p, []),
@@ -217,6 +219,14 @@ LAUNCH_MODES = {"plain": 0, "pdl": 1, "graph": 2}
 
 def lbm_set_launch_mode(h, mode) -> int:
     return load().lbm_set_launch_mode(h, int(mode))
+
+
+def lbm_set_cells_per_thread(h, cells) -> int:
+    return load().lbm_set_cells_per_thread(h, int(cells))
+
+
+def lbm_cells_per_thread(h) -> int:
+    return load().lbm_cells_per_thread(h)
 
 
 def lbm_destroy(h) -> None:
@@ -459,6 +469,14 @@ class Lattice:
     @property
     def time(self) -> int:
         return lbm_time(self.h)
+
+    @property
+    def cells_per_thread(self) -> int:
+        return lbm_cells_per_thread(self.h)
+
+    @cells_per_thread.setter
+    def cells_per_thread(self, cells: int) -> None:
+        check(lbm_set_cells_per_thread(self.h, cells), self.h, "lbm_set_cells_per_thread")
 
     def close(self) -> None:
         if getattr(self, "h", None):

@@ -26,7 +26,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_CELL))
-    ap.add_argument("--variant", default="II", choices=["none", "I", "II", "III"])
+    ap.add_argument("--variant", default="II", choices=["none", "I", "II", "III", "viscous"])
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--width", type=int, default=128)
