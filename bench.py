@@ -390,7 +390,7 @@ def with_warn(fn):
 
 KERNEL_SOURCES = ("d2q9_cell.cuh", "lbm_step.cuh", "step_f32.cu", "lbm_step2.cuh", "step2_f32.cu",
                   "lbm_internal.h")
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_f32_meanflow_1024x1024_traffic.md")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step2_kernel_f32_meanflow_1024x1024_traffic.md")
 
 
 def kernel_source_hash() -> str:

@@ -41,6 +41,7 @@ struct lbm_ctx {
     StepConst<float> k32{};
     StepConst<lbm::F2> k2{};          // the FP32 constants, duplicated for the pair kernel
     int cpt = 1;                      // cells per thread of the step kernel: 1, or 2 (FP32 / 16-bit)
+    int spl = 1;                      // time steps per launch: 1, or 2 (needs cpt == 2)
     bool initialised = false;
     int64_t time = 0;
     int launch_mode = 2;              // kLaunchGraph; LBM_LAUNCH=plain|pdl|graph overrides
@@ -163,6 +164,19 @@ cudaError_t launch_one_step(lbm_ctx* h, const void* src, void* dst, cudaStream_t
     }
 }
 
+// Two steps src (time t) -> dst (time t + 2) in one launch.
+cudaError_t launch_two_steps(lbm_ctx* h, const void* src, void* dst, cudaStream_t st, bool pdl) {
+    const int p = pdl ? 1 : 0;
+    const auto* tx = static_cast<const lbm::AxisCoef<float>*>(h->chi_x);
+    const auto* ty = static_cast<const lbm::AxisCoef<float>*>(h->chi_y);
+    switch (h->storage) {
+        case LBM_F32: return lbm::launch_step_tb2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
+        case LBM_F16DEV: return lbm::launch_step_tb2_f16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
+        case LBM_BF16DEV: return lbm::launch_step_tb2_bf16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 void drop_graphs(lbm_ctx* h) {
     for (int i = 0; i < 2; ++i) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
@@ -183,8 +197,11 @@ cudaError_t ensure_graph(lbm_ctx* h, int parity) {
     e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     int c = parity;
-    for (int t = 0; t < kGraphChunk && e == cudaSuccess; ++t) {
-        e = launch_one_step(h, h->buf[c], h->buf[1 - c], h->capture_stream, t > 0);
+    for (int t = 0; t < kGraphChunk && e == cudaSuccess; t += h->spl) {
+        if (h->spl == 2)
+            e = launch_two_steps(h, h->buf[c], h->buf[1 - c], h->capture_stream, t > 0);
+        else
+            e = launch_one_step(h, h->buf[c], h->buf[1 - c], h->capture_stream, t > 0);
         c = 1 - c;
     }
     cudaGraph_t g = nullptr;
@@ -286,6 +303,10 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     h->cpt = pair_kernel_ok(h) ? 2 : 1;
     if (const char* c = std::getenv("LBM_CPT")) {
         if (!std::strcmp(c, "1")) h->cpt = 1;
+    }
+    if (const char* c = std::getenv("LBM_SPL")) {
+        if (!std::strcmp(c, "2") && h->cpt == 2) h->spl = 2;
+        if (!std::strcmp(c, "1")) h->spl = 1;
     }
     if (const char* m = std::getenv("LBM_LAUNCH")) {
         if (!std::strcmp(m, "plain")) h->launch_mode = kLaunchPlain;
@@ -430,16 +451,19 @@ int lbm_step(lbm_handle h, int nsteps) {
             while (nsteps >= kGraphChunk) {
                 e = cudaGraphLaunch(h->graph[h->cur], h->stream);
                 if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step graph launch");
-                h->time += kGraphChunk;  // an even chunk leaves cur unchanged
+                h->time += kGraphChunk;  // an even number of launches leaves cur unchanged
                 nsteps -= kGraphChunk;
             }
         }
     }
-    for (int t = 0; t < nsteps; ++t) {
-        e = launch_one_step(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl);
+    while (nsteps > 0) {
+        const int n = (h->spl == 2 && nsteps >= 2) ? 2 : 1;
+        e = n == 2 ? launch_two_steps(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl)
+                   : launch_one_step(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl);
         if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step launch");
         h->cur = 1 - h->cur;
-        ++h->time;
+        h->time += n;
+        nsteps -= n;
     }
     return LBM_OK;
 }
@@ -535,9 +559,26 @@ int lbm_set_cells_per_thread(lbm_handle h, int cells) {
         cudaStreamSynchronize(h->stream);
         drop_graphs(h);  // the captured launches name the other kernel
         h->cpt = cells;
+        if (cells == 1) h->spl = 1;
     }
     return LBM_OK;
 }
+
+int lbm_set_steps_per_launch(lbm_handle h, int steps) {
+    if (!h) return LBM_ERR_ARG;
+    if (steps != 1 && steps != 2) return fail(h, LBM_ERR_ARG, "steps per launch must be 1 or 2");
+    if (steps == 2 && h->cpt != 2)
+        return fail(h, LBM_ERR_ARG, "two steps per launch needs two cells per thread");
+    if (steps != h->spl) {
+        DeviceGuard dg(h->device);
+        cudaStreamSynchronize(h->stream);
+        drop_graphs(h);  // the captured launches name the other kernel
+        h->spl = steps;
+    }
+    return LBM_OK;
+}
+
+int lbm_steps_per_launch(lbm_handle h) { return h ? h->spl : LBM_ERR_ARG; }
 
 int lbm_cells_per_thread(lbm_handle h) { return h ? h->cpt : LBM_ERR_ARG; }
 

@@ -189,6 +189,21 @@ cudaError_t launch_step2_bf16(const void* src, void* dst, const Geometry& g, con
                               const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
                               int bc, cudaStream_t st, int pdl);
 
+// Two steps per launch (temporal blocking through shared memory) on the
+// two-cells-per-thread arithmetic: src holds time t, dst receives t + 2.
+cudaError_t launch_step_tb2_f32(const void* src, void* dst, const Geometry& g,
+                                const StepConst<F2>& k, const AxisCoef<float>* tx,
+                                const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
+                                int pdl);
+cudaError_t launch_step_tb2_f16(const void* src, void* dst, const Geometry& g,
+                                const StepConst<F2>& k, const AxisCoef<float>* tx,
+                                const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
+                                int pdl);
+cudaError_t launch_step_tb2_bf16(const void* src, void* dst, const Geometry& g,
+                                 const StepConst<F2>& k, const AxisCoef<float>* tx,
+                                 const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
+                                 int pdl);
+
 // Base-state parameters of the auxiliary kernels (always FP64).
 struct BaseState {
     double rho0, ux0, uy0;

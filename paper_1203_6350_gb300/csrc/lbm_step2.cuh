@@ -77,34 +77,44 @@ struct PairCodec<__half> : PairCodec16<__half, __half2> {};
 template <>
 struct PairCodec<__nv_bfloat16> : PairCodec16<__nv_bfloat16, __nv_bfloat162> {};
 
-template <typename T>
+// Loads of one element or one pair: through the read-only data path from
+// global memory (SHARED = false) or plain loads from shared memory.
+template <typename T, bool SHARED>
+__device__ __forceinline__ T ld_one(const T* p) {
+    if (SHARED) return *p;
+    return __ldg(p);
+}
+template <typename T, bool SHARED>
 __device__ __forceinline__ typename PairCodec<T>::Raw2 ld_pair(const T* p) {
-    return __ldg(reinterpret_cast<const typename PairCodec<T>::Raw2*>(p));
+    const auto* q = reinterpret_cast<const typename PairCodec<T>::Raw2*>(p);
+    if (SHARED) return *q;
+    return __ldg(q);
 }
 
-// Pull the nine populations of the pair at element offset o (row y, x even),
-// all sources inside the lattice.  Element offsets are 32-bit unsigned:
+// Pull the nine populations of the pair at element offset o (row y, x even)
+// of a store of 9 planes (`plane` elements apart) of rows `pitch` elements
+// long, all sources inside the store.  Element offsets are 32-bit unsigned:
 // valid while the nine planes hold fewer than 2^32 elements.
-template <typename T>
+template <typename T, bool SHARED = false>
 __device__ __forceinline__ void pull_pair_interior(const T* __restrict__ s, unsigned plane,
                                                    unsigned pitch, unsigned o, F2 (&v)[9]) {
     using PC = PairCodec<T>;
     const unsigned up = o - pitch, dn = o + pitch;  // rows y - 1, y + 1
-    v[0] = PC::template dec2<0>(ld_pair(s + o));
-    v[2] = PC::template dec2<2>(ld_pair(s + (2 * plane + up)));  // from (x, y - 1)
-    v[4] = PC::template dec2<4>(ld_pair(s + (4 * plane + dn)));  // from (x, y + 1)
-    const T* p1 = s + (plane + o);                                // from (x - 1, y)
-    v[1] = PC::template dec11<1>(__ldg(p1 - 1), __ldg(p1));
-    const T* p3 = s + (3 * plane + o);                            // from (x + 1, y)
-    v[3] = PC::template dec11<3>(__ldg(p3 + 1), __ldg(p3 + 2));
-    const T* p5 = s + (5 * plane + up);                           // from (x - 1, y - 1)
-    v[5] = PC::template dec11<5>(__ldg(p5 - 1), __ldg(p5));
-    const T* p6 = s + (6 * plane + up);                           // from (x + 1, y - 1)
-    v[6] = PC::template dec11<6>(__ldg(p6 + 1), __ldg(p6 + 2));
-    const T* p7 = s + (7 * plane + dn);                           // from (x + 1, y + 1)
-    v[7] = PC::template dec11<7>(__ldg(p7 + 1), __ldg(p7 + 2));
-    const T* p8 = s + (8 * plane + dn);                           // from (x - 1, y + 1)
-    v[8] = PC::template dec11<8>(__ldg(p8 - 1), __ldg(p8));
+    v[0] = PC::template dec2<0>(ld_pair<T, SHARED>(s + o));
+    v[2] = PC::template dec2<2>(ld_pair<T, SHARED>(s + (2 * plane + up)));  // from (x, y - 1)
+    v[4] = PC::template dec2<4>(ld_pair<T, SHARED>(s + (4 * plane + dn)));  // from (x, y + 1)
+    const T* p1 = s + (plane + o);                                           // from (x - 1, y)
+    v[1] = PC::template dec11<1>(ld_one<T, SHARED>(p1 - 1), ld_one<T, SHARED>(p1));
+    const T* p3 = s + (3 * plane + o);                                       // from (x + 1, y)
+    v[3] = PC::template dec11<3>(ld_one<T, SHARED>(p3 + 1), ld_one<T, SHARED>(p3 + 2));
+    const T* p5 = s + (5 * plane + up);                                      // from (x - 1, y - 1)
+    v[5] = PC::template dec11<5>(ld_one<T, SHARED>(p5 - 1), ld_one<T, SHARED>(p5));
+    const T* p6 = s + (6 * plane + up);                                      // from (x + 1, y - 1)
+    v[6] = PC::template dec11<6>(ld_one<T, SHARED>(p6 + 1), ld_one<T, SHARED>(p6 + 2));
+    const T* p7 = s + (7 * plane + dn);                                      // from (x + 1, y + 1)
+    v[7] = PC::template dec11<7>(ld_one<T, SHARED>(p7 + 1), ld_one<T, SHARED>(p7 + 2));
+    const T* p8 = s + (8 * plane + dn);                                      // from (x - 1, y + 1)
+    v[8] = PC::template dec11<8>(ld_one<T, SHARED>(p8 - 1), ld_one<T, SHARED>(p8));
 }
 
 // Population I of cell (c, y) pulled from (c - c_ix, y - c_iy) with the
@@ -182,21 +192,21 @@ __device__ __forceinline__ void store_lo(T* __restrict__ d, unsigned plane, unsi
     d[8 * plane + o] = PairCodec<T>::template enc_lo<8>(v[8]);
 }
 
-// Collide the pair (x, x + 1) of row y.  Both cells take the damping path as
-// soon as one of them lies in the layer; with chi = 0 that path reduces to
-// the plain relaxation.
+// Collide a pair of cells of row y at columns xa (lo lane) and xb (hi lane),
+// both inside the lattice.  Both cells take the damping path as soon as one
+// of them lies in the layer; with chi = 0 that path reduces to the plain
+// relaxation.
 template <int VAR>
-__device__ __forceinline__ void collide_pair(F2 (&v)[9], int x, int y, int nx,
-                                             const StepConst<F2>& k,
-                                             const AxisCoef<float>* __restrict__ tx,
-                                             const AxisCoef<float>* __restrict__ ty) {
-    if (VAR == kNone ||
-        (x >= k.bulk_x0 && x + 1 < k.bulk_x1 && y >= k.bulk_y0 && y < k.bulk_y1)) {
+__device__ __forceinline__ void collide_lanes(F2 (&v)[9], int xa, int xb, int y,
+                                              const StepConst<F2>& k,
+                                              const AxisCoef<float>* __restrict__ tx,
+                                              const AxisCoef<float>* __restrict__ ty) {
+    if (VAR == kNone || (xa >= k.bulk_x0 && xa < k.bulk_x1 && xb >= k.bulk_x0 &&
+                         xb < k.bulk_x1 && y >= k.bulk_y0 && y < k.bulk_y1)) {
         collide_bulk(v, k);
         return;
     }
-    // the phantom cell of an odd-width lattice reuses its neighbour's coefficients
-    const AxisCoef<float> a0 = load_coef(tx, x), a1 = load_coef(tx, min(x + 1, nx - 1));
+    const AxisCoef<float> a0 = load_coef(tx, xa), a1 = load_coef(tx, xb);
     const AxisCoef<float> ay = load_coef(ty, y);
     const float c0 = fmaxf(a0.chi, ay.chi), c1 = fmaxf(a1.chi, ay.chi);
     if (c0 > 0.0f || c1 > 0.0f) {
@@ -208,6 +218,16 @@ __device__ __forceinline__ void collide_pair(F2 (&v)[9], int x, int y, int nx,
     } else {
         collide_bulk(v, k);
     }
+}
+
+// The pair (x, x + 1) of row y; the phantom cell x + 1 = nx of an odd-width
+// lattice borrows the coefficients of its neighbour (its result is dropped).
+template <int VAR>
+__device__ __forceinline__ void collide_pair(F2 (&v)[9], int x, int y, int nx,
+                                             const StepConst<F2>& k,
+                                             const AxisCoef<float>* __restrict__ tx,
+                                             const AxisCoef<float>* __restrict__ ty) {
+    collide_lanes<VAR>(v, x, min(x + 1, nx - 1), y, k, tx, ty);
 }
 
 template <typename T, int VAR, int BC>

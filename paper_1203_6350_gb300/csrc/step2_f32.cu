@@ -1,5 +1,6 @@
-// Two-cells-per-thread step kernels for float population storage (packed FP32 compute).
-#include "lbm_step2.cuh"
+// Two-cells-per-thread step kernels for float population storage (packed FP32
+// compute): one step per launch, and two steps per launch (temporal blocking).
+#include "lbm_step_tb.cuh"
 
 namespace lbm {
 
@@ -7,6 +8,13 @@ cudaError_t launch_step2_f32(const void* src, void* dst, const Geometry& g, cons
                            const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
                            int bc, cudaStream_t st, int pdl) {
     return launch_step2_t<float>(src, dst, g, k, tx, ty, variant, bc, st, pdl);
+}
+
+cudaError_t launch_step_tb2_f32(const void* src, void* dst, const Geometry& g,
+                              const StepConst<F2>& k, const AxisCoef<float>* tx,
+                              const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
+                              int pdl) {
+    return launch_step_tb2_t<float>(src, dst, g, k, tx, ty, variant, bc, st, pdl);
 }
 
 }  // namespace lbm

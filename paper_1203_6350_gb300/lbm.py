@@ -80,6 +80,8 @@ SIGNATURES = [
     ("lbm_set_launch_mode", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_set_cells_per_thread", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_cells_per_thread", ctypes.c_int, [_vp]),
+    ("lbm_set_steps_per_launch", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_steps_per_launch", ctypes.c_int, [_vp]),
     ("lbm_destroy", None, [_vp]),
     ("lbm_last_error", ctypes.c_char_p, [_vp]),
     ("lbm_version", ctypes.c_char_p, []),
@@ -227,6 +229,14 @@ def lbm_set_cells_per_thread(h, cells) -> int:
 
 def lbm_cells_per_thread(h) -> int:
     return load().lbm_cells_per_thread(h)
+
+
+def lbm_set_steps_per_launch(h, steps) -> int:
+    return load().lbm_set_steps_per_launch(h, int(steps))
+
+
+def lbm_steps_per_launch(h) -> int:
+    return load().lbm_steps_per_launch(h)
 
 
 def lbm_destroy(h) -> None:
@@ -477,6 +487,14 @@ class Lattice:
     @cells_per_thread.setter
     def cells_per_thread(self, cells: int) -> None:
         check(lbm_set_cells_per_thread(self.h, cells), self.h, "lbm_set_cells_per_thread")
+
+    @property
+    def steps_per_launch(self) -> int:
+        return lbm_steps_per_launch(self.h)
+
+    @steps_per_launch.setter
+    def steps_per_launch(self, steps: int) -> None:
+        check(lbm_set_steps_per_launch(self.h, steps), self.h, "lbm_set_steps_per_launch")
 
     def close(self) -> None:
         if getattr(self, "h", None):

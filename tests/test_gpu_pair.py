@@ -48,13 +48,15 @@ def _workload(nx, ny, bc, variant, layer, seed):
                        rho_dev=1e-3 * rng.standard_normal((ny, nx)), steps=25, storage="f32")
 
 
-def _run(w, storage, cells, steps):
+def _run(w, storage, cells, steps, per_launch=1):
     """Decoded stored populations (float64, storage scale) and rho', ux, uy."""
     from paper_1203_6350_gb300 import lbm
 
     with lbm.Lattice.from_workload(w, storage=storage) as lat:
         lat.cells_per_thread = cells
         assert lat.cells_per_thread == cells
+        lat.steps_per_launch = per_launch
+        assert lat.steps_per_launch == per_launch
         lat.step(steps)
         buf, t = lat.get_state()
         assert t == steps
@@ -95,6 +97,51 @@ def test_pair_kernel_matches_the_one_cell_kernel(shape, bc, variant):
                 den = np.linalg.norm(x)
                 if den > 0:
                     assert np.linalg.norm(x - y) <= MANY_STEPS[storage] * den, (storage, layer)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 7), (130, 3), (257, 129), (64, 16),
+                                   (65, 17), (129, 33), (1025, 40)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("variant", ["none", "I", "II", "III", "viscous"])
+def test_two_steps_per_launch_match_one(shape, bc, variant):
+    """Temporal blocking: one launch of the two-step kernel against two
+    launches of the two-cell kernel (tiles of 64 x 16 cells whose ring of
+    step-one cells crosses the lattice edge, wraps, or stays inside), then
+    25 steps (12 two-step launches and one one-step launch)."""
+    nx, ny = shape
+    for layer in (0, 5):
+        if layer and 2 * layer >= min(nx, ny):
+            continue
+        w = _workload(nx, ny, bc, variant, layer, seed=nx * 104729 + ny)
+        for storage in ("f32", "f16dev", "bf16dev"):
+            a, _ = _run(w, storage, 2, 2, per_launch=1)
+            b, _ = _run(w, storage, 2, 2, per_launch=2)
+            scale = np.abs(a).max()
+            assert np.abs(a - b).max() <= 2 * ONE_STEP[storage] * scale, (storage, layer)
+            _, fa = _run(w, storage, 2, w.steps, per_launch=1)
+            _, fb = _run(w, storage, 2, w.steps, per_launch=2)
+            for x, y in zip(fa, fb):
+                den = np.linalg.norm(x)
+                if den > 0:
+                    assert np.linalg.norm(x - y) <= MANY_STEPS[storage] * den, (storage, layer)
+
+
+def test_two_steps_per_launch_through_graph_chunks():
+    """70 steps: one replayed graph of 32 two-step launches, then three more;
+    against the one-step-per-launch run, and the step counter."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = _workload(300, 190, "dirichlet", "III", 16, seed=11)
+    _, fa = _run(w, "f32", 2, 70, per_launch=1)
+    _, fb = _run(w, "f32", 2, 70, per_launch=2)
+    for x, y in zip(fa, fb):
+        assert np.linalg.norm(x - y) <= MANY_STEPS["f32"] * np.linalg.norm(x)
+    with lbm.Lattice.from_workload(w, storage="f32") as lat:
+        lat.steps_per_launch = 2
+        lat.step(70)
+        assert lat.time == 70
+        lat.step(1)
+        assert lat.time == 71
 
 
 def test_kernel_switches_rebuild_the_captured_graphs():
@@ -138,4 +185,12 @@ def test_cells_per_thread_choices():
         assert lat.cells_per_thread == 2  # the default where available
         for bad in (0, 3, -1):
             assert lbm.lbm_set_cells_per_thread(lat.h, bad) == lbm.LBM_ERR_ARG
+            assert lbm.lbm_set_steps_per_launch(lat.h, bad) == lbm.LBM_ERR_ARG
         assert lat.cells_per_thread == 2
+        lat.steps_per_launch = 2
+        lat.cells_per_thread = 1  # falls back to one step per launch
+        assert lat.steps_per_launch == 1
+        assert lbm.lbm_set_steps_per_launch(lat.h, 2) == lbm.LBM_ERR_ARG
+    with lbm.Lattice.from_workload(w, storage="f64") as lat:
+        assert lbm.lbm_set_steps_per_launch(lat.h, 2) == lbm.LBM_ERR_ARG
+        assert lat.steps_per_launch == 1
