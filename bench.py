@@ -420,13 +420,16 @@ def profiled_traffic():
 
 
 STEP_KERNEL = {1: "lbm::step_kernel<float, variant, Dirichlet> (one cell per thread)",
-               2: "lbm::step2_kernel<float, variant, Dirichlet> (two cells per thread, packed FP32)"}
+               2: "lbm::step2_kernel<float, variant, Dirichlet> (two cells per thread, packed FP32)",
+               "tb2": "lbm::step_tb2_kernel<float, variant, Dirichlet> (two cells per thread, "
+                      "two time steps per launch through shared memory)"}
 
 
-def timed_steps(w, steps: int, cells=None, warm: int = 10) -> float:
-    """Seconds for `steps` steps of workload w (device pulse init, `warm`
-    untimed steps first), through the graph-replayed lbm_step on a side stream;
-    cells = cells per thread of the step kernel (None: the library default)."""
+def timed_steps(w, steps: int, cells=None, per_launch=None, warm: int = 10):
+    """(seconds, steps per launch) for `steps` steps of workload w (device pulse
+    init, `warm` untimed steps first), through the graph-replayed lbm_step on a
+    side stream; cells = cells per thread, per_launch = time steps per launch
+    (None: the library's default for the lattice)."""
     import torch
 
     from paper_1203_6350_gb300 import lbm
@@ -436,6 +439,9 @@ def timed_steps(w, steps: int, cells=None, warm: int = 10) -> float:
         lat = with_warn(lambda: lbm.Lattice.from_workload(w, stream=stream, init="pulse"))
         if cells is not None:
             lat.cells_per_thread = cells
+        if per_launch is not None:
+            lat.steps_per_launch = per_launch
+        spl = lat.steps_per_launch
         lat.step(warm)
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
@@ -444,23 +450,34 @@ def timed_steps(w, steps: int, cells=None, warm: int = 10) -> float:
         z.record(stream)
         z.synchronize()
         lat.close()
-    return a.elapsed_time(z) / 1e3
+    return a.elapsed_time(z) / 1e3, spl
 
 
 def roofline_large(peaks, side: int = 4096, steps: int = 100):
-    """The same FP32 step kernel on a lattice larger than L2 (HBM-bound), with
-    two cells per thread (the default) and with one."""
+    """The FP32 step on a lattice larger than L2 (HBM-bound): the library's
+    default there (two cells per thread, two time steps per launch), and for
+    comparison one step per launch with two cells and with one cell per thread.
+    Algorithmic bytes per launch: 72 B per cell (9 FP32 populations read and
+    written once), whether the launch advances one step or two."""
     w = wl.quiescent(side, storage="f32", steps=steps, width=128, pulse=True)
-    per_launch = timed_steps(w, steps) / steps
-    per_launch_1 = timed_steps(w, steps, cells=1) / steps
-    achieved = BYTES_PER_CELL["f32"] * w.cells / per_launch / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "case": f"{side}x{side} FP32, 128-cell layer",
-            "kernel": STEP_KERNEL[2],
-            "avg_launch_us": per_launch * 1e6, "mlups": w.cells / per_launch / 1e6,
-            "one_cell_per_thread": {"avg_launch_us": per_launch_1 * 1e6,
-                                    "mlups": w.cells / per_launch_1 / 1e6},
-            "traffic_profile": "profiles/step_kernel_f32_4096x4096_full.md"}
+    out = {}
+    for key, cells, per_launch in (("default", None, None), ("one_step_per_launch", 2, 1),
+                                   ("one_cell_per_thread", 1, 1)):
+        t, spl = timed_steps(w, steps, cells=cells, per_launch=per_launch)
+        per_launch_s = t / (steps / spl)
+        out[key] = {"steps_per_launch": spl, "avg_launch_us": per_launch_s * 1e6,
+                    "mlups": w.cells * steps / t / 1e6,
+                    "achieved": BYTES_PER_CELL["f32"] * w.cells / per_launch_s / 1e9,
+                    "kernel": STEP_KERNEL["tb2" if spl == 2 else (cells or 2)]}
+    d = out["default"]
+    return {"bound": "hbm", "achieved": d["achieved"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": d["achieved"] / peaks["hbm_gbs"], "case": f"{side}x{side} FP32, 128-cell layer",
+            "kernel": d["kernel"], "steps_per_launch": d["steps_per_launch"],
+            "avg_launch_us": d["avg_launch_us"], "mlups": d["mlups"],
+            "bytes_per_launch": BYTES_PER_CELL["f32"] * w.cells,
+            "one_step_per_launch": out["one_step_per_launch"],
+            "one_cell_per_thread": out["one_cell_per_thread"],
+            "traffic_profile": "profiles/step_tb2_kernel_f32_4096x4096_full.md"}
 
 
 def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", "f16dev",
@@ -478,11 +495,14 @@ def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", 
     for side in sides:
         for st in storages:
             w = wl.quiescent(side, storage=st, steps=steps, width=128)
-            for cells in (2, 1):
-                t = timed_steps(w, steps, cells=cells)
-                gbs = BYTES_PER_CELL[st] * w.cells * steps / t / 1e9
-                rows.append({"side": side, "storage": st, "cells_per_thread": cells,
-                             "bytes_per_cell_step": BYTES_PER_CELL[st],
+            for cells, per_launch in ((None, None), (2, 1), (1, 1)):
+                t, spl = timed_steps(w, steps, cells=cells, per_launch=per_launch)
+                launches = steps / spl
+                gbs = BYTES_PER_CELL[st] * w.cells * launches / t / 1e9
+                rows.append({"side": side, "storage": st, "cells_per_thread": cells or 2,
+                             "steps_per_launch": spl, "library_default": cells is None,
+                             "bytes_per_cell_launch": BYTES_PER_CELL[st],
+                             "bytes_per_cell_step": BYTES_PER_CELL[st] / spl,
                              "mlups": w.cells * steps / t / 1e6, "gbs": gbs,
                              "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]})
             torch.cuda.empty_cache()

@@ -198,8 +198,10 @@ int lbm_cells_per_thread(lbm_handle h);
  * switches it back to 1).  lbm_step(h, n) then issues n / 2 two-step
  * launches and one one-step launch for an odd n.  Results agree with one step
  * per launch to FP32 rounding.  LBM_ERR_ARG for any other value or an
- * unsupported 2.  Waits for the handle's stream.  The environment variable
- * LBM_SPL=1|2 sets the initial choice of new handles where 2 is available. */
+ * unsupported 2.  Waits for the handle's stream.  New handles start with 2
+ * where it is available and the two population buffers together exceed the
+ * device's L2 cache (the step is then HBM-bound), else 1; the environment
+ * variable LBM_SPL=1|2 overrides that choice. */
 int lbm_set_steps_per_launch(lbm_handle h, int steps);
 /* The current choice (LBM_ERR_ARG for a NULL handle). */
 int lbm_steps_per_launch(lbm_handle h);

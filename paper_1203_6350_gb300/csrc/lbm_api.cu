@@ -304,6 +304,13 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     if (const char* c = std::getenv("LBM_CPT")) {
         if (!std::strcmp(c, "1")) h->cpt = 1;
     }
+    // Two steps per launch pay off once the double-buffered state no longer
+    // fits in L2 (the step is then HBM-bound); below that the extra ring of
+    // collisions costs more than the traffic it saves.
+    int l2 = 0;
+    if (h->cpt == 2 && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device) == cudaSuccess &&
+        2 * h->buf_bytes > static_cast<size_t>(l2))
+        h->spl = 2;
     if (const char* c = std::getenv("LBM_SPL")) {
         if (!std::strcmp(c, "2") && h->cpt == 2) h->spl = 2;
         if (!std::strcmp(c, "1")) h->spl = 1;
