@@ -251,6 +251,19 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
  * the tile in rows).  Default 128 x 8. */
 int lbm_batch_set_tiling(lbm_batch b, int tile_x, int tile_y);
 
+/* Cells each thread of the batched launch advances: 1, or 2 (the pair of
+ * cells (x, x + 1) on packed FP32 arithmetic, as lbm_set_cells_per_thread;
+ * a block of 256 threads then covers tile_x / 2 pairs per row).  2 is the
+ * default for LBM_F16DEV and LBM_BF16DEV batches, 1 for LBM_F32 (whose
+ * batched step is bound by memory latency, where the one-cell kernel's
+ * higher occupancy wins) and LBM_F64 (which has no pair kernel).  The
+ * environment variable LBM_CPT=1|2 overrides the default of new batches.
+ * LBM_ERR_ARG for any other value or 2 with LBM_F64.  Waits for the batch's
+ * stream. */
+int lbm_batch_set_cells_per_thread(lbm_batch b, int cells);
+/* The current choice (LBM_ERR_ARG for a NULL batch). */
+int lbm_batch_cells_per_thread(lbm_batch b);
+
 /* Add an instance (arguments as lbm_create and lbm_set_sponge; chi arrays are
  * host arrays, copied) with a budget of nsteps >= 0 steps.  Allocates its
  * buffers; *id receives its handle.  It takes no steps until

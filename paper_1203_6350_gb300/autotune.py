@@ -3,7 +3,8 @@
 For a set of lattice shapes and a storage type it times the batched step with
 each candidate tile shape on a scratch batch of the same shapes (CUDA events
 on the batch's stream, after warm-up steps) and picks the fastest.  Results
-are cached per (GPU name, storage, shape signature) in a JSON file, by default
+are cached per (GPU name, storage, cells per thread, shape signature) in a
+JSON file, by default
 ~/.cache/lbm_gb300/autotune.json (LBM_AUTOTUNE_CACHE overrides it).
 """
 from __future__ import annotations
@@ -48,8 +49,19 @@ def _store(d):
     os.replace(tmp, p)
 
 
-def measure(shapes, storage="f32", candidates=CANDIDATES, steps=64, warmup=32):
-    """Seconds per batched step for each candidate tile shape."""
+def default_cells(storage: str) -> int:
+    """Cells per thread a new batch of this storage uses (see lbm_batch_create)."""
+    env = os.environ.get("LBM_CPT")
+    if storage == "f64" or env == "1":
+        return 1
+    if env == "2":
+        return 2
+    return 2 if storage in ("f16dev", "bf16dev") else 1
+
+
+def measure(shapes, storage="f32", candidates=CANDIDATES, steps=64, warmup=32, cells=None):
+    """Seconds per batched step for each candidate tile shape (cells = cells per
+    thread of the batched kernel; None: the batch's default)."""
     import torch
 
     from .batch import Batch
@@ -58,6 +70,8 @@ def measure(shapes, storage="f32", candidates=CANDIDATES, steps=64, warmup=32):
     out = {}
     with torch.cuda.stream(stream):
         b = Batch(storage, stream=stream)
+        if cells is not None:
+            b.cells_per_thread = cells
         for nx, ny in shapes:
             i = b.add(nx, ny, steps=1 << 40, s=1.99, variant="II",
                       chi_x=[0.1] * min(8, nx) + [0.0] * (nx - min(8, nx)),
@@ -77,15 +91,17 @@ def measure(shapes, storage="f32", candidates=CANDIDATES, steps=64, warmup=32):
     return out
 
 
-def tuned_tiling(shapes, storage="f32", retune=False, candidates=CANDIDATES):
-    """Best (tile_x, tile_y) for this shape set, from the cache or measured."""
+def tuned_tiling(shapes, storage="f32", retune=False, candidates=CANDIDATES, cells=None):
+    """Best (tile_x, tile_y) for this shape set and kernel (cells per thread;
+    None: the batch's default), from the cache or measured."""
     import torch
 
-    key = f"{torch.cuda.get_device_name()}|{storage}|{signature(shapes)}"
+    cells = default_cells(storage) if cells is None else cells
+    key = f"{torch.cuda.get_device_name()}|{storage}|cpt{cells}|{signature(shapes)}"
     cache = _load()
     if not retune and key in cache:
         return tuple(cache[key]["tile"])
-    times = measure(shapes, storage, candidates)
+    times = measure(shapes, storage, candidates, cells=cells)
     best = min(times, key=times.get)
     cache[key] = {"tile": list(best), "seconds_per_step": {f"{a}x{b}": t for (a, b), t in
                                                            times.items()}}

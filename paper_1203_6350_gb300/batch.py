@@ -44,6 +44,15 @@ class Batch:
     def set_tiling(self, tile_x: int, tile_y: int) -> None:
         self._check(lbm.lbm_batch_set_tiling(self.b, tile_x, tile_y), "lbm_batch_set_tiling")
 
+    @property
+    def cells_per_thread(self) -> int:
+        return lbm.lbm_batch_cells_per_thread(self.b)
+
+    @cells_per_thread.setter
+    def cells_per_thread(self, cells: int) -> None:
+        self._check(lbm.lbm_batch_set_cells_per_thread(self.b, cells),
+                    "lbm_batch_set_cells_per_thread")
+
     def add(self, nx, ny, steps, s=1.9, n=0.5, m=0.5, rho0=1.0, u0=(0.0, 0.0), bc="dirichlet",
             variant="none", chi_x=None, chi_y=None, rho_ref=None, u_ref=None) -> int:
         cx = np.ascontiguousarray(np.zeros(nx) if chi_x is None else chi_x, dtype=np.float64)

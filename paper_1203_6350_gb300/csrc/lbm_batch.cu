@@ -20,16 +20,28 @@
 #include <vector>
 
 #include "lbm.h"
-#include "lbm_step.cuh"
+#include "lbm_step2.cuh"
 
 namespace lbm {
 
-// Device descriptor of one instance.
+// Element type of the per-axis tables for a compute type (the packed pair
+// reads the FP32 tables).
+template <typename CT>
+struct AxisOf {
+    using type = CT;
+};
+template <>
+struct AxisOf<F2> {
+    using type = float;
+};
+
+// Device descriptor of one instance; CT is the compute type of its constants
+// (double, float, or F2 for the two-cells-per-thread kernel).
 template <typename CT>
 struct BatchInst {
     void* buf[2];
-    const AxisCoef<CT>* tx;
-    const AxisCoef<CT>* ty;
+    const AxisCoef<typename AxisOf<CT>::type>* tx;
+    const AxisCoef<typename AxisOf<CT>::type>* ty;
     long long start, end;  // active for start <= step < end
     long long plane;
     int nx, ny, pitch, variant, bc, pad;
@@ -57,29 +69,21 @@ struct BatchMinBlocks<double> {
     static constexpr int value = 3;
 };
 
-// One time step of every active instance.  Block b of G walks the tiles b,
-// b + G, ..., so that at any moment the G blocks sweep one compact stretch of
-// the tile table (a contiguous run per block spreads the DRAM accesses and
-// measured 27 % slower).  The tile table lists each instance's tiles
-// together: a block copies an instance descriptor to shared memory only when
-// its next tile belongs to another instance, and it fetches the next tile
-// entry while it processes the current tile.  The block covers a
-// tile_x x tile_y tile with blockDim = (tile_x, 256/tile_x).
-template <typename T>
-__global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
-    batch_step_kernel(const BatchInst<typename Codec<T>::CT>* __restrict__ insts,
-                      const BatchTile* __restrict__ tiles, const int* __restrict__ ntiles_p,
-                      const long long* __restrict__ step_p, int k_in_chunk, int tile_y) {
-    using CT = typename Codec<T>::CT;
-    using Inst = BatchInst<CT>;
-    __shared__ __align__(16) unsigned char raw[sizeof(Inst)];
-    Inst& sd = *reinterpret_cast<Inst*>(raw);
+// Walk this block's tiles b, b + G, ... of the table, so that at any moment
+// the G blocks sweep one compact stretch of it (a contiguous run per block
+// spreads the DRAM accesses and measured 27 % slower).  The table lists each
+// instance's tiles together: the block copies an instance descriptor to
+// shared memory only when its next tile belongs to another instance, and it
+// fetches the next tile entry while it processes the current one.  body(tile,
+// descriptor, step) runs for the tiles of instances active at `step`
+// (start <= step < end); every branch on the descriptor is block-uniform.
+template <typename Inst, typename Body>
+__device__ __forceinline__ void walk_tiles(const Inst* __restrict__ insts,
+                                           const BatchTile* __restrict__ tiles, int ntiles,
+                                           long long step, unsigned char* raw, Body& body) {
+    const Inst& sd = *reinterpret_cast<const Inst*>(raw);
     constexpr int kWords = (int)(sizeof(Inst) / 4);
     static_assert(sizeof(Inst) % 4 == 0, "descriptor must be word-sized");
-    // the previous step's grid must have finished before any buffer is touched
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const long long step = *step_p + k_in_chunk;
-    const int ntiles = *ntiles_p;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
     const int G = gridDim.x;
@@ -97,6 +101,18 @@ __global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
             held = tile.inst;
         }
         if (step < sd.start || step >= sd.end) continue;  // block-uniform
+        body(tile, sd, step);
+    }
+}
+
+// One cell per thread: the tile is tile_x x tile_y cells, blockDim =
+// (tile_x, 256 / tile_x).
+template <typename T>
+struct CellTile {
+    using CT = typename Codec<T>::CT;
+    int tile_y;
+    __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<CT>& sd,
+                                               long long step) const {
         const int parity = (int)((step - sd.start) & 1);
         const T* src = static_cast<const T*>(sd.buf[parity]);
         T* dst = static_cast<T*>(sd.buf[1 - parity]);
@@ -131,21 +147,118 @@ __global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
             store_all_b<T>(dst, plane, o, v);
         }
     }
+};
+
+// Two cells per thread (packed FP32): the tile is tile_x x tile_y cells,
+// blockDim = (tile_x / 2, 512 / tile_x); a thread steps the pair (x, x + 1)
+// of each of its rows, with the single-lattice pair kernel's pull, collision
+// and store.
+template <typename T>
+struct PairTile {
+    int tile_y;
+    __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<F2>& sd,
+                                               long long step) const {
+        const int parity = (int)((step - sd.start) & 1);
+        const T* src = static_cast<const T*>(sd.buf[parity]);
+        T* dst = static_cast<T*>(sd.buf[1 - parity]);
+        const unsigned plane = static_cast<unsigned>(sd.plane);  // 9 * plane < 2^31 (checked on add)
+        const int nx = sd.nx, ny = sd.ny, pitch = sd.pitch;
+        const int x = tile.x0 + 2 * threadIdx.x;
+        if (x >= nx) return;
+        for (int ry = threadIdx.y; ry < tile_y; ry += blockDim.y) {
+            const int y = tile.y0 + ry;
+            if (y >= ny) break;
+            const unsigned o = static_cast<unsigned>(y * pitch + x);
+            F2 v[9];
+            if (x > 0 && x + 2 < nx && y > 0 && y + 1 < ny)
+                pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch), o, v);
+            else if (sd.bc == kPeriodic)
+                pull_pair_edge<T, kPeriodic>(src, plane, pitch, x, y, nx, ny, v);
+            else
+                pull_pair_edge<T, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
+            switch (sd.variant) {
+                case kTypeI: collide_pair<kTypeI>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeII: collide_pair<kTypeII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeIII: collide_pair<kTypeIII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kViscous: collide_pair<kViscous>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                default: collide_pair<kNone>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+            }
+            if (x + 1 < nx)
+                store_pair<T>(dst, plane, o, v);
+            else
+                store_lo<T>(dst, plane, o, v);
+        }
+    }
+};
+
+// One time step of every active instance, one cell per thread.
+template <typename T>
+__global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
+    batch_step_kernel(const BatchInst<typename Codec<T>::CT>* __restrict__ insts,
+                      const BatchTile* __restrict__ tiles, const int* __restrict__ ntiles_p,
+                      const long long* __restrict__ step_p, int k_in_chunk, int tile_y) {
+    __shared__ __align__(16) unsigned char raw[sizeof(BatchInst<typename Codec<T>::CT>)];
+    // the previous step's grid must have finished before any buffer is touched
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    CellTile<T> body{tile_y};
+    walk_tiles(insts, tiles, *ntiles_p, *step_p + k_in_chunk, raw, body);
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+// One time step of every active instance, two cells per thread.  At most 80
+// registers (3 blocks per SM): left to itself the compiler keeps the packed
+// descriptor constants in registers across the tile's rows and needs 116.
+template <typename T>
+__global__ void __launch_bounds__(256, 3)
+    batch_step2_kernel(const BatchInst<F2>* __restrict__ insts, const BatchTile* __restrict__ tiles,
+                       const int* __restrict__ ntiles_p, const long long* __restrict__ step_p,
+                       int k_in_chunk, int tile_y) {
+    __shared__ __align__(16) unsigned char raw[sizeof(BatchInst<F2>)];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    PairTile<T> body{tile_y};
+    walk_tiles(insts, tiles, *ntiles_p, *step_p + k_in_chunk, raw, body);
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
 __global__ void advance_step_kernel(long long* step_p, int by) { *step_p += by; }
 
 template <typename T>
-const void* batch_kernel_ptr() {
+const void* batch_kernel_ptr(int cells) {
+    if (cells == 2) return reinterpret_cast<const void*>(&batch_step2_kernel<T>);
     return reinterpret_cast<const void*>(&batch_step_kernel<T>);
 }
+template <>
+const void* batch_kernel_ptr<double>(int) {
+    return reinterpret_cast<const void*>(&batch_step_kernel<double>);
+}
 
+// One batched step; cells = cells per thread (2: FP32 and 16-bit storage).
 template <typename T>
 cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int* ntiles,
                            const long long* step, int k, int tile_x, int tile_y, int grid,
-                           cudaStream_t st, int pdl) {
+                           int cells, cudaStream_t st, int pdl) {
     using CT = typename Codec<T>::CT;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = cells == 2 ? dim3(tile_x / 2, 512 / tile_x) : dim3(tile_x, 256 / tile_x);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    if (cells == 2)
+        return cudaLaunchKernelEx(&cfg, batch_step2_kernel<T>,
+                                  static_cast<const BatchInst<F2>*>(insts), tiles, ntiles, step, k,
+                                  tile_y);
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel<T>,
+                              static_cast<const BatchInst<CT>*>(insts), tiles, ntiles, step, k,
+                              tile_y);
+}
+template <>
+cudaError_t launch_batch_t<double>(const void* insts, const BatchTile* tiles, const int* ntiles,
+                                   const long long* step, int k, int tile_x, int tile_y, int grid,
+                                   int, cudaStream_t st, int pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(tile_x, 256 / tile_x);
@@ -155,8 +268,8 @@ cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int*
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, batch_step_kernel<T>,
-                              static_cast<const BatchInst<CT>*>(insts), tiles, ntiles, step, k,
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel<double>,
+                              static_cast<const BatchInst<double>*>(insts), tiles, ntiles, step, k,
                               tile_y);
 }
 
@@ -199,6 +312,7 @@ struct lbm_batch_ctx {
     std::map<int, Instance> insts;
     int next_id = 0;
     int64_t step = 0;  // global step (host mirror of *d_step)
+    int cpt = 1;       // cells per thread of the batched kernel (2 is the 16-bit default)
     int tile_x = 128, tile_y = 8;
     int grid = 0;
     // device tables
@@ -275,8 +389,9 @@ BatchInst<CT> desc_of(const Instance& in) {
     BatchInst<CT> d{};
     d.buf[0] = in.buf[0];
     d.buf[1] = in.buf[1];
-    d.tx = static_cast<const AxisCoef<CT>*>(in.tabs);
-    d.ty = static_cast<const AxisCoef<CT>*>(in.tabs) + in.nx;
+    using A = AxisCoef<typename lbm::AxisOf<CT>::type>;
+    d.tx = static_cast<const A*>(in.tabs);
+    d.ty = static_cast<const A*>(in.tabs) + in.nx;
     d.start = in.initialised ? in.start : LLONG_MAX;
     d.end = in.initialised ? in.start + in.budget : LLONG_MAX;
     d.plane = in.geo.plane;
@@ -289,8 +404,9 @@ BatchInst<CT> desc_of(const Instance& in) {
     return d;
 }
 
-size_t desc_size(int storage) {
-    return storage == LBM_F64 ? sizeof(BatchInst<double>) : sizeof(BatchInst<float>);
+size_t desc_size(int storage, int cells) {
+    if (storage == LBM_F64) return sizeof(BatchInst<double>);
+    return cells == 2 ? sizeof(BatchInst<lbm::F2>) : sizeof(BatchInst<float>);
 }
 
 void drop_batch_graph(lbm_batch_ctx* b) {
@@ -302,27 +418,27 @@ cudaError_t launch_batch(lbm_batch_ctx* b, cudaStream_t st, int k, int pdl) {
     switch (b->storage) {
         case LBM_F64:
             return lbm::launch_batch_t<double>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
-                                               b->tile_x, b->tile_y, b->grid, st, pdl);
+                                               b->tile_x, b->tile_y, b->grid, 1, st, pdl);
         case LBM_F32:
             return lbm::launch_batch_t<float>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
-                                              b->tile_x, b->tile_y, b->grid, st, pdl);
+                                              b->tile_x, b->tile_y, b->grid, b->cpt, st, pdl);
         case LBM_F16DEV:
             return lbm::launch_batch_t<__half>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
-                                               b->tile_x, b->tile_y, b->grid, st, pdl);
+                                               b->tile_x, b->tile_y, b->grid, b->cpt, st, pdl);
         default:
             return lbm::launch_batch_t<__nv_bfloat16>(b->d_insts, b->d_tiles, b->d_ntiles,
                                                       b->d_step, k, b->tile_x, b->tile_y,
-                                                      b->grid, st, pdl);
+                                                      b->grid, b->cpt, st, pdl);
     }
 }
 
 cudaError_t compute_grid(lbm_batch_ctx* b) {
     const void* fn = nullptr;
     switch (b->storage) {
-        case LBM_F64: fn = lbm::batch_kernel_ptr<double>(); break;
-        case LBM_F32: fn = lbm::batch_kernel_ptr<float>(); break;
-        case LBM_F16DEV: fn = lbm::batch_kernel_ptr<__half>(); break;
-        default: fn = lbm::batch_kernel_ptr<__nv_bfloat16>(); break;
+        case LBM_F64: fn = lbm::batch_kernel_ptr<double>(1); break;
+        case LBM_F32: fn = lbm::batch_kernel_ptr<float>(b->cpt); break;
+        case LBM_F16DEV: fn = lbm::batch_kernel_ptr<__half>(b->cpt); break;
+        default: fn = lbm::batch_kernel_ptr<__nv_bfloat16>(b->cpt); break;
     }
     int per_sm = 0, sms = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
@@ -338,7 +454,7 @@ int sync_tables(lbm_batch_ctx* b) {
     b->dense.clear();
     std::vector<unsigned char> descs;
     std::vector<BatchTile> tiles;
-    const size_t ds = desc_size(b->storage);
+    const size_t ds = desc_size(b->storage, b->cpt);
     for (auto& kv : b->insts) {
         const Instance& in = kv.second;
         const int di = static_cast<int>(b->dense.size());
@@ -347,6 +463,9 @@ int sync_tables(lbm_batch_ctx* b) {
         descs.resize(off + ds);
         if (b->storage == LBM_F64) {
             const BatchInst<double> d = desc_of<double>(in);
+            std::memcpy(descs.data() + off, &d, ds);
+        } else if (b->cpt == 2) {
+            const BatchInst<lbm::F2> d = desc_of<lbm::F2>(in);
             std::memcpy(descs.data() + off, &d, ds);
         } else {
             const BatchInst<float> d = desc_of<float>(in);
@@ -451,6 +570,14 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
     if (alloc && (!alloc->alloc || !alloc->free)) return LBM_ERR_ARG;
     lbm_batch_ctx* b = new lbm_batch_ctx();
     b->storage = storage;
+    // 16-bit batches are issue-bound and gain from the packed pair (1.2x measured);
+    // FP32 batches are memory-latency-bound and the one-cell kernel's higher
+    // occupancy wins (1.04x).
+    b->cpt = (storage == LBM_F16DEV || storage == LBM_BF16DEV) ? 2 : 1;
+    if (const char* c = std::getenv("LBM_CPT")) {
+        if (!std::strcmp(c, "1")) b->cpt = 1;
+        if (!std::strcmp(c, "2") && storage != LBM_F64) b->cpt = 2;
+    }
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     if (alloc) {
         b->alloc = *alloc;
@@ -496,6 +623,24 @@ int lbm_batch_set_tiling(lbm_batch b, int tile_x, int tile_y) {
     drop_batch_graph(b);
     return LBM_OK;
 }
+
+int lbm_batch_set_cells_per_thread(lbm_batch b, int cells) {
+    if (!b) return LBM_ERR_ARG;
+    if (cells != 1 && cells != 2) return bfail(b, LBM_ERR_ARG, "cells per thread must be 1 or 2");
+    if (cells == 2 && b->storage == LBM_F64)
+        return bfail(b, LBM_ERR_ARG, "two cells per thread needs FP32 or 16-bit storage");
+    if (cells == b->cpt) return LBM_OK;
+    BDeviceGuard dg(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_batch_graph(b);  // the captured launches name the other kernel
+    b->cpt = cells;
+    b->dirty = true;      // the descriptors change type
+    const cudaError_t e = compute_grid(b);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("grid: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_batch_cells_per_thread(lbm_batch b) { return b ? b->cpt : LBM_ERR_ARG; }
 
 int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double uy0,
                   const lbm_rates* rates, lbm_bc bc, lbm_variant variant, const double* chi_x,

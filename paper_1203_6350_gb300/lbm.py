@@ -93,6 +93,8 @@ SIGNATURES = [
     ("lbm_batch_create", ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(lbm_allocator),
                                         ctypes.POINTER(_vp)]),
     ("lbm_batch_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    ("lbm_batch_set_cells_per_thread", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_batch_cells_per_thread", ctypes.c_int, [_vp]),
     ("lbm_batch_add", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(lbm_rates),
                                      ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double,
@@ -266,6 +268,14 @@ def lbm_batch_create(storage, stream=None, alloc: Optional[lbm_allocator] = None
 
 def lbm_batch_set_tiling(b, tile_x, tile_y) -> int:
     return load().lbm_batch_set_tiling(b, int(tile_x), int(tile_y))
+
+
+def lbm_batch_set_cells_per_thread(b, cells) -> int:
+    return load().lbm_batch_set_cells_per_thread(b, int(cells))
+
+
+def lbm_batch_cells_per_thread(b) -> int:
+    return load().lbm_batch_cells_per_thread(b)
 
 
 def lbm_batch_add(b, nx, ny, rho0, ux0, uy0, rates: lbm_rates, bc, variant, chi_x_ptr,

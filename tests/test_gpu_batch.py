@@ -3,7 +3,8 @@ of the single-lattice path, whatever else is in the batch, whatever the tile
 shape, and whenever it was admitted.
 
 Within the batched path the per-cell instruction sequence does not depend on
-the tile shape or on the other instances, so those comparisons are bit-exact.
+the tile shape or on the other instances, so those comparisons are bit-exact,
+for the one-cell and for the two-cell (packed FP32) batched kernel alike.
 Against the single-lattice kernel the source arithmetic is shared but the
 compiler may contract multiply-adds differently in the two kernels: FP64 is
 bit-exact there, FP32 / FP16 agree to a few ulps (held to the parity
@@ -84,29 +85,64 @@ def test_batch_equals_single_lattice(storage):
                 _close(a, c, 0 if storage == "f64" else TOL[storage])
 
 
-def _batch_run(works, storage, tiling=None, steps=100):
+def _batch_run(works, storage, tiling=None, steps=100, cells=None):
     from paper_1203_6350_gb300.batch import Batch
 
     with Batch(storage, tiling=tiling) as b:
+        if cells is not None:
+            b.cells_per_thread = cells
+            assert b.cells_per_thread == cells
         ids = [b.add_workload(w) for w in works]
         b.step(steps)
         return [b.moments(i)[0] for i in ids]
 
 
+@pytest.mark.parametrize("cells", [1, 2])
 @pytest.mark.parametrize("tiling", [(32, 8), (64, 4), (128, 2), (128, 16), (256, 1), (256, 4)])
-def test_tile_shape_does_not_change_results(tiling):
+def test_tile_shape_does_not_change_results(tiling, cells):
     works = _mixed_workloads("f32")
-    ref = _batch_run(works, "f32")
-    for r, q in zip(_batch_run(works, "f32", tiling), ref):
+    ref = _batch_run(works, "f32", cells=cells)
+    for r, q in zip(_batch_run(works, "f32", tiling, cells=cells), ref):
         np.testing.assert_array_equal(r, q)
 
 
-def test_result_alone_equals_result_in_the_mix():
+@pytest.mark.parametrize("cells", [1, 2])
+def test_result_alone_equals_result_in_the_mix(cells):
     works = _mixed_workloads("f32")
-    mixed = _batch_run(works, "f32")
+    mixed = _batch_run(works, "f32", cells=cells)
     for w, m in zip(works, mixed):
-        (alone,) = _batch_run([w], "f32")
+        (alone,) = _batch_run([w], "f32", cells=cells)
         np.testing.assert_array_equal(alone, m)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev"])
+def test_pair_batch_kernel_matches_the_one_cell_batch_kernel(storage):
+    """The two batched kernels agree to the storage format's rounding level
+    (the pair form's fused products differ in the last bits; see
+    test_gpu_pair.py) on ragged, 1-cell, periodic, MRT and layered lattices."""
+    works = _mixed_workloads(storage)
+    tol = {"f32": 1e-5, "f16dev": 1e-2, "bf16dev": 6e-2}[storage]
+    one = _batch_run(works, storage, cells=1)
+    two = _batch_run(works, storage, cells=2)
+    for a, c in zip(two, one):
+        _close(a, c, tol)
+
+
+def test_cells_per_thread_of_a_batch():
+    from paper_1203_6350_gb300 import lbm
+    from paper_1203_6350_gb300.batch import Batch
+
+    with Batch("f64") as b:
+        assert b.cells_per_thread == 1
+        assert lbm.lbm_batch_set_cells_per_thread(b.b, 2) == lbm.LBM_ERR_ARG
+    with Batch("f16dev") as b:
+        assert b.cells_per_thread == 2
+    with Batch("f32") as b:
+        assert b.cells_per_thread == 1
+        for bad in (0, 3):
+            assert lbm.lbm_batch_set_cells_per_thread(b.b, bad) == lbm.LBM_ERR_ARG
+        b.cells_per_thread = 2
+        assert b.cells_per_thread == 2
 
 
 def test_staggered_admission_and_removal():
