@@ -574,9 +574,9 @@ def run_e2e(works, lats, stream, dev, steps):
 def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
     """Batched workload: `count` independent lattices (sides log-uniform in
     [64, 1024], seeded pulses, Mach in [0, 0.2], chi_max log-uniform in [1e-3, 1],
-    layer 8-64 cells, variants cycled), FP32, `steps` steps, one persistent launch
-    per step (autotuned tile shape, graph-replayed) against one launch per lattice
-    per step through the single-lattice API."""
+    layer 8-64 cells, variants cycled), FP32, `steps` steps, persistent launches
+    (kernel and tile shape from the autotuner, graph-replayed) against one
+    launch per lattice per step through the single-lattice API."""
     import torch
 
     from paper_1203_6350_gb300 import autotune, lbm
@@ -584,11 +584,11 @@ def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
 
     works = wl.batch_of_lattices(seed=SEED, count=count, steps=steps + warmup, storage="f32")
     shapes = [(w.nx, w.ny) for w in works]
-    tile = autotune.tuned_tiling(shapes, "f32")
+    cfg = autotune.tuned_config(shapes, "f32")
     cells = sum(w.cells for w in works)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        b = Batch("f32", stream=stream, tiling=tile)
+        b = Batch("f32", stream=stream, config=cfg)
         for w in works:
             with_warn(lambda: b.add_workload(w))
         b.step(warmup)
@@ -620,7 +620,10 @@ def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
     return {
         "workload": f"{count} lattices, sides log-uniform in [64, 1024] (seed {SEED}), FP32, "
                     f"variants cycled I/II/III, {steps} steps",
-        "lattices": count, "cells": cells, "steps": steps, "tile": list(tile),
+        "lattices": count, "cells": cells, "steps": steps, "tile": list(cfg["tile"]),
+        "cells_per_thread": cfg["cells"], "steps_per_launch": cfg["steps_per_launch"],
+        "kernel": {(1, 1): "batch_step_kernel<float>", (2, 1): "batch_step2_kernel<float>",
+                   (2, 2): "batch_tb2_kernel<float>"}[(cfg["cells"], cfg["steps_per_launch"])],
         "mlups": cells * steps / t_batch / 1e6,
         "plain_loop_mlups": cells * steps / t_plain / 1e6,
         "speedup_vs_plain_loop": t_plain / t_batch,

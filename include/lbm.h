@@ -264,6 +264,18 @@ int lbm_batch_set_cells_per_thread(lbm_batch b, int cells);
 /* The current choice (LBM_ERR_ARG for a NULL batch). */
 int lbm_batch_cells_per_thread(lbm_batch b);
 
+/* Global time steps per batched launch: 1, or 2 (temporal blocking on tiles
+ * of 64 x 16 cells through shared memory, as lbm_set_steps_per_launch; the
+ * tile shape of lbm_batch_set_tiling then applies to one-step launches only).
+ * An instance whose budget ends after the first step of a two-step launch
+ * takes that one step.  Needs two cells per thread
+ * (lbm_batch_set_cells_per_thread(b, 1) switches it back to 1).  Default 1.
+ * LBM_ERR_ARG for any other value or an unsupported 2.  Waits for the
+ * batch's stream. */
+int lbm_batch_set_steps_per_launch(lbm_batch b, int steps);
+/* The current choice (LBM_ERR_ARG for a NULL batch). */
+int lbm_batch_steps_per_launch(lbm_batch b);
+
 /* Add an instance (arguments as lbm_create and lbm_set_sponge; chi arrays are
  * host arrays, copied) with a budget of nsteps >= 0 steps.  Allocates its
  * buffers; *id receives its handle.  It takes no steps until

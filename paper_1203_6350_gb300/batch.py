@@ -16,7 +16,9 @@ from . import lbm
 
 class Batch:
     def __init__(self, storage: str = "f32", stream=None, allocator: str = "torch",
-                 device: int = 0, tiling: Optional[tuple] = None):
+                 device: int = 0, tiling: Optional[tuple] = None, config: Optional[dict] = None):
+        """config: a kernel configuration {"cells", "steps_per_launch", "tile"}
+        (as autotune.tuned_config returns); tiling: a tile shape only."""
         import torch
 
         self.torch = torch
@@ -33,6 +35,8 @@ class Batch:
         self.shapes = {}
         if tiling is not None:
             self.set_tiling(*tiling)
+        if config is not None:
+            self.configure(config["cells"], config["steps_per_launch"], config["tile"])
 
     def _check(self, rc: int, what: str) -> int:
         if rc < 0:
@@ -44,6 +48,14 @@ class Batch:
     def set_tiling(self, tile_x: int, tile_y: int) -> None:
         self._check(lbm.lbm_batch_set_tiling(self.b, tile_x, tile_y), "lbm_batch_set_tiling")
 
+    def configure(self, cells: int, steps_per_launch: int, tile) -> None:
+        """Kernel (cells per thread, time steps per launch) and one-step tile shape."""
+        if steps_per_launch == 1:
+            self.steps_per_launch = 1
+        self.cells_per_thread = cells
+        self.steps_per_launch = steps_per_launch
+        self.set_tiling(*tile)
+
     @property
     def cells_per_thread(self) -> int:
         return lbm.lbm_batch_cells_per_thread(self.b)
@@ -52,6 +64,15 @@ class Batch:
     def cells_per_thread(self, cells: int) -> None:
         self._check(lbm.lbm_batch_set_cells_per_thread(self.b, cells),
                     "lbm_batch_set_cells_per_thread")
+
+    @property
+    def steps_per_launch(self) -> int:
+        return lbm.lbm_batch_steps_per_launch(self.b)
+
+    @steps_per_launch.setter
+    def steps_per_launch(self, steps: int) -> None:
+        self._check(lbm.lbm_batch_set_steps_per_launch(self.b, steps),
+                    "lbm_batch_set_steps_per_launch")
 
     def add(self, nx, ny, steps, s=1.9, n=0.5, m=0.5, rho0=1.0, u0=(0.0, 0.0), bc="dirichlet",
             variant="none", chi_x=None, chi_y=None, rho_ref=None, u_ref=None) -> int:

@@ -6,7 +6,11 @@
 // boundary, reference state, absorbing profile) with its own double buffer.
 // It is active for the global steps start <= s < end, so instances admitted
 // at different times and with different step budgets share every launch and
-// each takes exactly its own number of steps.  The per-cell arithmetic is the
+// each takes exactly its own number of steps.  A launch advances one global
+// step, or two (temporal blocking); an instance whose budget ends after the
+// first of the two takes only that one.  Every launch swaps the buffers of
+// the instances it advanced, so an instance's current buffer is the parity of
+// the number of launches it took, which the host counts.  The per-cell arithmetic is the
 // single-lattice kernel's (collide_cell, pull_all, store_all), so a lattice
 // gives the same result alone and in a batch.
 #include <algorithm>
@@ -20,7 +24,7 @@
 #include <vector>
 
 #include "lbm.h"
-#include "lbm_step2.cuh"
+#include "lbm_step_tb.cuh"
 
 namespace lbm {
 
@@ -43,6 +47,7 @@ struct BatchInst {
     const AxisCoef<typename AxisOf<CT>::type>* tx;
     const AxisCoef<typename AxisOf<CT>::type>* ty;
     long long start, end;  // active for start <= step < end
+    long long l0;          // global launch index of its first launch (buffer 0 holds time 0)
     long long plane;
     int nx, ny, pitch, variant, bc, pad;
     StepConst<CT> k;
@@ -74,13 +79,16 @@ struct BatchMinBlocks<double> {
 // spreads the DRAM accesses and measured 27 % slower).  The table lists each
 // instance's tiles together: the block copies an instance descriptor to
 // shared memory only when its next tile belongs to another instance, and it
-// fetches the next tile entry while it processes the current one.  body(tile,
-// descriptor, step) runs for the tiles of instances active at `step`
-// (start <= step < end); every branch on the descriptor is block-uniform.
+// fetches the next tile entry while it processes the current one.
+// body(tile, descriptor, step, lpar) runs for the tiles of instances active
+// at `step` (start <= step < end), the first global step of this launch
+// (lpar = parity of the global launch index); every branch on the descriptor
+// is block-uniform.
 template <typename Inst, typename Body>
 __device__ __forceinline__ void walk_tiles(const Inst* __restrict__ insts,
                                            const BatchTile* __restrict__ tiles, int ntiles,
-                                           long long step, unsigned char* raw, Body& body) {
+                                           long long step, int lpar, unsigned char* raw,
+                                           Body& body) {
     const Inst& sd = *reinterpret_cast<const Inst*>(raw);
     constexpr int kWords = (int)(sizeof(Inst) / 4);
     static_assert(sizeof(Inst) % 4 == 0, "descriptor must be word-sized");
@@ -101,7 +109,7 @@ __device__ __forceinline__ void walk_tiles(const Inst* __restrict__ insts,
             held = tile.inst;
         }
         if (step < sd.start || step >= sd.end) continue;  // block-uniform
-        body(tile, sd, step);
+        body(tile, sd, step, lpar);
     }
 }
 
@@ -112,8 +120,8 @@ struct CellTile {
     using CT = typename Codec<T>::CT;
     int tile_y;
     __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<CT>& sd,
-                                               long long step) const {
-        const int parity = (int)((step - sd.start) & 1);
+                                               long long, int lpar) const {
+        const int parity = lpar ^ (int)(sd.l0 & 1);
         const T* src = static_cast<const T*>(sd.buf[parity]);
         T* dst = static_cast<T*>(sd.buf[1 - parity]);
         const int plane = static_cast<int>(sd.plane);  // 9 * plane < 2^31 (checked on add)
@@ -157,8 +165,8 @@ template <typename T>
 struct PairTile {
     int tile_y;
     __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<F2>& sd,
-                                               long long step) const {
-        const int parity = (int)((step - sd.start) & 1);
+                                               long long, int lpar) const {
+        const int parity = lpar ^ (int)(sd.l0 & 1);
         const T* src = static_cast<const T*>(sd.buf[parity]);
         T* dst = static_cast<T*>(sd.buf[1 - parity]);
         const unsigned plane = static_cast<unsigned>(sd.plane);  // 9 * plane < 2^31 (checked on add)
@@ -191,74 +199,180 @@ struct PairTile {
     }
 };
 
-// One time step of every active instance, one cell per thread.
+// Two time steps per launch on 64 x 16 tiles through shared memory (the
+// single-lattice two-step tile), for the instances active at both global
+// steps; an instance whose budget ends after the first takes one step.
+template <typename T>
+struct TwoStepTile {
+    T* sm;
+    __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<F2>& sd,
+                                               long long step, int lpar) const {
+        const int parity = lpar ^ (int)(sd.l0 & 1);
+        const T* src = static_cast<const T*>(sd.buf[parity]);
+        T* dst = static_cast<T*>(sd.buf[1 - parity]);
+        const unsigned plane = static_cast<unsigned>(sd.plane);
+        const int nx = sd.nx, ny = sd.ny, pitch = sd.pitch;
+        const int rank = threadIdx.x;
+        if (step + 1 < sd.end) {  // block-uniform
+#define LBM_TB2_TILE(V, B) \
+    tb2_tile<T, V, B>(src, dst, nx, ny, pitch, plane, sd.k, sd.tx, sd.ty, tile.x0, tile.y0, sm, rank)
+            if (sd.bc == kPeriodic) {
+                switch (sd.variant) {
+                    case kTypeI: LBM_TB2_TILE(kTypeI, kPeriodic); break;
+                    case kTypeII: LBM_TB2_TILE(kTypeII, kPeriodic); break;
+                    case kTypeIII: LBM_TB2_TILE(kTypeIII, kPeriodic); break;
+                    case kViscous: LBM_TB2_TILE(kViscous, kPeriodic); break;
+                    default: LBM_TB2_TILE(kNone, kPeriodic); break;
+                }
+            } else {
+                switch (sd.variant) {
+                    case kTypeI: LBM_TB2_TILE(kTypeI, kDirichlet); break;
+                    case kTypeII: LBM_TB2_TILE(kTypeII, kDirichlet); break;
+                    case kTypeIII: LBM_TB2_TILE(kTypeIII, kDirichlet); break;
+                    case kViscous: LBM_TB2_TILE(kViscous, kDirichlet); break;
+                    default: LBM_TB2_TILE(kNone, kDirichlet); break;
+                }
+            }
+#undef LBM_TB2_TILE
+            return;
+        }
+        // the last step of the budget: one step on the tile's pairs
+        for (int p = rank; p < (kTbW / 2) * kTbH; p += kTbThreads) {
+            const int x = tile.x0 + 2 * (p % (kTbW / 2)), y = tile.y0 + p / (kTbW / 2);
+            if (x >= nx || y >= ny) continue;
+            const unsigned o = static_cast<unsigned>(y * pitch + x);
+            F2 v[9];
+            if (x > 0 && x + 2 < nx && y > 0 && y + 1 < ny)
+                pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch), o, v);
+            else if (sd.bc == kPeriodic)
+                pull_pair_edge<T, kPeriodic>(src, plane, pitch, x, y, nx, ny, v);
+            else
+                pull_pair_edge<T, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
+            switch (sd.variant) {
+                case kTypeI: collide_pair<kTypeI>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeII: collide_pair<kTypeII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeIII: collide_pair<kTypeIII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kViscous: collide_pair<kViscous>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                default: collide_pair<kNone>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+            }
+            if (x + 1 < nx)
+                store_pair<T>(dst, plane, o, v);
+            else
+                store_lo<T>(dst, plane, o, v);
+        }
+    }
+};
+
+// The global step and launch counters of a batch, advanced on the device after
+// each run of launches: counters[0] = step, counters[1] = launch.  A launch
+// within a run reads counters + its offsets.
+
+// One step of every active instance, one cell per thread.
 template <typename T>
 __global__ void __launch_bounds__(256, BatchMinBlocks<T>::value)
     batch_step_kernel(const BatchInst<typename Codec<T>::CT>* __restrict__ insts,
                       const BatchTile* __restrict__ tiles, const int* __restrict__ ntiles_p,
-                      const long long* __restrict__ step_p, int k_in_chunk, int tile_y) {
+                      const long long* __restrict__ counters, int step_off, int launch_off,
+                      int tile_y) {
     __shared__ __align__(16) unsigned char raw[sizeof(BatchInst<typename Codec<T>::CT>)];
-    // the previous step's grid must have finished before any buffer is touched
+    // the previous launch must have finished before any buffer is touched
     asm volatile("griddepcontrol.wait;" ::: "memory");
     CellTile<T> body{tile_y};
-    walk_tiles(insts, tiles, *ntiles_p, *step_p + k_in_chunk, raw, body);
+    walk_tiles(insts, tiles, *ntiles_p, counters[0] + step_off,
+               (int)((counters[1] + launch_off) & 1), raw,
+               body);
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
-// One time step of every active instance, two cells per thread.  At most 80
+// One step of every active instance, two cells per thread.  At most 80
 // registers (3 blocks per SM): left to itself the compiler keeps the packed
 // descriptor constants in registers across the tile's rows and needs 116.
 template <typename T>
 __global__ void __launch_bounds__(256, 3)
     batch_step2_kernel(const BatchInst<F2>* __restrict__ insts, const BatchTile* __restrict__ tiles,
-                       const int* __restrict__ ntiles_p, const long long* __restrict__ step_p,
-                       int k_in_chunk, int tile_y) {
+                       const int* __restrict__ ntiles_p, const long long* __restrict__ counters,
+                       int step_off, int launch_off, int tile_y) {
     __shared__ __align__(16) unsigned char raw[sizeof(BatchInst<F2>)];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     PairTile<T> body{tile_y};
-    walk_tiles(insts, tiles, *ntiles_p, *step_p + k_in_chunk, raw, body);
+    walk_tiles(insts, tiles, *ntiles_p, counters[0] + step_off,
+               (int)((counters[1] + launch_off) & 1), raw,
+               body);
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
-__global__ void advance_step_kernel(long long* step_p, int by) { *step_p += by; }
-
+// Two steps of every active instance per launch (64 x 16 tiles, 256 threads,
+// tb_smem_bytes<T>() of dynamic shared memory).
 template <typename T>
-const void* batch_kernel_ptr(int cells) {
+__global__ void __launch_bounds__(kTbThreads, 3)
+    batch_tb2_kernel(const BatchInst<F2>* __restrict__ insts, const BatchTile* __restrict__ tiles,
+                     const int* __restrict__ ntiles_p, const long long* __restrict__ counters,
+                     int step_off, int launch_off) {
+    __shared__ __align__(16) unsigned char raw[sizeof(BatchInst<F2>)];
+    extern __shared__ __align__(16) unsigned char tb_raw[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    TwoStepTile<T> body{reinterpret_cast<T*>(tb_raw)};
+    walk_tiles(insts, tiles, *ntiles_p, counters[0] + step_off,
+               (int)((counters[1] + launch_off) & 1), raw,
+               body);
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+__global__ void advance_counters_kernel(long long* counters, int steps, int launches) {
+    counters[0] += steps;
+    counters[1] += launches;
+}
+
+// Kernel of a batch: cells per thread 1 or 2, steps per launch 1 or 2 (2
+// needs cells == 2).
+template <typename T>
+const void* batch_kernel_ptr(int cells, int spl) {
+    if (spl == 2) return reinterpret_cast<const void*>(&batch_tb2_kernel<T>);
     if (cells == 2) return reinterpret_cast<const void*>(&batch_step2_kernel<T>);
     return reinterpret_cast<const void*>(&batch_step_kernel<T>);
 }
 template <>
-const void* batch_kernel_ptr<double>(int) {
+const void* batch_kernel_ptr<double>(int, int) {
     return reinterpret_cast<const void*>(&batch_step_kernel<double>);
 }
 
-// One batched step; cells = cells per thread (2: FP32 and 16-bit storage).
+template <typename T>
+size_t batch_smem(int spl) {
+    return spl == 2 ? tb_smem_bytes<T>() : 0;
+}
+
+// One batched launch: step_off / launch_off added to the device counters.
 template <typename T>
 cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int* ntiles,
-                           const long long* step, int k, int tile_x, int tile_y, int grid,
-                           int cells, cudaStream_t st, int pdl) {
+                           const long long* counters, int step_off, int launch_off, int tile_x,
+                           int tile_y, int grid, int cells, int spl, cudaStream_t st, int pdl) {
     using CT = typename Codec<T>::CT;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = cells == 2 ? dim3(tile_x / 2, 512 / tile_x) : dim3(tile_x, 256 / tile_x);
+    cfg.blockDim = spl == 2 ? dim3(kTbThreads)
+                 : cells == 2 ? dim3(tile_x / 2, 512 / tile_x) : dim3(tile_x, 256 / tile_x);
+    cfg.dynamicSmemBytes = batch_smem<T>(spl);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
+    const auto* ip2 = static_cast<const BatchInst<F2>*>(insts);
+    if (spl == 2)
+        return cudaLaunchKernelEx(&cfg, batch_tb2_kernel<T>, ip2, tiles, ntiles, counters,
+                                  step_off, launch_off);
     if (cells == 2)
-        return cudaLaunchKernelEx(&cfg, batch_step2_kernel<T>,
-                                  static_cast<const BatchInst<F2>*>(insts), tiles, ntiles, step, k,
-                                  tile_y);
-    return cudaLaunchKernelEx(&cfg, batch_step_kernel<T>,
-                              static_cast<const BatchInst<CT>*>(insts), tiles, ntiles, step, k,
-                              tile_y);
+        return cudaLaunchKernelEx(&cfg, batch_step2_kernel<T>, ip2, tiles, ntiles, counters,
+                                  step_off, launch_off, tile_y);
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel<T>, static_cast<const BatchInst<CT>*>(insts),
+                              tiles, ntiles, counters, step_off, launch_off, tile_y);
 }
 template <>
 cudaError_t launch_batch_t<double>(const void* insts, const BatchTile* tiles, const int* ntiles,
-                                   const long long* step, int k, int tile_x, int tile_y, int grid,
-                                   int, cudaStream_t st, int pdl) {
+                                   const long long* counters, int step_off, int launch_off,
+                                   int tile_x, int tile_y, int grid, int, int, cudaStream_t st,
+                                   int pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(tile_x, 256 / tile_x);
@@ -269,8 +383,8 @@ cudaError_t launch_batch_t<double>(const void* insts, const BatchTile* tiles, co
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, batch_step_kernel<double>,
-                              static_cast<const BatchInst<double>*>(insts), tiles, ntiles, step, k,
-                              tile_y);
+                              static_cast<const BatchInst<double>*>(insts), tiles, ntiles, counters,
+                              step_off, launch_off, tile_y);
 }
 
 }  // namespace lbm
@@ -293,6 +407,8 @@ struct Instance {
     int variant = 0, bc = 0;
     int64_t budget = 0;
     int64_t start = INT64_MAX;  // global step at which it started (after init)
+    int64_t l0 = 0;             // global launch index of its first launch
+    int64_t launched = 0;       // launches that advanced it (its buffer is launched & 1)
     Geometry geo{};
     size_t buf_bytes = 0, tab_bytes = 0;
     void* buf[2] = {nullptr, nullptr};
@@ -311,8 +427,10 @@ struct lbm_batch_ctx {
     bool custom_alloc = false;
     std::map<int, Instance> insts;
     int next_id = 0;
-    int64_t step = 0;  // global step (host mirror of *d_step)
-    int cpt = 1;       // cells per thread of the batched kernel (2 is the 16-bit default)
+    int64_t step = 0;      // global step (host mirror of d_counters[0])
+    int64_t launches = 0;  // global launch index (host mirror of d_counters[1])
+    int cpt = 1;           // cells per thread of the batched kernel (2 is the 16-bit default)
+    int spl = 1;           // time steps per launch (2 needs cpt == 2)
     int tile_x = 128, tile_y = 8;
     int grid = 0;
     // device tables
@@ -321,7 +439,7 @@ struct lbm_batch_ctx {
     BatchTile* d_tiles = nullptr;
     size_t tiles_cap = 0;  // entries
     int* d_ntiles = nullptr;
-    long long* d_step = nullptr;
+    long long* d_counters = nullptr;  // [0] global step, [1] global launch
     double* d_diag = nullptr;
     double* staging = nullptr;
     size_t staging_bytes = 0;
@@ -394,6 +512,7 @@ BatchInst<CT> desc_of(const Instance& in) {
     d.ty = static_cast<const A*>(in.tabs) + in.nx;
     d.start = in.initialised ? in.start : LLONG_MAX;
     d.end = in.initialised ? in.start + in.budget : LLONG_MAX;
+    d.l0 = in.l0;
     d.plane = in.geo.plane;
     d.nx = in.nx;
     d.ny = in.ny;
@@ -414,34 +533,69 @@ void drop_batch_graph(lbm_batch_ctx* b) {
     b->graph = nullptr;
 }
 
-cudaError_t launch_batch(lbm_batch_ctx* b, cudaStream_t st, int k, int pdl) {
+// One batched launch of `steps` (1 or 2) global steps; the offsets are added
+// to the device counters (pending advances of this run of launches).
+cudaError_t launch_batch(lbm_batch_ctx* b, cudaStream_t st, int steps, int step_off,
+                         int launch_off, int pdl) {
+    const int spl = steps == 2 ? 2 : 1;
+    // in two-step mode the tile table holds two-step tiles; a one-step launch
+    // covers them with the pair kernel
+    const int tx = b->spl == 2 ? lbm::kTbW : b->tile_x;
+    const int ty = b->spl == 2 ? lbm::kTbH : b->tile_y;
     switch (b->storage) {
         case LBM_F64:
-            return lbm::launch_batch_t<double>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
-                                               b->tile_x, b->tile_y, b->grid, 1, st, pdl);
+            return lbm::launch_batch_t<double>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
+                                               step_off, launch_off, tx, ty, b->grid, 1, 1, st,
+                                               pdl);
         case LBM_F32:
-            return lbm::launch_batch_t<float>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
-                                              b->tile_x, b->tile_y, b->grid, b->cpt, st, pdl);
+            return lbm::launch_batch_t<float>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
+                                              step_off, launch_off, tx, ty, b->grid, b->cpt, spl,
+                                              st, pdl);
         case LBM_F16DEV:
-            return lbm::launch_batch_t<__half>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_step, k,
-                                               b->tile_x, b->tile_y, b->grid, b->cpt, st, pdl);
+            return lbm::launch_batch_t<__half>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
+                                               step_off, launch_off, tx, ty, b->grid, b->cpt, spl,
+                                               st, pdl);
         default:
             return lbm::launch_batch_t<__nv_bfloat16>(b->d_insts, b->d_tiles, b->d_ntiles,
-                                                      b->d_step, k, b->tile_x, b->tile_y,
-                                                      b->grid, b->cpt, st, pdl);
+                                                      b->d_counters, step_off, launch_off, tx, ty,
+                                                      b->grid, b->cpt, spl, st, pdl);
+    }
+}
+
+// Count, for every instance, the launches among `count` launches of `d` steps
+// each, the first at global step step0, that advance it (those whose first
+// step lies in its window [start, start + budget)).
+void account(lbm_batch_ctx* b, int64_t step0, int d, int64_t count) {
+    auto ceil_div = [](int64_t a, int64_t q) { return a >= 0 ? (a + q - 1) / q : -((-a) / q); };
+    for (auto& kv : b->insts) {
+        Instance& in = kv.second;
+        if (!in.initialised) continue;
+        const int64_t lo = std::max<int64_t>(0, ceil_div(in.start - step0, d));
+        const int64_t hi = std::min<int64_t>(count, ceil_div(in.start + in.budget - step0, d));
+        if (hi > lo) in.launched += hi - lo;
     }
 }
 
 cudaError_t compute_grid(lbm_batch_ctx* b) {
     const void* fn = nullptr;
+    size_t smem = 0;
     switch (b->storage) {
-        case LBM_F64: fn = lbm::batch_kernel_ptr<double>(1); break;
-        case LBM_F32: fn = lbm::batch_kernel_ptr<float>(b->cpt); break;
-        case LBM_F16DEV: fn = lbm::batch_kernel_ptr<__half>(b->cpt); break;
-        default: fn = lbm::batch_kernel_ptr<__nv_bfloat16>(b->cpt); break;
+        case LBM_F64: fn = lbm::batch_kernel_ptr<double>(1, 1); break;
+        case LBM_F32:
+            fn = lbm::batch_kernel_ptr<float>(b->cpt, b->spl);
+            smem = lbm::batch_smem<float>(b->spl);
+            break;
+        case LBM_F16DEV:
+            fn = lbm::batch_kernel_ptr<__half>(b->cpt, b->spl);
+            smem = lbm::batch_smem<__half>(b->spl);
+            break;
+        default:
+            fn = lbm::batch_kernel_ptr<__nv_bfloat16>(b->cpt, b->spl);
+            smem = lbm::batch_smem<__nv_bfloat16>(b->spl);
+            break;
     }
     int per_sm = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e != cudaSuccess) return e;
     b->grid = std::max(1, per_sm * sms);
@@ -472,8 +626,10 @@ int sync_tables(lbm_batch_ctx* b) {
             std::memcpy(descs.data() + off, &d, ds);
         }
         if (!in.initialised) continue;
-        for (int y0 = 0; y0 < in.ny; y0 += b->tile_y)
-            for (int x0 = 0; x0 < in.nx; x0 += b->tile_x) tiles.push_back(BatchTile{di, x0, y0, 0});
+        const int tx = b->spl == 2 ? lbm::kTbW : b->tile_x;
+        const int ty = b->spl == 2 ? lbm::kTbH : b->tile_y;
+        for (int y0 = 0; y0 < in.ny; y0 += ty)
+            for (int x0 = 0; x0 < in.nx; x0 += tx) tiles.push_back(BatchTile{di, x0, y0, 0});
     }
     bool realloc = false;
     if (descs.size() > b->insts_cap) {
@@ -517,9 +673,11 @@ cudaError_t ensure_batch_graph(lbm_batch_ctx* b) {
     }
     e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < kBatchChunk && e == cudaSuccess; ++k) e = launch_batch(b, b->capture_stream, k, k > 0);
+    const int n = kBatchChunk / b->spl;  // launches per chunk
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+        e = launch_batch(b, b->capture_stream, b->spl, k * b->spl, k, k > 0);
     if (e == cudaSuccess) {
-        lbm::advance_step_kernel<<<1, 1, 0, b->capture_stream>>>(b->d_step, kBatchChunk);
+        lbm::advance_counters_kernel<<<1, 1, 0, b->capture_stream>>>(b->d_counters, kBatchChunk, n);
         e = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;
@@ -590,14 +748,14 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
         return LBM_ERR_CUDA;
     }
     b->d_ntiles = static_cast<int*>(bd_alloc(b, 256));
-    b->d_step = static_cast<long long*>(bd_alloc(b, 256));
+    b->d_counters = static_cast<long long*>(bd_alloc(b, 256));
     b->d_diag = static_cast<double*>(bd_alloc(b, sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag)));
-    if (!b->d_ntiles || !b->d_step || !b->d_diag) {
+    if (!b->d_ntiles || !b->d_counters || !b->d_diag) {
         lbm_batch_destroy(b);
         return LBM_ERR_OOM;
     }
     e = cudaMemsetAsync(b->d_ntiles, 0, sizeof(int), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(long long), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         lbm_batch_destroy(b);
@@ -634,6 +792,7 @@ int lbm_batch_set_cells_per_thread(lbm_batch b, int cells) {
     cudaStreamSynchronize(b->stream);
     drop_batch_graph(b);  // the captured launches name the other kernel
     b->cpt = cells;
+    if (cells == 1) b->spl = 1;
     b->dirty = true;      // the descriptors change type
     const cudaError_t e = compute_grid(b);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("grid: ") + cudaGetErrorString(e));
@@ -641,6 +800,24 @@ int lbm_batch_set_cells_per_thread(lbm_batch b, int cells) {
 }
 
 int lbm_batch_cells_per_thread(lbm_batch b) { return b ? b->cpt : LBM_ERR_ARG; }
+
+int lbm_batch_set_steps_per_launch(lbm_batch b, int steps) {
+    if (!b) return LBM_ERR_ARG;
+    if (steps != 1 && steps != 2) return bfail(b, LBM_ERR_ARG, "steps per launch must be 1 or 2");
+    if (steps == 2 && b->cpt != 2)
+        return bfail(b, LBM_ERR_ARG, "two steps per launch needs two cells per thread");
+    if (steps == b->spl) return LBM_OK;
+    BDeviceGuard dg(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_batch_graph(b);  // the captured launches name the other kernel
+    b->spl = steps;
+    b->dirty = true;      // the tile table changes shape
+    const cudaError_t e = compute_grid(b);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("grid: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_batch_steps_per_launch(lbm_batch b) { return b ? b->spl : LBM_ERR_ARG; }
 
 int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double uy0,
                   const lbm_rates* rates, lbm_bc bc, lbm_variant variant, const double* chi_x,
@@ -765,6 +942,8 @@ int lbm_batch_init_equilibrium(lbm_batch b, int id, const double* rho, const dou
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_init_equilibrium: ") + cudaGetErrorString(e));
     in->initialised = true;
     in->start = b->step;
+    in->l0 = b->launches;
+    in->launched = 0;
     b->dirty = true;
     return LBM_OK;
 }
@@ -784,6 +963,8 @@ int lbm_batch_init_pulse(lbm_batch b, int id, double eps, double half_width, dou
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_init_pulse: ") + cudaGetErrorString(e));
     in->initialised = true;
     in->start = b->step;
+    in->l0 = b->launches;
+    in->launched = 0;
     b->dirty = true;
     return LBM_OK;
 }
@@ -801,22 +982,32 @@ int lbm_batch_step(lbm_batch b, int nsteps) {
     if (cs == cudaStreamCaptureStatusNone && nsteps >= kBatchChunk) {
         e = ensure_batch_graph(b);
         if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+        const int n = kBatchChunk / b->spl;
         while (nsteps >= kBatchChunk) {
             e = cudaGraphLaunch(b->graph, b->stream);
             if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+            account(b, b->step, b->spl, n);
             b->step += kBatchChunk;
+            b->launches += n;
             nsteps -= kBatchChunk;
         }
     }
-    for (int k = 0; k < nsteps; ++k) {
-        e = launch_batch(b, b->stream, k, k > 0);
+    int step_off = 0, launch_off = 0;
+    while (nsteps > 0) {
+        const int d = (b->spl == 2 && nsteps >= 2) ? 2 : 1;
+        e = launch_batch(b, b->stream, d, step_off, launch_off, launch_off > 0);
         if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+        account(b, b->step + step_off, d, 1);
+        step_off += d;
+        ++launch_off;
+        nsteps -= d;
     }
-    if (nsteps > 0) {
-        lbm::advance_step_kernel<<<1, 1, 0, b->stream>>>(b->d_step, nsteps);
+    if (launch_off > 0) {
+        lbm::advance_counters_kernel<<<1, 1, 0, b->stream>>>(b->d_counters, step_off, launch_off);
         e = cudaGetLastError();
         if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch advance: ") + cudaGetErrorString(e));
-        b->step += nsteps;
+        b->step += step_off;
+        b->launches += launch_off;
     }
     return LBM_OK;
 }
@@ -842,7 +1033,7 @@ int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* 
         dx = ux ? b->staging + n : nullptr;
         dy = uy ? b->staging + 2 * n : nullptr;
     }
-    const int cur = (int)(inst_time(b, *in) & 1);
+    const int cur = (int)(in->launched & 1);
     cudaError_t e = lbm::launch_moments(b->storage, in->buf[cur], in->geo,
                                         lbm::BaseState{in->rho0, in->ux0, in->uy0}, in->bc, dr, dx, dy,
                                         b->stream);
@@ -864,7 +1055,7 @@ int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, d
     if (x0 < 0 || y0 < 0 || x1 > in->nx || y1 > in->ny || x0 > x1 || y0 > y1)
         return bfail(b, LBM_ERR_ARG, "region outside the lattice");
     BDeviceGuard dg(b->device);
-    const int cur = (int)(inst_time(b, *in) & 1);
+    const int cur = (int)(in->launched & 1);
     double* res = b->d_diag + lbm::kDiagBlocks * lbm::kDiag;
     cudaError_t e = lbm::launch_diagnostics(b->storage, in->buf[cur], in->geo,
                                             lbm::BaseState{in->rho0, in->ux0, in->uy0}, in->bc, x0,
@@ -908,7 +1099,7 @@ void lbm_batch_destroy(lbm_batch b) {
     bd_free(b, b->d_insts, b->insts_cap);
     bd_free(b, b->d_tiles, b->tiles_cap * sizeof(BatchTile));
     bd_free(b, b->d_ntiles, 256);
-    bd_free(b, b->d_step, 256);
+    bd_free(b, b->d_counters, 256);
     bd_free(b, b->d_diag, sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag));
     bd_free(b, b->staging, b->staging_bytes);
     delete b;

@@ -93,3 +93,15 @@ def test_rates_struct_layout_matches_header():
 
     assert ctypes.sizeof(lbm.lbm_rates) == 11 * 8
     assert ctypes.sizeof(lbm.lbm_allocator) == 3 * ctypes.sizeof(ctypes.c_void_p)
+
+
+def test_autotuner_configurations_cover_every_batched_kernel():
+    from paper_1203_6350_gb300 import autotune
+
+    f32 = autotune.configurations("f32")
+    kernels = {(c, s) for c, s, _, _ in f32}
+    assert kernels == {(1, 1), (2, 1), (2, 2)}
+    assert [t for c, s, *t in f32 if s == 2] == [list(autotune.TWO_STEP_TILE)]
+    assert {(c, s) for c, s, _, _ in autotune.configurations("f64")} == {(1, 1)}
+    # the signature ignores order and buckets sizes by powers of two
+    assert autotune.signature([(100, 60), (64, 33)]) == autotune.signature([(70, 40), (127, 63)])

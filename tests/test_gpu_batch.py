@@ -85,13 +85,16 @@ def test_batch_equals_single_lattice(storage):
                 _close(a, c, 0 if storage == "f64" else TOL[storage])
 
 
-def _batch_run(works, storage, tiling=None, steps=100, cells=None):
+def _batch_run(works, storage, tiling=None, steps=100, cells=None, per_launch=None):
     from paper_1203_6350_gb300.batch import Batch
 
     with Batch(storage, tiling=tiling) as b:
         if cells is not None:
             b.cells_per_thread = cells
             assert b.cells_per_thread == cells
+        if per_launch is not None:
+            b.steps_per_launch = per_launch
+            assert b.steps_per_launch == per_launch
         ids = [b.add_workload(w) for w in works]
         b.step(steps)
         return [b.moments(i)[0] for i in ids]
@@ -181,3 +184,97 @@ def test_batch_against_the_oracle():
     # 1e-10 relative plus the oracle's own FP64 rounding (~10 x 2^-53 per cell per step)
     floor = 10 * 121 * 2.0**-53 * np.sqrt(ref.size)
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref) + floor, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16dev"])
+def test_two_steps_per_batched_launch(storage):
+    """Temporal blocking in the batch: budgets of 40, 57, 74, 91, 108 and 125
+    steps (odd budgets end on a one-step half of a two-step launch), stepped
+    131 steps (four 32-step graphs, one two-step and one one-step launch),
+    against one step per launch at the format's rounding level, and the step
+    counters."""
+    from paper_1203_6350_gb300.batch import Batch
+
+    works = _mixed_workloads(storage)
+    tol = {"f32": 1e-5, "f16dev": 1e-2}[storage]
+    one = _batch_run(works, storage, steps=131, cells=2, per_launch=1)
+    two = _batch_run(works, storage, steps=131, cells=2, per_launch=2)
+    for a, c in zip(two, one):
+        _close(a, c, tol)
+    with Batch(storage) as b:
+        b.cells_per_thread = 2
+        b.steps_per_launch = 2
+        ids = [b.add_workload(w) for w in works]
+        b.step(131)
+        for i, w in zip(ids, works):
+            assert b.time(i) == w.steps
+
+
+def test_two_step_batch_alone_equals_in_the_mix_and_staggered():
+    """Two-step launches: a lattice alone and in the mix are bit-identical;
+    instances admitted mid-run, at odd global steps, with odd budgets, end with
+    the single-lattice result (rounding level) and their own step counts."""
+    from paper_1203_6350_gb300.batch import Batch
+
+    works = _mixed_workloads("f32")
+    mixed = _batch_run(works, "f32", cells=2, per_launch=2)
+    for w, m in zip(works, mixed):
+        (alone,) = _batch_run([w], "f32", cells=2, per_launch=2)
+        np.testing.assert_array_equal(alone, m)
+    with Batch("f32") as b:
+        b.cells_per_thread = 2
+        b.steps_per_launch = 2
+        a = b.add_workload(works[2].with_(steps=91))
+        b.step(21)  # ends on a one-step launch: the global step is now odd
+        c = b.add_workload(works[5].with_(steps=51))
+        d = b.add_workload(works[0].with_(steps=200))
+        b.step(33)
+        b.remove(d)
+        e = b.add_workload(works[1].with_(steps=7))
+        b.step(65)
+        assert b.time(a) == 91 and b.time(c) == 51 and b.time(e) == 7
+        for i, w, n in ((a, works[2], 91), (c, works[5], 51), (e, works[1], 7)):
+            _close(b.moments(i)[0], _single(w, "f32", n)[0], TOL["f32"])
+
+
+def test_steps_per_launch_of_a_batch():
+    from paper_1203_6350_gb300 import lbm
+    from paper_1203_6350_gb300.batch import Batch
+
+    with Batch("f32") as b:
+        assert b.steps_per_launch == 1
+        assert lbm.lbm_batch_set_steps_per_launch(b.b, 2) == lbm.LBM_ERR_ARG  # needs pairs
+        b.cells_per_thread = 2
+        b.steps_per_launch = 2
+        assert b.steps_per_launch == 2
+        b.cells_per_thread = 1
+        assert b.steps_per_launch == 1
+        for bad in (0, 3):
+            assert lbm.lbm_batch_set_steps_per_launch(b.b, bad) == lbm.LBM_ERR_ARG
+    with Batch("f64") as b:
+        assert lbm.lbm_batch_set_steps_per_launch(b.b, 2) == lbm.LBM_ERR_ARG
+
+
+def test_autotuner_picks_a_kernel_and_tile(tmp_path, monkeypatch):
+    """The autotuner times every (cells per thread, steps per launch, tile)
+    configuration on the shape set, caches the fastest, and a batch built from
+    it steps to the same result as the default batch (rounding level)."""
+    from paper_1203_6350_gb300 import autotune
+
+    monkeypatch.setenv("LBM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    works = _mixed_workloads("f32")
+    shapes = [(w.nx, w.ny) for w in works]
+    configs = [(1, 1, 64, 8), (2, 1, 128, 16), (2, 2) + autotune.TWO_STEP_TILE]
+    cfg = autotune.tuned_config(shapes, "f32", configs=configs)
+    assert (cfg["cells"], cfg["steps_per_launch"]) + tuple(cfg["tile"]) in configs
+    assert autotune.tuned_config(shapes, "f32") == cfg  # served from the cache
+    from paper_1203_6350_gb300.batch import Batch
+
+    with Batch("f32", config=cfg) as b:
+        assert b.cells_per_thread == cfg["cells"]
+        assert b.steps_per_launch == cfg["steps_per_launch"]
+        ids = [b.add_workload(w) for w in works]
+        b.step(100)
+        got = [b.moments(i)[0] for i in ids]
+    for a, c in zip(got, _batch_run(works, "f32")):
+        _close(a, c, TOL["f32"])
