@@ -654,7 +654,7 @@ def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
     small = [j.id for j in jobs if j.workload.cells * j.workload.steps <= 3e8]
     n_sample = max(1, int(math.ceil(0.01 * len(jobs))))
     sample = set(int(x) for x in rng.choice(small, size=min(n_sample, len(small)), replace=False))
-    srv = Server(hbm_budget=budget, chunk=32, keep_fields=sample)
+    srv = Server(hbm_budget=budget, chunk=64, keep_fields=sample)
     t0 = time.perf_counter()
     done = srv.run(copy.deepcopy(jobs))
     wall = time.perf_counter() - t0

@@ -307,11 +307,18 @@ int64_t lbm_batch_time(lbm_batch b, int id);
 int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* uy, int on_device);
 int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, double out[6]);
 
-/* Remove instance id and free its buffers (synchronises the stream). */
+/* Remove instance id.  Its buffers are released once the launches issued
+ * before the call have completed (an event recorded now, checked on later
+ * calls and at lbm_batch_destroy); the call itself does not wait. */
 int lbm_batch_remove(lbm_batch b, int id);
 
 /* Number of instances in the batch (-1 for NULL). */
 int lbm_batch_count(lbm_batch b);
+
+/* Replace the batch's stream (borrowed).  Later calls on the batch issue
+ * their work there; work already issued stays where it was.  A caller that
+ * moves the batch between streams orders them (events) itself. */
+int lbm_batch_set_stream(lbm_batch b, void* cuda_stream);
 
 /* Message of the last error on b. */
 const char* lbm_batch_last_error(lbm_batch b);

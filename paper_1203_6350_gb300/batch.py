@@ -45,6 +45,12 @@ class Batch:
             warnings.warn(f"liblbm warning {rc} in {what}", RuntimeWarning, stacklevel=3)
         return rc
 
+    def set_stream(self, stream) -> None:
+        """Issue later work on `stream` (a torch.cuda.Stream); the caller orders
+        it after work already issued on the old one."""
+        self._check(lbm.lbm_batch_set_stream(self.b, stream.cuda_stream), "lbm_batch_set_stream")
+        self.stream = stream
+
     def set_tiling(self, tile_x: int, tile_y: int) -> None:
         self._check(lbm.lbm_batch_set_tiling(self.b, tile_x, tile_y), "lbm_batch_set_tiling")
 

@@ -413,6 +413,7 @@ struct Instance {
     size_t buf_bytes = 0, tab_bytes = 0;
     void* buf[2] = {nullptr, nullptr};
     void* tabs = nullptr;  // AxisCoef x table followed by y table
+    std::vector<unsigned char> tabs_host;  // the tables' host image (source of the upload)
     int bulk[4] = {0, 0, 0, 0};  // rectangle [x0, x1) x [y0, y1) where chi = 0
     bool initialised = false;
 };
@@ -445,6 +446,18 @@ struct lbm_batch_ctx {
     size_t staging_bytes = 0;
     std::vector<int> dense;  // dense index -> instance id
     bool dirty = true;
+    // host images of the device tables, kept as the source of their uploads
+    std::vector<unsigned char> h_descs;
+    std::vector<BatchTile> h_tiles;
+    int h_ntiles = 0;
+    // buffers of removed instances, freed once the launches issued before the
+    // removal have completed (their event), so that removal never waits
+    struct Retired {
+        void* p;
+        size_t bytes;
+        cudaEvent_t ev;
+    };
+    std::vector<Retired> retired;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture_stream = nullptr;
     std::string err;
@@ -475,6 +488,34 @@ void bd_free(lbm_batch_ctx* b, void* p, size_t bytes) {
         b->alloc.free(p, bytes, b->alloc.ctx);
     else
         cudaFree(p);
+}
+
+// Free the buffers of removed instances whose removal event has completed
+// (all of them with wait = true, after the stream has drained).  Entries are
+// grouped: an entry with an event is followed by the other buffers of the
+// same instance (event nullptr).
+void reap(lbm_batch_ctx* b, bool wait) {
+    if (wait) cudaStreamSynchronize(b->stream);
+    std::vector<lbm_batch_ctx::Retired> keep;
+    bool done = true;
+    for (auto& r : b->retired) {
+        if (r.ev) {
+            const cudaError_t q = cudaEventQuery(r.ev);
+            done = wait || q == cudaSuccess;
+            if (q != cudaSuccess && q != cudaErrorNotReady) cudaGetLastError();
+            if (done) {
+                cudaEventDestroy(r.ev);
+                r.ev = nullptr;
+                bd_free(b, r.p, r.bytes);
+                continue;
+            }
+        } else if (done) {
+            bd_free(b, r.p, r.bytes);
+            continue;
+        }
+        keep.push_back(r);
+    }
+    b->retired.swap(keep);
 }
 
 struct BDeviceGuard {
@@ -606,8 +647,10 @@ cudaError_t compute_grid(lbm_batch_ctx* b) {
 int sync_tables(lbm_batch_ctx* b) {
     if (!b->dirty) return LBM_OK;
     b->dense.clear();
-    std::vector<unsigned char> descs;
-    std::vector<BatchTile> tiles;
+    std::vector<unsigned char>& descs = b->h_descs;
+    std::vector<BatchTile>& tiles = b->h_tiles;
+    descs.clear();
+    tiles.clear();
     const size_t ds = desc_size(b->storage, b->cpt);
     for (auto& kv : b->insts) {
         const Instance& in = kv.second;
@@ -655,10 +698,11 @@ int sync_tables(lbm_batch_ctx* b) {
     if (e == cudaSuccess && !tiles.empty())
         e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile),
                             cudaMemcpyHostToDevice, b->stream);
-    const int nt = static_cast<int>(tiles.size());
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ntiles, &nt, sizeof(int), cudaMemcpyHostToDevice, b->stream);
-    // the host vectors die here: make sure the copies have consumed them
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->h_ntiles = static_cast<int>(tiles.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_ntiles, &b->h_ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    // Stream-ordered after the launches that read the old tables.  The host
+    // images live in the context, so nothing here waits for the device.
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(e));
     b->dirty = false;
     return LBM_OK;
@@ -879,8 +923,10 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
     }
     const double nn = rates->n, mm = rates->m;
     cudaError_t e;
+    // The host image stays with the instance, so the upload needs no wait.
+    in.tabs_host.assign(in.tab_bytes, 0);
     if (b->storage == LBM_F64) {
-        std::vector<double> t(4 * (size_t)(nx + ny));
+        double* t = reinterpret_cast<double*>(in.tabs_host.data());
         for (int i = 0; i < nx + ny; ++i) {
             const double c = i < nx ? chi_x[i] : chi_y[i - nx];
             t[4 * i] = c;
@@ -888,10 +934,8 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
             t[4 * i + 2] = 1.0 / (1.0 + mm * c);
             t[4 * i + 3] = 0.0;
         }
-        e = cudaMemcpyAsync(in.tabs, t.data(), in.tab_bytes, cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     } else {
-        std::vector<float> t(4 * (size_t)(nx + ny));
+        float* t = reinterpret_cast<float*>(in.tabs_host.data());
         for (int i = 0; i < nx + ny; ++i) {
             const double c = i < nx ? chi_x[i] : chi_y[i - nx];
             t[4 * i] = (float)c;
@@ -899,9 +943,8 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
             t[4 * i + 2] = (float)(1.0 / (1.0 + mm * c));
             t[4 * i + 3] = 0.0f;
         }
-        e = cudaMemcpyAsync(in.tabs, t.data(), in.tab_bytes, cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     }
+    e = cudaMemcpyAsync(in.tabs, in.tabs_host.data(), in.tab_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) {
         bd_free(b, in.buf[0], in.buf_bytes);
         bd_free(b, in.buf[1], in.buf_bytes);
@@ -1072,16 +1115,32 @@ int lbm_batch_remove(lbm_batch b, int id) {
     Instance* in = find(b, id);
     if (!in) return bfail(b, LBM_ERR_ARG, "unknown instance");
     BDeviceGuard dg(b->device);
-    cudaStreamSynchronize(b->stream);  // no launch may still use its buffers
-    bd_free(b, in->buf[0], in->buf_bytes);
-    bd_free(b, in->buf[1], in->buf_bytes);
-    bd_free(b, in->tabs, in->tab_bytes);
+    // launches already issued may still read its buffers: free them once an
+    // event recorded now has completed (checked here and on later calls)
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, b->stream);
+    if (e != cudaSuccess) {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+        cudaStreamSynchronize(b->stream);  // fall back to waiting
+    }
+    b->retired.push_back({in->buf[0], in->buf_bytes, ev});
+    b->retired.push_back({in->buf[1], in->buf_bytes, nullptr});
+    b->retired.push_back({in->tabs, in->tab_bytes, nullptr});
     b->insts.erase(id);
     b->dirty = true;
+    reap(b, false);
     return LBM_OK;
 }
 
 int lbm_batch_count(lbm_batch b) { return b ? static_cast<int>(b->insts.size()) : -1; }
+
+int lbm_batch_set_stream(lbm_batch b, void* cuda_stream) {
+    if (!b) return LBM_ERR_ARG;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LBM_OK;
+}
 
 const char* lbm_batch_last_error(lbm_batch b) { return b ? b->err.c_str() : ""; }
 
@@ -1089,6 +1148,7 @@ void lbm_batch_destroy(lbm_batch b) {
     if (!b) return;
     BDeviceGuard dg(b->device);
     cudaStreamSynchronize(b->stream);
+    reap(b, true);
     drop_batch_graph(b);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     for (auto& kv : b->insts) {

@@ -112,6 +112,7 @@ SIGNATURES = [
                                              ctypes.c_int, ctypes.c_int, _vp]),
     ("lbm_batch_remove", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_batch_count", ctypes.c_int, [_vp]),
+    ("lbm_batch_set_stream", ctypes.c_int, [_vp, _vp]),
     ("lbm_batch_last_error", ctypes.c_char_p, [_vp]),
     ("lbm_batch_destroy", None, [_vp]),
 ]
@@ -335,6 +336,10 @@ def lbm_batch_count(b) -> int:
     return int(load().lbm_batch_count(b))
 
 
+def lbm_batch_set_stream(b, stream) -> int:
+    return load().lbm_batch_set_stream(b, stream)
+
+
 def lbm_batch_last_error(b) -> str:
     return (load().lbm_batch_last_error(b) or b"").decode()
 
@@ -429,6 +434,12 @@ class Lattice:
         else:
             lat.init_equilibrium(*w.initial_fields())
         return lat
+
+    def set_stream(self, stream) -> None:
+        """Issue later work on `stream` (a torch.cuda.Stream); the caller orders
+        it after work already issued on the old one."""
+        check(lbm_set_stream(self.h, stream.cuda_stream), self.h, "lbm_set_stream")
+        self.stream = stream
 
     def init_pulse(self, eps: float, half_width: float, x0: float, y0: float) -> None:
         check(lbm_init_pulse(self.h, eps, half_width, x0, y0), self.h, "lbm_init_pulse")

@@ -32,6 +32,7 @@ class Job:
     workload: object            # workloads.Workload (its storage field selects the format)
     arrival: float = 0.0        # seconds after the start of the run
     admitted: Optional[float] = None
+    admitted_round: int = 0
     finished: Optional[float] = None
     result: Optional[np.ndarray] = None   # lbm diagnostics over the layer-free interior
     field: Optional[np.ndarray] = None    # final rho' (when the server keeps fields)
@@ -55,7 +56,7 @@ class Server:
     def __init__(self, hbm_budget: float = 150e9, chunk: int = 64, keep_fields=False,
                  tiling: Optional[tuple] = None, device: int = 0, stream=None,
                  max_resident_cells: Optional[int] = 4 << 20, init: str = "pulse",
-                 solo_cells: Optional[int] = 1 << 20):
+                 solo_cells: Optional[int] = 1 << 20, batch_config: Optional[dict] = None):
         """hbm_budget: device bytes the resident jobs may hold.  max_resident_cells:
         slot limit -- jobs are admitted while the resident lattices hold fewer
         cells than this (enough to keep the GPU's bandwidth busy; more only
@@ -65,7 +66,12 @@ class Server:
         through the single-lattice kernel (chunk by chunk, interleaved on the
         same stream with the batched launch of the smaller resident jobs); None
         sends every job through the batch.  A job's path depends only on its
-        size, so its result does not depend on what else is resident."""
+        size, so its result does not depend on what else is resident.
+        batch_config: kernel of the batched launches ({"cells", "steps_per_launch",
+        "tile"}, as autotune.tuned_config gives); default: two cells per thread
+        and two steps per launch for FP32 and 16-bit storage (the fastest on
+        the mixed-size 256-lattice workload), the batch default for FP64;
+        tiling overrides the tile of one-step launches."""
         import torch
 
         self.torch = torch
@@ -77,19 +83,25 @@ class Server:
         self.chunk = int(chunk)
         self.keep_fields = keep_fields
         self.tiling = tiling
+        self.batch_config = batch_config
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        self.side = torch.cuda.Stream(device)  # set-up and read-out, off the stepping stream
         self.batches = {}
         self.pending = deque()
         self.resident = {}  # job id -> (storage, instance id, job)
         self.used = 0
         self.done = []
         self.steps_run = 0
+        self.round = 0
 
     def _batch(self, storage) -> Batch:
         if storage not in self.batches:
+            cfg = self.batch_config
+            if cfg is None and storage != "f64":
+                cfg = {"cells": 2, "steps_per_launch": 2, "tile": self.tiling or (64, 16)}
             self.batches[storage] = Batch(storage, stream=self.stream, device=self.device,
-                                          tiling=self.tiling)
+                                          tiling=self.tiling, config=cfg)
         return self.batches[storage]
 
     def submit(self, job: Job) -> None:
@@ -106,8 +118,12 @@ class Server:
             job = self.pending.popleft()
             w = job.workload
             if self.solo_cells is not None and w.cells >= self.solo_cells:
-                lat = lbm.Lattice.from_workload(w, init=self.init, stream=self.stream,
+                # created and initialised on the side stream (lbm_create waits for
+                # its stream), then handed to the stepping stream
+                lat = lbm.Lattice.from_workload(w, init=self.init, stream=self.side,
                                                 device=self.device)
+                self.stream.wait_stream(self.side)
+                lat.set_stream(self.stream)
                 self.resident[job.id] = ("solo", lat, job)
             else:
                 b = self._batch(w.storage)
@@ -116,52 +132,78 @@ class Server:
             self.used += job.bytes
             self.cells += w.cells
             job.admitted = now
+            job.admitted_round = self.round
             n += 1
         return n
 
-    def retire(self, clock) -> int:
-        n = 0
-        for jid, (st, i, job) in list(self.resident.items()):
+    def _complete(self, st, h, job) -> bool:
+        """Has every step of the job been issued?"""
+        t = h.time if st == "solo" else self.batches[st].time(h)
+        return t >= job.workload.steps
+
+    def retire(self, clock, ids, after) -> int:
+        """Read out and release the jobs `ids`, whose last steps were issued
+        before the event `after`.  The read-out runs on the side stream, which
+        waits for `after` only, so the chunk issued since keeps the GPU busy
+        while the host waits for the results."""
+        if not ids:
+            return 0
+        if after is not None:
+            self.side.wait_event(after)
+        else:
+            self.side.wait_stream(self.stream)
+        for jid in ids:
+            st, h, job = self.resident.pop(jid)
             keep = self.keep_fields
             keep = keep is True or (isinstance(keep, (set, frozenset)) and job.id in keep)
             if st == "solo":
-                if i.time < job.workload.steps:
-                    continue
-                job.result = i.diagnostics(interior(job.workload))
+                h.set_stream(self.side)
+                job.result = h.diagnostics(interior(job.workload))
                 if keep:
-                    job.field = i.moments()[0]
-                i.close()
+                    job.field = h.moments()[0]
+                h.close()  # waits for the side stream only
             else:
                 b = self.batches[st]
-                if b.time(i) < job.workload.steps:
-                    continue
-                job.result = b.diagnostics(i, interior(job.workload))
+                b.set_stream(self.side)
+                job.result = b.diagnostics(h, interior(job.workload))
                 if keep:
-                    job.field = b.moments(i)[0]
-                b.remove(i)
+                    job.field = b.moments(h)[0]
+                b.set_stream(self.stream)
+                b.remove(h)  # freed once the launches issued so far have completed
             self.used -= job.bytes
             self.cells -= job.workload.cells
-            del self.resident[jid]
             job.finished = clock()
             self.done.append(job)
-            n += 1
-        return n
+        return len(ids)
 
-    def advance(self) -> None:
+    def advance(self) -> bool:
+        """Issue one chunk of steps for every resident job that still needs
+        steps; False if none does."""
+        busy = False
         with self.torch.cuda.stream(self.stream):
             for st, b in self.batches.items():
-                if len(b):
+                if len(b) and any(s == st and not self._complete(s, h, j)
+                                  for s, h, j in self.resident.values()):
                     b.step(self.chunk)
+                    busy = True
             for st, lat, job in self.resident.values():
                 if st == "solo":
                     n = min(self.chunk, job.workload.steps - lat.time)
                     if n > 0:
                         lat.step(n)
-        self.steps_run += self.chunk
+                        busy = True
+        if busy:
+            self.steps_run += self.chunk
+        return busy
 
     def run(self, jobs, realtime: bool = True):
         """Serve `jobs` (sorted by arrival).  realtime: arrivals follow the wall
-        clock; otherwise every job is submitted at once in arrival order."""
+        clock; otherwise every job is submitted at once in arrival order.
+
+        Each round: admit what fits, note the resident jobs whose steps have all
+        been issued, issue the next chunk for the others, then read out and
+        release the noted ones (on the side stream, behind the event of the
+        previous chunk)."""
         jobs = sorted(jobs, key=lambda j: j.arrival)
         t0 = time.perf_counter()
 
@@ -169,19 +211,29 @@ class Server:
             return time.perf_counter() - t0
 
         k = 0
+        prev = None  # event after the last chunk issued
         while k < len(jobs) or self.pending or self.resident:
             now = clock()
             while k < len(jobs) and (not realtime or jobs[k].arrival <= now):
                 self.submit(jobs[k])
                 k += 1
+            self.round += 1
             self.admit(now)
             if not self.resident:
                 if k < len(jobs) and realtime:
                     time.sleep(max(0.0, jobs[k].arrival - clock()))
                 continue
+            # jobs admitted this round are read out next round at the earliest, so
+            # that the read-out is ordered after their initialisation
+            finished = [jid for jid, (st, h, job) in self.resident.items()
+                        if job.admitted_round < self.round and self._complete(st, h, job)]
             self.advance()
-            self.retire(clock)
+            ev = self.torch.cuda.Event()
+            ev.record(self.stream)  # also covers this round's initialisations
+            self.retire(clock, finished, prev)
+            prev = ev
         self.stream.synchronize()
+        self.side.synchronize()
         return self.done
 
     def close(self) -> None:

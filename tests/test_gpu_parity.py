@@ -309,6 +309,39 @@ def test_roofline_sweep_2048_error(storage):
     assert_close(got, _big_ref["ref"], TOL[storage], w.steps, storage)
 
 
+@pytest.mark.parametrize("side,storage", [(16384, "f32"), (8192, "f16dev"), (4096, "bf16dev"),
+                                          (2048, "f32")])
+def test_full_size_sweep_lattice_window_against_the_oracle(side, storage):
+    """Roofline-sweep lattices at full size, in the launch configuration the
+    library picks for them (two steps per launch, as the sweep times them):
+    the centred eps = 1e-3, b = 5 pulse after 60 steps, compared in the central
+    200 x 200 window with the oracle on a 400 x 400 lattice holding the same
+    pulse at its centre.  A signal moves at most one cell per step, so after 60
+    steps the window depends only on cells within 160 of the centre; those are
+    inside the big lattice's chi = 0 core and 200 cells from the small
+    lattice's edge, with the same initial data on both (the Gaussian tail at
+    160 cells is below 1e-300)."""
+    from paper_1203_6350_gb300 import lbm
+
+    steps, half, win = 60, 200, 100
+    big = wl.quiescent(side, storage=storage, steps=steps, width=128, pulse=True)
+    with lbm.Lattice.from_workload(big, init="pulse") as lat:
+        assert lat.steps_per_launch == (2 if side >= 2048 else 1)
+        lat.step(steps)
+        fields = lat.moments(device=True)
+        c = side // 2
+        got = [f[c - win:c + win, c - win:c + win].cpu().numpy() for f in fields]
+        del fields
+    small = wl.pulse_workload(2 * half, 2 * half, variant=big.variant, storage="f64", eps=1e-3,
+                              b=5.0, width=0, chi_max=0.0, steps=steps, name="window")
+    ref = run_oracle(small)
+    c = half
+    ref = [r[c - win:c + win, c - win:c + win] for r in ref]
+    assert_close(got[0], ref[0], TOL[storage], steps, storage)
+    for g, r in zip(got[1:], ref[1:]):
+        assert_close(g, r, TOL[storage], steps, storage)
+
+
 def test_quiescent_lattice_stays_exactly_at_rest():
     """A medium at rest with q_ref = the far field is a fixed point: every deviation
     stays exactly zero at any size (here 4096^2, 20 steps, FP32 and FP16)."""
