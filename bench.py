@@ -388,8 +388,8 @@ def with_warn(fn):
         return fn()
 
 
-KERNEL_SOURCES = ("d2q9_cell.cuh", "lbm_step.cuh", "step_f32.cu", "lbm_step2.cuh", "step2_f32.cu",
-                  "lbm_internal.h")
+KERNEL_SOURCES = ("d2q9_cell.cuh", "lbm_step.cuh", "step_f32.cu", "lbm_step2.cuh", "lbm_step_tb.cuh",
+                  "step2_f32.cu", "lbm_internal.h")
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step2_kernel_f32_meanflow_1024x1024_traffic.md")
 
 

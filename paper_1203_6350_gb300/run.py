@@ -4,8 +4,9 @@
 
 Square lattice at rest (optionally with a centred pulse) with a ramped
 absorbing layer; prints one JSON line with MLUPS, algorithmic GB/s
-(bytes/cell/step x cells x steps / time) and the fraction of the measured HBM
-copy bandwidth.  Timing uses CUDA events on the lattice's stream after
+(bytes/cell per launch x cells x launches / time: one launch moves each
+population in and out once, whether it advances one time step or two) and
+the fraction of the measured HBM copy bandwidth.  Timing uses CUDA events on the lattice's stream after
 warm-up steps; the state is larger than L2 for sides >= 2048 in FP32.
 """
 from __future__ import annotations
@@ -34,6 +35,10 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0,
                     help="run this many copies of the lattice through the batched path")
     ap.add_argument("--tile", default=None, help="batched tile shape, e.g. 128x16")
+    ap.add_argument("--cells", type=int, default=None, choices=[1, 2],
+                    help="cells per thread (default: the library's choice)")
+    ap.add_argument("--per-launch", type=int, default=None, choices=[1, 2],
+                    help="time steps per launch (default: the library's choice)")
     args = ap.parse_args(argv)
 
     import torch
@@ -54,6 +59,11 @@ def main(argv=None):
             ids = [lat.add_workload(w, steps=1 << 40, init="pulse") for _ in range(copies)]
         else:
             lat = lbm.Lattice.from_workload(w, stream=stream, init="pulse")
+        if args.cells is not None:
+            lat.cells_per_thread = args.cells
+        if args.per_launch is not None:
+            lat.steps_per_launch = args.per_launch
+        spl = lat.steps_per_launch
         lat.step(args.warmup)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -63,17 +73,19 @@ def main(argv=None):
     b.synchronize()
     t = a.elapsed_time(b) / 1e3
     cells = w.cells * args.steps * copies
-    gbs = BYTES_PER_CELL[args.storage] * cells / t / 1e9
+    gbs = BYTES_PER_CELL[args.storage] * cells / spl / t / 1e9
     peak = None
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         peak = float(json.load(open(p))["hbm_gbs"])
     d = lat.diagnostics(ids[0]) if args.batch else lat.diagnostics()
+    cpt = lat.cells_per_thread
     lat.close()
     print(json.dumps({
         "case": f"{copies} x {args.side}x{args.side} {args.storage} variant {args.variant} "
                 f"layer {args.width}" + (" (batched)" if args.batch else ""),
-        "steps": args.steps, "mlups": cells / t / 1e6, "gbs": gbs,
+        "steps": args.steps, "cells_per_thread": cpt, "steps_per_launch": spl,
+        "mlups": cells / t / 1e6, "gbs": gbs,
         "frac_of_measured_hbm": gbs / peak if peak else None, "us_per_step": 1e6 * t / args.steps,
         "nonfinite_cells": d[5],
     }))
