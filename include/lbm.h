@@ -170,8 +170,8 @@ int64_t lbm_time(lbm_handle h);
 /* How lbm_step issues its kernels: 0 one launch per step; 1 one launch per
  * step, each a programmatic dependent of the previous (its launch overlaps
  * the previous step's tail); 2 (default) replays of a captured graph of 64
- * such launches, with single launches for the remainder.  All three compute
- * identical results.  The environment variable LBM_LAUNCH=plain|pdl|graph
+ * steps of such launches (64 one-step or 32 two-step launches), with single
+ * launches for the remainder.  All three compute identical results.  The environment variable LBM_LAUNCH=plain|pdl|graph
  * sets the initial mode of new handles. */
 int lbm_set_launch_mode(lbm_handle h, int mode);
 

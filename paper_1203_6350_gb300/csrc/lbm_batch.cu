@@ -1,5 +1,5 @@
-// Batched time step: many independent lattices advanced by one persistent
-// launch per step over a tile table, and the C ABI that manages the batch
+// Batched time step: many independent lattices advanced together by
+// persistent launches over a tile table, and the C ABI that manages the batch
 // (lbm_batch_* in include/lbm.h).
 //
 // Each instance is a lattice of its own (size, rates, damping variant,
@@ -10,9 +10,12 @@
 // step, or two (temporal blocking); an instance whose budget ends after the
 // first of the two takes only that one.  Every launch swaps the buffers of
 // the instances it advanced, so an instance's current buffer is the parity of
-// the number of launches it took, which the host counts.  The per-cell arithmetic is the
-// single-lattice kernel's (collide_cell, pull_all, store_all), so a lattice
-// gives the same result alone and in a batch.
+// the number of launches it took, which the host counts.
+//
+// The per-cell arithmetic is that of the single-lattice kernels (one cell per
+// thread, the packed pair, the two-step tile), and it does not depend on the
+// tile shape or on the other instances: within the batched path a lattice
+// gives the same result, bit for bit, alone and in any mix.
 #include <algorithm>
 #include <climits>
 #include <cstdio>
