@@ -21,7 +21,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblbm_oracle.so")
 
 VARIANTS = {"none": 0, "I": 1, "II": 2, "III": 3, "viscous": 4}
-BCS = {"dirichlet": 0, "periodic": 1}
+BCS = {"dirichlet": 0, "periodic": 1, "channel": 2}
 
 
 class _Params(ctypes.Structure):
@@ -39,6 +39,10 @@ class _Params(ctypes.Structure):
         ("s", ctypes.c_double * 9),
         ("n", ctypes.c_double),
         ("m", ctypes.c_double),
+        ("src_amp", ctypes.c_double),
+        ("src_omega", ctypes.c_double),
+        ("src_phase", ctypes.c_double),
+        ("t0", ctypes.c_double),
     ]
 
 
@@ -95,7 +99,10 @@ class Problem:
     act on the conserved rows (rate s_c), ``n``/``m`` are the Guo weights,
     ``rho0/u0`` the far-field (boundary) state, ``rho_f/u_f`` the reference
     state q_ref of the absorbing term, ``chi_x``/``chi_y`` the per-axis
-    absorbing strengths (chi = max of the two at a cell).
+    absorbing strengths (chi = max of the two at a cell).  With bc="channel"
+    (the line source of Sec. 4.2) the left edge is a source of density
+    rho0 + src_amp sin(src_omega t + src_phase) moving at u0, the right edge an
+    outflow, and y is periodic.
     """
 
     nx: int
@@ -111,6 +118,9 @@ class Problem:
     u_f: tuple = (0.0, 0.0)
     chi_x: np.ndarray = field(default=None)
     chi_y: np.ndarray = field(default=None)
+    src_amp: float = 0.0
+    src_omega: float = 0.0
+    src_phase: float = 0.0
 
     def __post_init__(self):
         self.s = np.asarray(self.s, dtype=np.float64)
@@ -131,6 +141,8 @@ class Problem:
         for k in range(9):
             p.s[k] = float(self.s[k])
         p.n, p.m = self.n, self.m
+        p.src_amp, p.src_omega, p.src_phase = self.src_amp, self.src_omega, self.src_phase
+        p.t0 = 0.0
         return p
 
 
@@ -151,6 +163,7 @@ class State:
         self.t = 0
 
     def run(self, nsteps: int, nthreads: int = 0) -> "State":
+        self._p.t0 = float(self.t)
         rc = lib().oracle_run(ctypes.byref(self._p), _dp(self.prob.chi_x), _dp(self.prob.chi_y),
                               _dp(self.f), int(nsteps), int(nthreads))
         if rc != 0:

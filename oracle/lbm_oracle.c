@@ -43,6 +43,14 @@
  *     outside the lattice takes the value f^eq_i(rho0, u0).  This holds at
  *     every time level including t = 0 (oracle_init applies it).
  *   - Periodic: the lattice wraps in both directions.
+ *   - Channel (the time-dependent line source of Sec. 4.2): periodic in y; at
+ *     the left edge a population streaming in from x = -1 takes the value of
+ *     the equilibrium f^eq_i(rho_s(t), u0) with rho_s(t) = rho0 + A sin(w t +
+ *     phi), t the time of the post-collision state it leaves; at the right
+ *     edge (outflow) a population streaming in from x = nx takes the
+ *     post-collision value of the same population at x = nx - 1 (zero
+ *     gradient).  At t = 0 (oracle_init) the left edge takes rho_s(-1) and the
+ *     right edge the equilibrium of the initial state at x = nx - 2.
  *
  * Layout: f[(i * ny + iy) * nx + ix], i = 0..8 in the velocity order fixed by
  * rows 1-2 of M (App. A.1): c = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
@@ -57,12 +65,14 @@
 
 typedef struct {
     int nx, ny;
-    int bc;        /* 0: Dirichlet far-field equilibrium, 1: periodic */
+    int bc;        /* 0: Dirichlet far-field equilibrium, 1: periodic, 2: channel */
     int variant;   /* 0: none, 1: type I, 2: type II, 3: type III, 4: viscosity sponge */
     double rho0, ux0, uy0;    /* far-field state of the boundary */
     double rho_f, ux_f, uy_f; /* reference state q_ref of the absorbing term */
     double s[9];   /* diagonal of S in the row order of M */
     double n, m;   /* weights of the Guo parameterisation */
+    double src_amp, src_omega, src_phase;  /* channel: rho_s(t) = rho0 + A sin(w t + phi) */
+    double t0;     /* time of the state oracle_run starts from */
 } oracle_params;
 
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -229,24 +239,39 @@ static inline size_t idx(const oracle_params* p, int i, int iy, int ix) {
     return ((size_t)i * p->ny + iy) * p->nx + ix;
 }
 
+/* Density of the line source at time t (channel boundary). */
+static double source_rho(const oracle_params* p, double t) {
+    return p->rho0 + p->src_amp * sin(p->src_omega * t + p->src_phase);
+}
+
 /* Initial state: f = f^eq(rho(x), u(x)) at every cell, then the boundary rule
- * for populations entering from outside (Dirichlet only).  rho, ux, uy are
- * [ny][nx] row-major. */
+ * for populations entering from outside (Dirichlet and channel).  rho, ux, uy
+ * are [ny][nx] row-major. */
 int oracle_init(const oracle_params* p, const double* rho, const double* ux, const double* uy,
                 double* f) {
     const int nx = p->nx, ny = p->ny;
     if (nx <= 0 || ny <= 0) return -1;
-    double fb[9];
+    if (p->bc == 2 && nx < 2) return -1;
+    double fb[9], fs[9];
     oracle_feq(p->rho0, p->ux0, p->uy0, fb);
+    oracle_feq(source_rho(p, p->t0 - 1.0), p->ux0, p->uy0, fs);
     for (int iy = 0; iy < ny; ++iy)
         for (int ix = 0; ix < nx; ++ix) {
-            double fe[9];
+            double fe[9], fo[9];
             const size_t c = (size_t)iy * nx + ix;
             oracle_feq(rho[c], ux[c], uy[c], fe);
+            if (p->bc == 2 && ix == nx - 1) {  /* zero gradient: the column inside */
+                const size_t c2 = (size_t)iy * nx + ix - 1;
+                oracle_feq(rho[c2], ux[c2], uy[c2], fo);
+            }
             for (int i = 0; i < 9; ++i) {
                 const int sx = ix - CX[i], sy = iy - CY[i];
                 const int outside = sx < 0 || sx >= nx || sy < 0 || sy >= ny;
-                f[idx(p, i, iy, ix)] = (outside && p->bc == 0) ? fb[i] : fe[i];
+                double v = fe[i];
+                if (p->bc == 0 && outside) v = fb[i];
+                if (p->bc == 2 && sx < 0) v = fs[i];
+                if (p->bc == 2 && sx >= nx) v = fo[i];
+                f[idx(p, i, iy, ix)] = v;
             }
         }
     return 0;
@@ -262,6 +287,7 @@ int oracle_run(const oracle_params* p, const double* chi_x, const double* chi_y,
     if (oracle_lambda(p->s, lam) != 0) return -2;
     for (int k = 0; k < 9; ++k) s1[k] = k < 3 ? p->s[k] : 1.0;
     if (oracle_lambda(s1, lam1) != 0) return -2;
+    if (p->bc == 2 && nx < 2) return -1;
     double fb[9];
     oracle_feq(p->rho0, p->ux0, p->uy0, fb);
     const size_t ncell = (size_t)nx * ny;
@@ -290,6 +316,8 @@ int oracle_run(const oracle_params* p, const double* chi_x, const double* chi_y,
             }
         }
         /* streaming: f_i(x) = fhat_i(x - c_i) */
+        double fs[9];  /* channel: the source column's post-collision state at this time */
+        oracle_feq(source_rho(p, p->t0 + step), p->ux0, p->uy0, fs);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(nthreads)
 #endif
@@ -304,6 +332,14 @@ int oracle_run(const oracle_params* p, const double* chi_x, const double* chi_y,
                         sx = (sx + nx) % nx;
                         sy = (sy + ny) % ny;
                         v = post[idx(p, i, sy, sx)];
+                    } else if (p->bc == 2) {
+                        sy = (sy + ny) % ny;
+                        if (sx < 0)
+                            v = fs[i];
+                        else if (sx >= nx)
+                            v = post[idx(p, i, sy, nx - 1)];
+                        else
+                            v = post[idx(p, i, sy, sx)];
                     } else {
                         v = fb[i];
                     }

@@ -45,12 +45,29 @@ def feq_linear(rho, jx, jy):
     return W.reshape(sh) * (rho + 3 * (C[:, 0].reshape(sh) * jx + C[:, 1].reshape(sh) * jy))
 
 
-def init(rho, ux, uy, bc="dirichlet", rho0=1.0, u0=(0.0, 0.0)):
+def source_rho(source, rho0, t):
+    """Density of the line source (channel boundary) at time t."""
+    amp, omega, phase = source
+    return rho0 + amp * np.sin(omega * t + phase)
+
+
+def init(rho, ux, uy, bc="dirichlet", rho0=1.0, u0=(0.0, 0.0), source=(0.0, 0.0, 0.0)):
     """f = f^eq(rho, u); with the Dirichlet rule, populations entering from
-    outside take f^eq(rho0, u0)."""
+    outside take f^eq(rho0, u0).  Channel: those entering at the left edge take
+    the source equilibrium of time -1, those entering at the right edge the
+    equilibrium of the column inside (x = nx - 2) in the same row."""
+    rho, ux, uy = np.broadcast_arrays(*(np.asarray(a, dtype=np.float64) for a in (rho, ux, uy)))
     f = feq(rho, ux, uy)
     if bc == "dirichlet":
         _apply_dirichlet(f, feq(rho0, *u0))
+    elif bc == "channel":
+        fs = feq(source_rho(source, rho0, -1.0), *u0)
+        fo = feq(rho[:, -2], ux[:, -2], uy[:, -2])  # [9, ny]
+        for i in range(9):
+            if C[i, 0] == 1:
+                f[i, :, 0] = fs[i]
+            elif C[i, 0] == -1:
+                f[i, :, -1] = fo[i]
     return f
 
 
@@ -66,8 +83,9 @@ def _apply_dirichlet(f, fb):
 
 
 def step(f, chi, s, variant="II", n=0.5, m=0.5, rho_f=1.0, u_f=(0.0, 0.0), bc="dirichlet",
-         rho0=1.0, u0=(0.0, 0.0)):
-    """One time step of the scheme.  f: [9, ny, nx]; chi: [ny, nx]."""
+         rho0=1.0, u0=(0.0, 0.0), source=(0.0, 0.0, 0.0), t=0):
+    """One time step of the scheme from time t.  f: [9, ny, nx]; chi: [ny, nx]."""
+    kw = dict(source=source, t=t)
     lam = np.linalg.inv(M) @ np.diag(s) @ M
     if variant == "viscous":
         # Sec. 4.1 comparison: no damping term, the non-conserved rates fall
@@ -85,7 +103,7 @@ def step(f, chi, s, variant="II", n=0.5, m=0.5, rho_f=1.0, u_f=(0.0, 0.0), bc="d
                 sk[3:] = sk[3:] + (1.0 - sk[3:]) * r[iy, ix]
                 lam_c = minv @ np.diag(sk) @ M
                 out_post[:, iy, ix] = f[:, iy, ix] + lam_c @ (fs[:, iy, ix] - f[:, iy, ix])
-        return _stream(out_post, bc, rho0, u0)
+        return _stream(out_post, bc, rho0, u0, **kw)
     if variant == "none":  # no absorbing term: F = 0, so rho* = rho and j* = j
         chi = np.zeros_like(chi)
     rho = f.sum(0)
@@ -106,16 +124,32 @@ def step(f, chi, s, variant="II", n=0.5, m=0.5, rho_f=1.0, u_f=(0.0, 0.0), bc="d
     else:
         t = 0.0
     post = f + coll + t
-    return _stream(post, bc, rho0, u0)
+    return _stream(post, bc, rho0, u0, **kw)
 
 
-def _stream(post, bc, rho0, u0):
-    """Pull streaming f_i(x) = fhat_i(x - c_i) with the boundary rule."""
+def _stream(post, bc, rho0, u0, source=(0.0, 0.0, 0.0), t=0):
+    """Pull streaming f_i(x) = fhat_i(x - c_i) with the boundary rule (t: the
+    time of the post-collision state)."""
     f = post
     out = np.empty_like(f)
     if bc == "periodic":
         for i in range(9):
             out[i] = np.roll(post[i], shift=(C[i, 1], C[i, 0]), axis=(0, 1))
+    elif bc == "channel":
+        _, ny, nx = f.shape
+        fs = feq(source_rho(source, rho0, t), *u0)
+        for i in range(9):
+            cx, cy = C[i]
+            for iy in range(ny):
+                sy = (iy - cy) % ny
+                for ix in range(nx):
+                    sx = ix - cx
+                    if sx < 0:
+                        out[i, iy, ix] = fs[i]
+                    elif sx >= nx:
+                        out[i, iy, ix] = post[i, sy, nx - 1]
+                    else:
+                        out[i, iy, ix] = post[i, sy, sx]
     else:
         _, ny, nx = f.shape
         fb = feq(rho0, *u0)

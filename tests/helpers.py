@@ -7,7 +7,8 @@ import numpy as np
 
 def oracle_problem(core, w):
     return core.Problem(w.nx, w.ny, w.s, n=w.n, m=w.m, variant=w.variant, bc=w.bc, rho0=w.rho0,
-                        u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x, chi_y=w.chi_y)
+                        u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x, chi_y=w.chi_y,
+                        src_amp=w.source[0], src_omega=w.source[1], src_phase=w.source[2])
 
 
 def run_oracle(w, steps=None, nthreads=0):

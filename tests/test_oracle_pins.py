@@ -303,7 +303,8 @@ def test_pulse_converges_to_the_bessel_solution(oracle_lib, U0):
 
 def _run_workload(core, w, steps):
     prob = core.Problem(w.nx, w.ny, w.s, n=w.n, m=w.m, variant=w.variant, bc=w.bc, rho0=w.rho0,
-                        u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x, chi_y=w.chi_y)
+                        u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x, chi_y=w.chi_y,
+                        src_amp=w.source[0], src_omega=w.source[1], src_phase=w.source[2])
     return core.State(prob, *w.initial_fields()).run(steps)
 
 
@@ -332,32 +333,94 @@ def test_mirror_symmetry(oracle_lib, variant):
 
 @pytest.mark.parametrize("nx,ny", [(4, 4), (5, 3), (1, 1), (2, 7)])
 @pytest.mark.parametrize("variant", ["none", "I", "II", "III", "viscous"])
-@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic", "channel"])
 def test_c_oracle_matches_numpy_twin(oracle_lib, nx, ny, variant, bc):
     """Tiny lattices, random populations, MRT rates, 3 steps: the C oracle equals the
     independent NumPy statement to round-off.  Catches indexing, layout and
-    boundary mistakes in the C code."""
+    boundary mistakes in the C code.  The channel (line source, outflow,
+    periodic y) runs its steps in two calls, which pins the source's clock."""
     from oracle import twin
 
+    if bc == "channel" and nx < 2:
+        pytest.skip("the channel's outflow needs two columns")
     rng = np.random.default_rng(nx * 100 + ny)
     s = np.array([1.6, 1.6, 1.6, 1.1, 1.2, 1.3, 1.3, 1.9, 1.9])
     u0 = (0.03, -0.01)
+    src = (2e-3, 0.7, 0.3)
     chi_x = rng.uniform(0, 0.6, nx)
     chi_y = rng.uniform(0, 0.6, ny)
     prob = _prob(oracle_lib, nx, ny, s, variant=variant, bc=bc, n=0.4, m=0.6, rho0=1.0, u0=u0,
-                 rho_f=1.01, u_f=(0.02, 0.01), chi_x=chi_x, chi_y=chi_y)
+                 rho_f=1.01, u_f=(0.02, 0.01), chi_x=chi_x, chi_y=chi_y, src_amp=src[0],
+                 src_omega=src[1], src_phase=src[2])
     rho = 1 + 0.01 * rng.standard_normal((ny, nx))
     ux = 0.03 + 0.01 * rng.standard_normal((ny, nx))
     uy = -0.01 + 0.01 * rng.standard_normal((ny, nx))
     st = oracle_lib.State(prob, rho, ux, uy)
-    f = twin.init(rho, ux, uy, bc=bc, rho0=1.0, u0=u0)
+    f = twin.init(rho, ux, uy, bc=bc, rho0=1.0, u0=u0, source=src)
     np.testing.assert_allclose(st.f, f, atol=1e-15)
     chi = np.maximum(chi_x[None, :], chi_y[:, None])
-    for _ in range(3):
+    for t in range(3):
         f = twin.step(f, chi, s, variant, n=0.4, m=0.6, rho_f=1.01, u_f=(0.02, 0.01), bc=bc,
-                      rho0=1.0, u0=u0)
-    st.run(3)
+                      rho0=1.0, u0=u0, source=src, t=t)
+    st.run(2)
+    st.run(1)
     np.testing.assert_allclose(st.f, f, atol=2e-15)
+
+
+# ------------------------------------------------------------ line source ----
+
+def _zero_crossings(y):
+    """Positions (linear interpolation) where y crosses zero upwards."""
+    i = np.nonzero((y[:-1] < 0) & (y[1:] >= 0))[0]
+    return i + y[i] / (y[i] - y[i + 1])
+
+
+@pytest.mark.parametrize("ux", [0.0, 0.1])
+def test_line_source_emits_a_plane_wave_at_the_sound_speed(oracle_lib, ux):
+    """Sec. 4.2: the line source rho0 + A sin(2 pi t / T) on the left edge of a
+    y-periodic channel emits a plane wave.  The field does not depend on y, and
+    behind the front the wavelength is (c_s + U) T, the downstream phase speed of
+    linear acoustics in a mean flow U (c_s = 1/sqrt(3), Sec. 2.1).  Catches a
+    source on the wrong populations, a wrong clock or a mis-wrapped y."""
+    T = 100.0
+    w = wl.line_source(nx=700, ny=3, variant="none", width=0, period=T, u0=(ux, 0.0), nu=2e-4)
+    st = _run_workload(oracle_lib, w, 900)
+    r = st.moments()[0]
+    assert np.abs(r - r[0]).max() == 0.0
+    x0 = _zero_crossings(r[0, 40:420])
+    lam = np.diff(x0).mean()
+    assert abs(lam - (wl.CS + ux) * T) < 0.01 * (wl.CS + ux) * T, (lam, (wl.CS + ux) * T)
+    # the source drives an O(A) wave
+    amp = np.abs(r[0, 40:420]).max()
+    assert 0.3 * w.source[0] < amp < 1.5 * w.source[0]
+
+
+def _line_source_error(core, variant, width, ux=0.0, nx=800):
+    """Relative L2 error of rho' over the first 640 cells of the channel at the
+    paper's sample time, against the same source in a channel long enough that
+    nothing comes back from its far end before that time."""
+    w = wl.line_source(nx=nx, ny=2, variant=variant, width=width, u0=(ux, 0.0))
+    ref = wl.line_source(nx=1200, ny=2, variant="none", width=0, u0=(ux, 0.0), steps=w.steps)
+    got = _run_workload(core, w, w.steps).moments()[0][0, :640]
+    want = _run_workload(core, ref, w.steps).moments()[0][0, :640]
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+@pytest.mark.parametrize("ux", [0.0, 0.1])
+def test_line_source_layer_removes_the_outflow_reflection(oracle_lib, ux):
+    """Sec. 4.2 (Figs. 9-10): at t = T_o + 10 T_p the type II layer (chi = 4/s -
+    0.001, 0.8 H = 160 cells) leaves the field in front of it almost exactly
+    the unbounded solution, the outflow alone reflects strongly, the viscosity
+    sponge lies in between, and a layer one wavelength thick (58 cells, about
+    0.3 H) already does nearly as well as the full one."""
+    e_none = _line_source_error(oracle_lib, "none", 0, ux)
+    e_visc = _line_source_error(oracle_lib, "viscous", 160, ux)
+    e_ii = _line_source_error(oracle_lib, "II", 160, ux)
+    e_ii_thin = _line_source_error(oracle_lib, "II", 58, ux)
+    # measured: none 0.22 / 0.15, viscous 0.14 / 0.10, type II 1.1e-4, one wavelength 5.3e-4
+    assert e_ii < 0.002 * e_none, (e_ii, e_none)
+    assert e_ii < e_visc < 0.8 * e_none, (e_ii, e_visc, e_none)
+    assert e_ii_thin < 0.01 * e_none, (e_ii_thin, e_none)
 
 
 # ------------------------------------------------------ absorption trends ----

@@ -73,6 +73,28 @@ def orszag_profile(n: int, width: int, chi: float) -> np.ndarray:
     return chi * np.where(d > 0, sig, 0.0)
 
 
+def outflow_layer(n: int, width: int, chi: float, profile: str = "orszag") -> np.ndarray:
+    """Absorbing strength along x for the channel of Sec. 4.2: a layer of `width`
+    cells at the right (outflow) end only, depth 0 at its inner edge rising to
+    `width` at the last cell; profile "orszag" (Eq. normalizedsigma, A = n = 4),
+    "ramp" (quadratic) or "viscous" (the layer fraction r = d / width)."""
+    out = np.zeros(n)
+    if width <= 0:
+        return out
+    i = np.arange(n)
+    d = np.clip(i - (n - 1 - width), 0, width).astype(np.float64)
+    if profile == "orszag":
+        L = width + 1.0
+        out = chi * np.where(d > 0, 3125.0 * (L - d) * d**4 / (256.0 * L**5), 0.0)
+    elif profile == "ramp":
+        out = chi * (d / width) ** 2
+    elif profile == "viscous":
+        out = d / width
+    else:
+        raise ValueError(profile)
+    return out
+
+
 def gaussian_pulse(nx: int, ny: int, x0: float, y0: float, eps: float, b: float) -> np.ndarray:
     """rho' = eps exp(-alpha r^2), alpha = ln2 / b^2 (Eq. 3:para0), on cell centres
     (ix, iy), as [ny, nx]."""
@@ -107,6 +129,7 @@ class Workload:
     chi_max: float = 0.0
     seed: int | None = None
     meta: dict = field(default_factory=dict)
+    source: tuple = (0.0, 0.0, 0.0)  # channel: (amplitude, omega per step, phase) of the line source
 
     def __post_init__(self):
         if self.chi_x is None:
@@ -189,6 +212,33 @@ def quiescent(side: int, storage="f32", steps=200, width=128, chi_max=0.1, varia
                        b=5.0, width=width, chi_max=chi_max, steps=steps,
                        name=f"quiescent-{side}x{side}")
     return w
+
+
+def line_source(nx: int = 800, ny: int = 200, variant: str = "II", width: int = 160,
+                amplitude: float = 1e-3, period: float = 100.0, u0=(0.0, 0.0), nu: float = 2e-4,
+                steps: int | None = None, storage: str = "f32", profile: str | None = None,
+                eps: float = 1e-3, name: str = "line-source") -> Workload:
+    """The time-dependent acoustic line source of Sec. 4.2 in lattice units: a
+    channel W = 4H with H = ny cells (200 cells per unit length), periodic in y,
+    the source rho0 + A sin(2 pi t / period) on the left edge, an outflow on the
+    right, and an absorbing layer of `width` cells (0.8 H) in front of the
+    outflow with chi_max = 4/s - eps (the paper's choice).  omega = 2 per unit
+    time with delta t = 1/200 gives a period of 100 steps and a wavelength of
+    c_s * 100 = 57.7 cells (c_s / 2 = 0.2887 units).  nu = 2e-4 is Re = 1/nu
+    = 1e6 in those units.  The default number of steps is the paper's sample
+    time T_o + 10 T_p (T_o = W / (c_s + u0x), T_p = one period)."""
+    s = rate_from_viscosity(nu)
+    chi_max = 4.0 / s - eps
+    if profile is None:
+        profile = "viscous" if variant == "viscous" else "orszag"
+    chi_x = outflow_layer(nx, width, chi_max, profile) if variant != "none" else np.zeros(nx)
+    if steps is None:
+        steps = int(round(nx / (CS + u0[0]) + 10 * period))
+    return Workload(name=name, nx=nx, ny=ny, s=np.full(9, s), variant=variant, bc="channel",
+                    u0=tuple(u0), u_f=tuple(u0), chi_x=chi_x, chi_y=np.zeros(ny), steps=steps,
+                    storage=storage, width=width, chi_max=chi_max,
+                    source=(amplitude, 2.0 * math.pi / period, 0.0),
+                    meta={"period": period, "wavelength": (CS + u0[0]) * period})
 
 
 def batch_of_lattices(seed: int = 0, count: int = 256, lo: int = 64, hi: int = 1024,
