@@ -345,6 +345,7 @@ def run_native(args):
     roof["one_cell_per_thread"] = one_cell
     roof_large = roofline_large(peaks)
     sweep = None if args.no_sweep else run_roofline_sweep(peaks)
+    line_source = None if args.no_sweep else run_line_source(peaks)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -372,6 +373,7 @@ def run_native(args):
             "gpu_launches": launches_total,
             "reflected_energy": {k: refl.get(k) for k in VARIANTS},
             "roofline_sweep": sweep,
+            "line_source": line_source,
             "batched": batched,
             "serving": serving,
         }
@@ -478,6 +480,50 @@ def roofline_large(peaks, side: int = 4096, steps: int = 100):
             "one_step_per_launch": out["one_step_per_launch"],
             "one_cell_per_thread": out["one_cell_per_thread"],
             "traffic_profile": "profiles/step_tb2_kernel_f32_4096x4096_full.md"}
+
+
+def run_line_source(peaks):
+    """The time-dependent line source of Sec. 4.2 (channel W x H = 800 x 200
+    cells, source rho0 + 1e-3 sin(2 pi t / 100), type II layer of 160 cells
+    with chi = 4/s - 0.001, Re = 1e6) to the paper's sample time T_o + 10 T_p:
+    MLUPS in FP32, and the relative L2 error of rho' over the 640 cells in front
+    of the layer against a channel long enough that nothing returns from its
+    far end, for no layer, the viscosity sponge, the type II layer and a type
+    II layer one wavelength (58 cells) thick."""
+    import torch
+
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.line_source(storage="f32")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = with_warn(lambda: lbm.Lattice.from_workload(w, stream=stream))
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(w.steps)
+        z.record(stream)
+        z.synchronize()
+        lat.close()
+    t = a.elapsed_time(z) / 1e3
+
+    def interior(variant, width):
+        x = wl.line_source(ny=8, variant=variant, width=width, storage="f32")
+        ref = wl.line_source(nx=1200, ny=8, variant="none", width=0, storage="f32", steps=x.steps)
+        out = []
+        for y in (x, ref):
+            with with_warn(lambda: lbm.Lattice.from_workload(y)) as lt:
+                lt.step(x.steps)
+                out.append(lt.moments()[0][:, :640])
+        return float(np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[1]))
+
+    return {"case": "channel 800 x 200, FP32, type II layer 160 cells, "
+                    f"{w.steps} steps (T_o + 10 T_p)",
+            "mlups": w.cells * w.steps / t / 1e6,
+            "gbs": BYTES_PER_CELL["f32"] * w.cells * w.steps / t / 1e9,
+            "interior_rel_l2_vs_unbounded": {
+                "no_layer": interior("none", 0), "viscosity_sponge_160": interior("viscous", 160),
+                "type_II_160": interior("II", 160), "type_II_58_one_wavelength": interior("II", 58)}}
 
 
 def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", "f16dev",

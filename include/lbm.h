@@ -67,7 +67,16 @@ typedef enum {
     LBM_SPONGE_VISCOUS = 4
 } lbm_variant;
 
-typedef enum { LBM_BC_DIRICHLET_EQ = 0, LBM_BC_PERIODIC = 1 } lbm_bc;
+/* Boundary.  LBM_BC_CHANNEL is the acoustic line-source case of Sec. 4.2:
+ * periodic in y; a population entering at the left edge (x = 0) is that of
+ * the equilibrium f^eq(rho_s(t), u0) of the source column, rho_s(t) = rho0 +
+ * A sin(omega t + phase) (lbm_set_source; A = 0 until set), t the time of the
+ * post-collision state it leaves (so the state of time 0 takes rho_s(-1));
+ * a population entering at the right edge (outflow, x = nx - 1) takes the
+ * post-collision value of the same population of the last column (zero
+ * gradient), and at time 0 the initial equilibrium of the column x = nx - 2.
+ * Single lattices only (lbm_batch_add rejects it); one step per launch. */
+typedef enum { LBM_BC_DIRICHLET_EQ = 0, LBM_BC_PERIODIC = 1, LBM_BC_CHANNEL = 2 } lbm_bc;
 
 /* Relaxation rates: s[k] is the diagonal of S in the row order of M
  * (App. A.1): s[0..2] act on the conserved rows rho, j_x, j_y (rate s_c,
@@ -208,6 +217,14 @@ int lbm_steps_per_launch(lbm_handle h);
 
 /* Replace the handle's stream (borrowed; NULL = legacy default stream). */
 int lbm_set_stream(lbm_handle h, void* cuda_stream);
+
+/* The line source of an LBM_BC_CHANNEL lattice (Sec. 4.2): density
+ * rho0 + amplitude sin(omega t + phase) at step t, moving at u0 (the paper's
+ * omega = 2 per unit time is 2 pi / 100 per step at 200 cells per unit
+ * length).  Takes effect from the next call that launches work; waits for
+ * the handle's stream.  LBM_ERR_ARG for another boundary or non-finite
+ * input. */
+int lbm_set_source(lbm_handle h, double amplitude, double omega, double phase);
 
 /* Free the device buffers and the handle.  NULL is allowed. */
 void lbm_destroy(lbm_handle h);

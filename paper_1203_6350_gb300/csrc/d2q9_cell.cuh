@@ -351,8 +351,15 @@ struct PullSites {
         if (BC == kPeriodic) {
             if (!in_xm) from_xm = nx - 1;
             if (!in_xp) from_xp = -(nx - 1);
+        }
+        if (BC == kPeriodic || BC == kChannel) {
             if (!in_ym) from_ym = (ny - 1) * pitch;
             if (!in_yp) from_yp = -(ny - 1) * pitch;
+            in_ym = in_yp = true;
+        }
+        if (BC == kChannel && !in_xp) {  // outflow: the last column's own value
+            from_xp = 0;
+            in_xp = true;
         }
     }
     template <int I>
@@ -375,29 +382,34 @@ struct PullSites {
     }
 };
 
-// Pull population I of the cell at element offset o (a Dirichlet far-field
-// wall contributes a zero deviation).  CHECK = false: the cell is interior.
+// Pull population I of the cell at element offset o.  From outside the
+// lattice: a Dirichlet far-field wall contributes a zero deviation; the
+// channel's source edge contributes src_s * src_e[I] (see LineSource).
+// CHECK = false: the cell is interior.
 template <typename T, int BC, bool CHECK, int I>
 __device__ __forceinline__ typename Codec<T>::CT pull(const PlanePtrs<T>& src, int o,
-                                                      const PullSites& ps) {
+                                                      const PullSites& ps, double src_s = 0.0,
+                                                      const double* src_e = nullptr) {
     using CT = typename Codec<T>::CT;
     if (!CHECK || BC == kPeriodic || ps.inside<I>())
         return Codec<T>::template dec<I>(__ldg(src.p[I] + (o + ps.offset<I>())));
+    if (BC == kChannel) return CT(src_s * src_e[I]);  // only cx = +1 at x = 0 gets here
     return CT(0);
 }
 
 template <typename T, int BC, bool CHECK>
 __device__ __forceinline__ void pull_all(const PlanePtrs<T>& src, int o, const PullSites& ps,
-                                         typename Codec<T>::CT (&g)[9]) {
-    g[0] = pull<T, BC, CHECK, 0>(src, o, ps);
-    g[1] = pull<T, BC, CHECK, 1>(src, o, ps);
-    g[2] = pull<T, BC, CHECK, 2>(src, o, ps);
-    g[3] = pull<T, BC, CHECK, 3>(src, o, ps);
-    g[4] = pull<T, BC, CHECK, 4>(src, o, ps);
-    g[5] = pull<T, BC, CHECK, 5>(src, o, ps);
-    g[6] = pull<T, BC, CHECK, 6>(src, o, ps);
-    g[7] = pull<T, BC, CHECK, 7>(src, o, ps);
-    g[8] = pull<T, BC, CHECK, 8>(src, o, ps);
+                                         typename Codec<T>::CT (&g)[9], double src_s = 0.0,
+                                         const double* src_e = nullptr) {
+    g[0] = pull<T, BC, CHECK, 0>(src, o, ps, src_s, src_e);
+    g[1] = pull<T, BC, CHECK, 1>(src, o, ps, src_s, src_e);
+    g[2] = pull<T, BC, CHECK, 2>(src, o, ps, src_s, src_e);
+    g[3] = pull<T, BC, CHECK, 3>(src, o, ps, src_s, src_e);
+    g[4] = pull<T, BC, CHECK, 4>(src, o, ps, src_s, src_e);
+    g[5] = pull<T, BC, CHECK, 5>(src, o, ps, src_s, src_e);
+    g[6] = pull<T, BC, CHECK, 6>(src, o, ps, src_s, src_e);
+    g[7] = pull<T, BC, CHECK, 7>(src, o, ps, src_s, src_e);
+    g[8] = pull<T, BC, CHECK, 8>(src, o, ps, src_s, src_e);
 }
 
 template <typename T>

@@ -42,6 +42,8 @@ struct lbm_ctx {
     StepConst<lbm::F2> k2{};          // the FP32 constants, duplicated for the pair kernel
     int cpt = 1;                      // cells per thread of the step kernel: 1, or 2 (FP32 / 16-bit)
     int spl = 1;                      // time steps per launch: 1, or 2 (needs cpt == 2)
+    lbm::LineSource src{};            // channel boundary: the line source (amp 0 until lbm_set_source)
+    long long* d_time = nullptr;      // channel boundary: device copy of the step counter
     bool initialised = false;
     int64_t time = 0;
     int launch_mode = 2;              // kLaunchGraph; LBM_LAUNCH=plain|pdl|graph overrides
@@ -126,6 +128,18 @@ int ensure_staging(lbm_ctx* h) {
     return LBM_OK;
 }
 
+// e_i = f^eq_i(1, u0) of the line source (channel boundary), in FP64.
+void set_source_shape(lbm_ctx* h) {
+    const double ux = h->ux0, uy = h->uy0, uu = ux * ux + uy * uy;
+    const int CXS[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int CYS[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int i = 0; i < 9; ++i) {
+        const double cu = CXS[i] * ux + CYS[i] * uy;
+        h->src.e[i] = W[i] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
 // The pair kernel steps FP32 and 16-bit storage and addresses the nine
 // planes with 32-bit element offsets.
 bool pair_kernel_ok(const lbm_ctx* h) {
@@ -136,31 +150,52 @@ lbm::BaseState base_of(const lbm_ctx* h) { return lbm::BaseState{h->rho0, h->ux0
 
 bool is_finite(double v) { return std::isfinite(v); }
 
-cudaError_t launch_one_step(lbm_ctx* h, const void* src, void* dst, cudaStream_t st, bool pdl) {
+// The line source as a step launch sees it: the device step counter plus
+// t_off launches issued since it was last advanced.
+lbm::LineSource launch_source(const lbm_ctx* h, long long t_off) {
+    lbm::LineSource ls = h->src;
+    ls.time = h->d_time;
+    ls.t_off = t_off;
+    return ls;
+}
+
+// The line source as the read-out kernels see it: the state of time h->time.
+lbm::LineSource readout_source(const lbm_ctx* h) {
+    lbm::LineSource ls = h->src;
+    ls.time = nullptr;
+    ls.t_off = h->time;
+    return ls;
+}
+
+__global__ void advance_time_kernel(long long* t, int by) { *t += by; }
+
+cudaError_t launch_one_step(lbm_ctx* h, const void* src, void* dst, cudaStream_t st, bool pdl,
+                            long long t_off = 0) {
     const int p = pdl ? 1 : 0;
+    const lbm::LineSource ls = launch_source(h, t_off);
     const auto* tx = static_cast<const lbm::AxisCoef<float>*>(h->chi_x);
     const auto* ty = static_cast<const lbm::AxisCoef<float>*>(h->chi_y);
     if (h->cpt == 2) {
         switch (h->storage) {
-            case LBM_F32: return lbm::launch_step2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
-            case LBM_F16DEV: return lbm::launch_step2_f16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
-            case LBM_BF16DEV: return lbm::launch_step2_bf16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
+            case LBM_F32: return lbm::launch_step2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p, ls);
+            case LBM_F16DEV: return lbm::launch_step2_f16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p, ls);
+            case LBM_BF16DEV: return lbm::launch_step2_bf16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p, ls);
             default: break;
         }
     }
     switch (h->storage) {
         case LBM_F64:
             return lbm::launch_step_f64(src, dst, h->geo, h->k64, static_cast<const lbm::AxisCoef<double>*>(h->chi_x),
-                                        static_cast<const lbm::AxisCoef<double>*>(h->chi_y), h->variant, h->bc, st, p);
+                                        static_cast<const lbm::AxisCoef<double>*>(h->chi_y), h->variant, h->bc, st, p, ls);
         case LBM_F32:
             return lbm::launch_step_f32(src, dst, h->geo, h->k32, static_cast<const lbm::AxisCoef<float>*>(h->chi_x),
-                                        static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p);
+                                        static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p, ls);
         case LBM_F16DEV:
             return lbm::launch_step_f16(src, dst, h->geo, h->k32, static_cast<const lbm::AxisCoef<float>*>(h->chi_x),
-                                        static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p);
+                                        static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p, ls);
         default:
             return lbm::launch_step_bf16(src, dst, h->geo, h->k32, static_cast<const lbm::AxisCoef<float>*>(h->chi_x),
-                                         static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p);
+                                         static_cast<const lbm::AxisCoef<float>*>(h->chi_y), h->variant, h->bc, st, p, ls);
     }
 }
 
@@ -201,8 +236,12 @@ cudaError_t ensure_graph(lbm_ctx* h, int parity) {
         if (h->spl == 2)
             e = launch_two_steps(h, h->buf[c], h->buf[1 - c], h->capture_stream, t > 0);
         else
-            e = launch_one_step(h, h->buf[c], h->buf[1 - c], h->capture_stream, t > 0);
+            e = launch_one_step(h, h->buf[c], h->buf[1 - c], h->capture_stream, t > 0, t);
         c = 1 - c;
+    }
+    if (e == cudaSuccess && h->bc == LBM_BC_CHANNEL) {  // the line source's clock
+        advance_time_kernel<<<1, 1, 0, h->capture_stream>>>(h->d_time, kGraphChunk);
+        e = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
@@ -228,7 +267,9 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     if (nx < 1 || ny < 1 || (long long)nx * ny > 2147483647LL)
         return fail(nullptr, LBM_ERR_ARG, "lattice size out of range");
     if (storage < LBM_F64 || storage > LBM_BF16DEV) return fail(nullptr, LBM_ERR_ARG, "bad storage");
-    if (bc != LBM_BC_DIRICHLET_EQ && bc != LBM_BC_PERIODIC) return fail(nullptr, LBM_ERR_ARG, "bad bc");
+    if (bc != LBM_BC_DIRICHLET_EQ && bc != LBM_BC_PERIODIC && bc != LBM_BC_CHANNEL)
+        return fail(nullptr, LBM_ERR_ARG, "bad bc");
+    if (bc == LBM_BC_CHANNEL && nx < 2) return fail(nullptr, LBM_ERR_ARG, "the channel needs nx >= 2");
     if (!rates) return fail(nullptr, LBM_ERR_ARG, "rates is NULL");
     if (!(rho0 > 0) || !is_finite(rho0) || !is_finite(ux0) || !is_finite(uy0))
         return fail(nullptr, LBM_ERR_ARG, "far-field state must be finite with rho0 > 0");
@@ -285,7 +326,8 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     h->chi_x = dev_alloc(h, h->chi_bytes_x);
     h->chi_y = dev_alloc(h, h->chi_bytes_y);
     h->diag = static_cast<double*>(dev_alloc(h, h->diag_bytes));
-    if (!h->buf[0] || !h->buf[1] || !h->chi_x || !h->chi_y || !h->diag) {
+    h->d_time = static_cast<long long*>(dev_alloc(h, 256));
+    if (!h->buf[0] || !h->buf[1] || !h->chi_x || !h->chi_y || !h->diag || !h->d_time) {
         lbm_destroy(h);
         return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
     }
@@ -294,6 +336,7 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     if (e == cudaSuccess) e = cudaMemsetAsync(h->chi_y, 0, h->chi_bytes_y, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, h->buf_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->buf_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_time, 0, sizeof(long long), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         lbm_destroy(h);
@@ -315,6 +358,8 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
         if (!std::strcmp(c, "2") && h->cpt == 2) h->spl = 2;
         if (!std::strcmp(c, "1")) h->spl = 1;
     }
+    if (bc == LBM_BC_CHANNEL) h->spl = 1;  // the two-step tiles have no channel edges
+    set_source_shape(h);
     if (const char* m = std::getenv("LBM_LAUNCH")) {
         if (!std::strcmp(m, "plain")) h->launch_mode = kLaunchPlain;
         else if (!std::strcmp(m, "pdl")) h->launch_mode = kLaunchPdl;
@@ -423,6 +468,8 @@ int lbm_init_equilibrium(lbm_handle h, const double* rho, const double* ux, cons
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_init_equilibrium");
     h->initialised = true;
     h->time = 0;
+    e = cudaMemsetAsync(h->d_time, 0, sizeof(long long), h->stream);  // the line source's clock
+    if (e != cudaSuccess) return cuda_fail(h, e, "clock reset");
     return LBM_OK;
 }
 
@@ -438,6 +485,8 @@ int lbm_init_pulse(lbm_handle h, double eps, double half_width, double x0, doubl
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_init_pulse");
     h->initialised = true;
     h->time = 0;
+    e = cudaMemsetAsync(h->d_time, 0, sizeof(long long), h->stream);  // the line source's clock
+    if (e != cudaSuccess) return cuda_fail(h, e, "clock reset");
     return LBM_OK;
 }
 
@@ -463,14 +512,21 @@ int lbm_step(lbm_handle h, int nsteps) {
             }
         }
     }
+    int issued = 0;
     while (nsteps > 0) {
         const int n = (h->spl == 2 && nsteps >= 2) ? 2 : 1;
         e = n == 2 ? launch_two_steps(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl)
-                   : launch_one_step(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl);
+                   : launch_one_step(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl, issued);
         if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step launch");
         h->cur = 1 - h->cur;
         h->time += n;
         nsteps -= n;
+        issued += n;
+    }
+    if (issued > 0 && h->bc == LBM_BC_CHANNEL) {  // the line source's clock
+        advance_time_kernel<<<1, 1, 0, h->stream>>>(h->d_time, issued);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step clock");
     }
     return LBM_OK;
 }
@@ -489,7 +545,7 @@ int lbm_moments(lbm_handle h, double* rho_dev, double* ux, double* uy, int on_de
         dy = uy ? h->staging + 2 * n : nullptr;
     }
     cudaError_t e = lbm::launch_moments(h->storage, h->buf[h->cur], h->geo, base_of(h), h->bc, dr, dx,
-                                        dy, h->stream);
+                                        dy, h->stream, readout_source(h));
     if (e == cudaSuccess && !on_device) {
         if (rho_dev) e = cudaMemcpyAsync(rho_dev, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -510,7 +566,7 @@ int lbm_diagnostics(lbm_handle h, int x0, int y0, int x1, int y1, double out[6])
     double* partial = h->diag;
     double* res = h->diag + lbm::kDiagBlocks * lbm::kDiag;
     cudaError_t e = lbm::launch_diagnostics(h->storage, h->buf[h->cur], h->geo, base_of(h), h->bc, x0, y0,
-                                            x1, y1, partial, res, h->stream);
+                                            x1, y1, partial, res, h->stream, readout_source(h));
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, lbm::kDiag * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_diagnostics");
@@ -544,6 +600,8 @@ int lbm_set_state(lbm_handle h, const void* src, size_t bytes, int on_device, in
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_state");
     h->time = time;
     h->initialised = true;
+    e = cudaMemcpyAsync(h->d_time, &h->time, sizeof(long long), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "clock set");
     return LBM_OK;
 }
 
@@ -576,6 +634,8 @@ int lbm_set_steps_per_launch(lbm_handle h, int steps) {
     if (steps != 1 && steps != 2) return fail(h, LBM_ERR_ARG, "steps per launch must be 1 or 2");
     if (steps == 2 && h->cpt != 2)
         return fail(h, LBM_ERR_ARG, "two steps per launch needs two cells per thread");
+    if (steps == 2 && h->bc == LBM_BC_CHANNEL)
+        return fail(h, LBM_ERR_ARG, "two steps per launch is not available for the channel boundary");
     if (steps != h->spl) {
         DeviceGuard dg(h->device);
         cudaStreamSynchronize(h->stream);
@@ -586,6 +646,20 @@ int lbm_set_steps_per_launch(lbm_handle h, int steps) {
 }
 
 int lbm_steps_per_launch(lbm_handle h) { return h ? h->spl : LBM_ERR_ARG; }
+
+int lbm_set_source(lbm_handle h, double amplitude, double omega, double phase) {
+    if (!h) return LBM_ERR_ARG;
+    if (h->bc != LBM_BC_CHANNEL) return fail(h, LBM_ERR_ARG, "a line source needs the channel boundary");
+    if (!std::isfinite(amplitude) || !std::isfinite(omega) || !std::isfinite(phase))
+        return fail(h, LBM_ERR_ARG, "source parameters must be finite");
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);  // the captured launches carry the old source
+    h->src.amp = amplitude;
+    h->src.omega = omega;
+    h->src.phase = phase;
+    return LBM_OK;
+}
 
 int lbm_cells_per_thread(lbm_handle h) { return h ? h->cpt : LBM_ERR_ARG; }
 
@@ -606,6 +680,7 @@ void lbm_destroy(lbm_handle h) {
     dev_free(h, h->chi_x, h->chi_bytes_x);
     dev_free(h, h->chi_y, h->chi_bytes_y);
     dev_free(h, h->diag, h->diag_bytes);
+    dev_free(h, h->d_time, 256);
     dev_free(h, h->staging, h->staging_bytes);
     delete h;
 }

@@ -33,6 +33,7 @@ __device__ __forceinline__ void init_plane(const PlanePtrs<T>& dst, const Geomet
     using CT = typename Codec<T>::CT;
     // The pull at cell (x, y) + c_I reads this slot, so it holds f^eq there.
     int sx = x + cx(I), sy = y + cy(I);
+    if (bc == kChannel) sy = (sy + g.ny) % g.ny;  // periodic in y only
     bool ok = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
     if (!ok && bc == kPeriodic) {
         sx = (sx + g.nx) % g.nx;
@@ -74,6 +75,7 @@ __device__ __forceinline__ void pulse_plane(const PlanePtrs<T>& dst, const Geome
                                             double xc, double yc, int bc, int x, int y) {
     using CT = typename Codec<T>::CT;
     int sx = x + cx(I), sy = y + cy(I);
+    if (bc == kChannel) sy = (sy + g.ny) % g.ny;  // periodic in y only
     bool ok = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
     if (!ok && bc == kPeriodic) {
         sx = (sx + g.nx) % g.nx;
@@ -120,12 +122,13 @@ template <typename T, int BC>
 __device__ __forceinline__ void cell_moments(const PlanePtrs<T>& src, const Geometry& g, int x,
                                              int y, typename Codec<T>::CT& r,
                                              typename Codec<T>::CT& jx,
-                                             typename Codec<T>::CT& jy) {
+                                             typename Codec<T>::CT& jy, const LineSource& ls) {
     using CT = typename Codec<T>::CT;
     PullSites ps;
     ps.edge<BC>(x, y, g.nx, g.ny, static_cast<int>(g.pitch));
     CT v[9];
-    pull_all<T, BC, true>(src, y * static_cast<int>(g.pitch) + x, ps, v);
+    const double src_s = (BC == kChannel && x == 0) ? line_source_scale(ls) : 0.0;
+    pull_all<T, BC, true>(src, y * static_cast<int>(g.pitch) + x, ps, v, src_s, ls.e);
     CT m[9];
     moments9(v, m);
     r = m[0];
@@ -135,13 +138,13 @@ __device__ __forceinline__ void cell_moments(const PlanePtrs<T>& src, const Geom
 
 template <typename T, int BC>
 __global__ void moments_kernel(PlanePtrs<T> src, Geometry g, BaseState b, double* rho_dev,
-                               double* ux, double* uy) {
+                               double* ux, double* uy, LineSource ls) {
     using CT = typename Codec<T>::CT;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= g.nx || y >= g.ny) return;
     CT r, jx, jy;
-    cell_moments<T, BC>(src, g, x, y, r, jx, jy);
+    cell_moments<T, BC>(src, g, x, y, r, jx, jy, ls);
     const long long c = (long long)y * g.nx + x;
     const double rho = b.rho0 + double(r);
     if (rho_dev) rho_dev[c] = double(r);
@@ -163,7 +166,7 @@ constexpr int kDiagThreads = 256;
 template <typename T, int BC>
 __global__ void __launch_bounds__(kDiagThreads)
     diag_partial_kernel(PlanePtrs<T> src, Geometry g, BaseState b, int x0, int y0, int x1, int y1,
-                        double* partial) {
+                        double* partial, LineSource ls) {
     using CT = typename Codec<T>::CT;
     double acc[kDiag] = {0, 0, 0, 0, 0, 0};
     const CT rho0 = CT(b.rho0), ux0 = CT(b.ux0), uy0 = CT(b.uy0);
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(kDiagThreads)
         for (int x = x0 + blockIdx.x * kDiagThreads + threadIdx.x; x < x1;
              x += gridDim.x * kDiagThreads) {
             CT r, jx, jy;
-            cell_moments<T, BC>(src, g, x, y, r, jx, jy);
+            cell_moments<T, BC>(src, g, x, y, r, jx, jy, ls);
             // u - u0 = (j' - rho' u0) / rho, with j' = j - rho0 u0
             const CT inv = CT(1) / (rho0 + r);
             const CT dux = (jx - r * ux0) * inv;
@@ -232,19 +235,22 @@ cudaError_t init_t(void* dst, const Geometry& g, const BaseState& b, const doubl
 
 template <typename T>
 cudaError_t moments_t(const void* src, const Geometry& g, const BaseState& b, int bc, double* r,
-                      double* ux, double* uy, cudaStream_t st) {
+                      double* ux, double* uy, cudaStream_t st, const LineSource& ls) {
     const dim3 block(128, 2), grid((g.nx + 127) / 128, (g.ny + 1) / 2);
     const PlanePtrs<T> s = plane_ptrs<T>(const_cast<void*>(src), g.plane);
     if (bc == kPeriodic)
-        moments_kernel<T, kPeriodic><<<grid, block, 0, st>>>(s, g, b, r, ux, uy);
+        moments_kernel<T, kPeriodic><<<grid, block, 0, st>>>(s, g, b, r, ux, uy, ls);
+    else if (bc == kChannel)
+        moments_kernel<T, kChannel><<<grid, block, 0, st>>>(s, g, b, r, ux, uy, ls);
     else
-        moments_kernel<T, kDirichlet><<<grid, block, 0, st>>>(s, g, b, r, ux, uy);
+        moments_kernel<T, kDirichlet><<<grid, block, 0, st>>>(s, g, b, r, ux, uy, ls);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t diag_t(const void* src, const Geometry& g, const BaseState& b, int bc, int x0, int y0,
-                   int x1, int y1, double* partial, double* out, cudaStream_t st) {
+                   int x1, int y1, double* partial, double* out, cudaStream_t st,
+                   const LineSource& ls) {
     const PlanePtrs<T> s = plane_ptrs<T>(const_cast<void*>(src), g.plane);
     const int w = x1 - x0, h = y1 - y0;
     const int gx = w <= 0 ? 1 : (w + kDiagThreads - 1) / kDiagThreads < 4 ? (w + kDiagThreads - 1) / kDiagThreads : 4;
@@ -253,9 +259,11 @@ cudaError_t diag_t(const void* src, const Geometry& g, const BaseState& b, int b
     if (gy < 1) gy = 1;
     const dim3 grid(gx, gy);
     if (bc == kPeriodic)
-        diag_partial_kernel<T, kPeriodic><<<grid, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial);
+        diag_partial_kernel<T, kPeriodic><<<grid, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial, ls);
+    else if (bc == kChannel)
+        diag_partial_kernel<T, kChannel><<<grid, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial, ls);
     else
-        diag_partial_kernel<T, kDirichlet><<<grid, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial);
+        diag_partial_kernel<T, kDirichlet><<<grid, kDiagThreads, 0, st>>>(s, g, b, x0, y0, x1, y1, partial, ls);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final_kernel<<<1, kDiagThreads, 0, st>>>(partial, gx * gy, out);
@@ -290,24 +298,26 @@ cudaError_t launch_init_pulse(int storage, void* dst, const Geometry& g, const B
 }
 
 cudaError_t launch_moments(int storage, const void* src, const Geometry& g, const BaseState& b,
-                           int bc, double* rho_dev, double* ux, double* uy, cudaStream_t st) {
+                           int bc, double* rho_dev, double* ux, double* uy, cudaStream_t st,
+                           const LineSource& ls) {
     switch (storage) {
-        case kF64: return moments_t<double>(src, g, b, bc, rho_dev, ux, uy, st);
-        case kF32: return moments_t<float>(src, g, b, bc, rho_dev, ux, uy, st);
-        case kF16: return moments_t<__half>(src, g, b, bc, rho_dev, ux, uy, st);
-        case kBF16: return moments_t<__nv_bfloat16>(src, g, b, bc, rho_dev, ux, uy, st);
+        case kF64: return moments_t<double>(src, g, b, bc, rho_dev, ux, uy, st, ls);
+        case kF32: return moments_t<float>(src, g, b, bc, rho_dev, ux, uy, st, ls);
+        case kF16: return moments_t<__half>(src, g, b, bc, rho_dev, ux, uy, st, ls);
+        case kBF16: return moments_t<__nv_bfloat16>(src, g, b, bc, rho_dev, ux, uy, st, ls);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_diagnostics(int storage, const void* src, const Geometry& g,
                                const BaseState& b, int bc, int x0, int y0, int x1, int y1,
-                               double* partial, double* out, cudaStream_t st) {
+                               double* partial, double* out, cudaStream_t st,
+                               const LineSource& ls) {
     switch (storage) {
-        case kF64: return diag_t<double>(src, g, b, bc, x0, y0, x1, y1, partial, out, st);
-        case kF32: return diag_t<float>(src, g, b, bc, x0, y0, x1, y1, partial, out, st);
-        case kF16: return diag_t<__half>(src, g, b, bc, x0, y0, x1, y1, partial, out, st);
-        case kBF16: return diag_t<__nv_bfloat16>(src, g, b, bc, x0, y0, x1, y1, partial, out, st);
+        case kF64: return diag_t<double>(src, g, b, bc, x0, y0, x1, y1, partial, out, st, ls);
+        case kF32: return diag_t<float>(src, g, b, bc, x0, y0, x1, y1, partial, out, st, ls);
+        case kF16: return diag_t<__half>(src, g, b, bc, x0, y0, x1, y1, partial, out, st, ls);
+        case kBF16: return diag_t<__nv_bfloat16>(src, g, b, bc, x0, y0, x1, y1, partial, out, st, ls);
     }
     return cudaErrorInvalidValue;
 }

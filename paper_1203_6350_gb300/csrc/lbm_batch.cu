@@ -1082,7 +1082,7 @@ int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* 
     const int cur = (int)(in->launched & 1);
     cudaError_t e = lbm::launch_moments(b->storage, in->buf[cur], in->geo,
                                         lbm::BaseState{in->rho0, in->ux0, in->uy0}, in->bc, dr, dx, dy,
-                                        b->stream);
+                                        b->stream, lbm::LineSource{});
     if (e == cudaSuccess && !on_device) {
         if (rho_dev) e = cudaMemcpyAsync(rho_dev, dr, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
@@ -1105,7 +1105,7 @@ int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, d
     double* res = b->d_diag + lbm::kDiagBlocks * lbm::kDiag;
     cudaError_t e = lbm::launch_diagnostics(b->storage, in->buf[cur], in->geo,
                                             lbm::BaseState{in->rho0, in->ux0, in->uy0}, in->bc, x0,
-                                            y0, x1, y1, b->d_diag, res, b->stream);
+                                            y0, x1, y1, b->d_diag, res, b->stream, lbm::LineSource{});
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, lbm::kDiag * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_diagnostics: ") + cudaGetErrorString(e));

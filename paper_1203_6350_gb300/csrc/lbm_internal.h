@@ -2,6 +2,7 @@
 // Not part of the public interface (include/lbm.h is).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
@@ -155,7 +156,33 @@ inline void zero_run(const double* a, int n, int& lo, int& hi) {
 
 enum Storage { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum Variant { kNone = 0, kTypeI = 1, kTypeII = 2, kTypeIII = 3, kViscous = 4 };
-enum Bc { kDirichlet = 0, kPeriodic = 1 };
+// Boundary: Dirichlet far field; periodic in both axes; channel (the line
+// source of Sec. 4.2: source on the left edge, outflow on the right, periodic
+// in y).
+enum Bc { kDirichlet = 0, kPeriodic = 1, kChannel = 2 };
+
+// The line source of the channel boundary.  The populations entering at the
+// left edge are those of the source column's equilibrium at the time of the
+// post-collision state they leave; as deviations from the base state they are
+// amp sin(omega t + phase) e_i with e_i = f^eq_i(1, u0) (the equilibrium is
+// linear in rho at fixed u).  A pull that yields the state of time tau uses
+// t = tau - 1, tau = (time ? *time : 0) + t_off.
+struct LineSource {
+    const long long* time;  // device step counter (or nullptr)
+    long long t_off;
+    double amp, omega, phase;
+    double e[9];
+};
+
+// Source deviation scale of the state that a pull with source `s` yields.
+__host__ __device__ inline double line_source_scale(const LineSource& s) {
+#ifdef __CUDA_ARCH__
+    const long long tau = (s.time ? *s.time : 0) + s.t_off;
+#else
+    const long long tau = s.t_off;
+#endif
+    return s.amp * sin(s.omega * (double)(tau - 1) + s.phase);
+}
 
 // Step launchers, one translation unit per storage type.  src holds the
 // post-collision state of time t (pulled), dst receives that of time t + 1.
@@ -163,31 +190,31 @@ enum Bc { kDirichlet = 0, kPeriodic = 1 };
 cudaError_t launch_step_f64(const void* src, void* dst, const Geometry& g,
                             const StepConst<double>& k, const AxisCoef<double>* tx,
                             const AxisCoef<double>* ty, int variant, int bc, cudaStream_t st,
-                            int pdl);
+                            int pdl, const LineSource& ls);
 cudaError_t launch_step_f32(const void* src, void* dst, const Geometry& g,
                             const StepConst<float>& k, const AxisCoef<float>* tx,
                             const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
-                            int pdl);
+                            int pdl, const LineSource& ls);
 cudaError_t launch_step_f16(const void* src, void* dst, const Geometry& g,
                             const StepConst<float>& k, const AxisCoef<float>* tx,
                             const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
-                            int pdl);
+                            int pdl, const LineSource& ls);
 cudaError_t launch_step_bf16(const void* src, void* dst, const Geometry& g,
                              const StepConst<float>& k, const AxisCoef<float>* tx,
                              const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
-                            int pdl);
+                             int pdl, const LineSource& ls);
 
 // Two-cells-per-thread step launchers (FP32 and 16-bit storage; packed FP32
 // compute).  cudaErrorInvalidValue when 9 planes exceed 2^32 elements.
 cudaError_t launch_step2_f32(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
                              const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
-                             int bc, cudaStream_t st, int pdl);
+                             int bc, cudaStream_t st, int pdl, const LineSource& ls);
 cudaError_t launch_step2_f16(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
                              const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
-                             int bc, cudaStream_t st, int pdl);
+                             int bc, cudaStream_t st, int pdl, const LineSource& ls);
 cudaError_t launch_step2_bf16(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
                               const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
-                              int bc, cudaStream_t st, int pdl);
+                              int bc, cudaStream_t st, int pdl, const LineSource& ls);
 
 // Two steps per launch (temporal blocking through shared memory) on the
 // two-cells-per-thread arithmetic: src holds time t, dst receives t + 2.
@@ -218,16 +245,19 @@ cudaError_t launch_init(int storage, void* dst, const Geometry& g, const BaseSta
 cudaError_t launch_init_pulse(int storage, void* dst, const Geometry& g, const BaseState& b,
                               double eps, double half_width, double xc, double yc, int bc,
                               cudaStream_t st);
-// Fields of the current time (device outputs, any may be null).
+// Fields of the current time (device outputs, any may be null).  ls: the
+// line source (channel boundary, with t_off = the current time), else unused.
 cudaError_t launch_moments(int storage, const void* src, const Geometry& g, const BaseState& b,
-                           int bc, double* rho_dev, double* ux, double* uy, cudaStream_t st);
+                           int bc, double* rho_dev, double* ux, double* uy, cudaStream_t st,
+                           const LineSource& ls);
 // Diagnostics: first pass writes `blocks` partial sums of kDiag doubles to
 // partial[], second pass reduces them in a fixed order into out[kDiag].
 constexpr int kDiag = 6;
 constexpr int kDiagBlocks = 608;  // 4 per SM on a 152-SM GB300
 cudaError_t launch_diagnostics(int storage, const void* src, const Geometry& g,
                                const BaseState& b, int bc, int x0, int y0, int x1, int y1,
-                               double* partial, double* out, cudaStream_t st);
+                               double* partial, double* out, cudaStream_t st,
+                               const LineSource& ls);
 
 // Bytes per stored population.
 inline size_t storage_bytes(int storage) {

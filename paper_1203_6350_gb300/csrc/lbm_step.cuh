@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kStepBX* kStepBY)
     step_kernel(PlanePtrs<T> src, PlanePtrs<T> dst, int nx, int ny, int pitch,
                 StepConst<typename Codec<T>::CT> k,
                 const AxisCoef<typename Codec<T>::CT>* __restrict__ tx,
-                const AxisCoef<typename Codec<T>::CT>* __restrict__ ty) {
+                const AxisCoef<typename Codec<T>::CT>* __restrict__ ty, LineSource ls) {
     using CT = typename Codec<T>::CT;
     const int bx0 = blockIdx.x * kStepBX, by0 = blockIdx.y * kStepBY;
     const int x = bx0 + threadIdx.x;
@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(kStepBX* kStepBY)
         pull_all<T, BC, false>(src, o, ps, v);
     } else {
         ps.edge<BC>(x, y, nx, ny, pitch);
-        pull_all<T, BC, true>(src, o, ps, v);
+        // the channel's source edge: its deviation scale at this step
+        const double src_s = (BC == kChannel && x == 0) ? line_source_scale(ls) : 0.0;
+        pull_all<T, BC, true>(src, o, ps, v, src_s, ls.e);
     }
     collide_cell<CT, VAR>(v, x, y, k, tx, ty);
     store_all<T>(dst, o, v);
@@ -89,7 +91,7 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geometry& g,
                           const StepConst<typename Codec<T>::CT>& k,
                           const AxisCoef<typename Codec<T>::CT>* tx,
                           const AxisCoef<typename Codec<T>::CT>* ty, int variant, int bc,
-                          cudaStream_t st, int pdl) {
+                          cudaStream_t st, int pdl, const LineSource& ls) {
     const PlanePtrs<T> s = plane_ptrs<T>(const_cast<void*>(src), g.plane);
     const PlanePtrs<T> d = plane_ptrs<T>(dst, g.plane);
     const int pitch = static_cast<int>(g.pitch);
@@ -105,7 +107,7 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geometry& g,
     cfg.numAttrs = pdl ? 1 : 0;
 #define LBM_STEP_CASE(V, B)                                                                  \
     if (variant == V && bc == B)                                                             \
-        return cudaLaunchKernelEx(&cfg, step_kernel<T, V, B>, s, d, g.nx, g.ny, pitch, k, tx, ty);
+        return cudaLaunchKernelEx(&cfg, step_kernel<T, V, B>, s, d, g.nx, g.ny, pitch, k, tx, ty, ls);
     LBM_STEP_CASE(kNone, kDirichlet)
     LBM_STEP_CASE(kTypeI, kDirichlet)
     LBM_STEP_CASE(kTypeII, kDirichlet)
@@ -116,6 +118,11 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geometry& g,
     LBM_STEP_CASE(kTypeII, kPeriodic)
     LBM_STEP_CASE(kTypeIII, kPeriodic)
     LBM_STEP_CASE(kViscous, kPeriodic)
+    LBM_STEP_CASE(kNone, kChannel)
+    LBM_STEP_CASE(kTypeI, kChannel)
+    LBM_STEP_CASE(kTypeII, kChannel)
+    LBM_STEP_CASE(kTypeIII, kChannel)
+    LBM_STEP_CASE(kViscous, kChannel)
 #undef LBM_STEP_CASE
     return cudaErrorInvalidValue;
 }

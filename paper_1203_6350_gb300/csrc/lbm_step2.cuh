@@ -122,16 +122,23 @@ __device__ __forceinline__ void pull_pair_interior(const T* __restrict__ s, unsi
 
 // Population I of cell (c, y) pulled from (c - c_ix, y - c_iy) with the
 // boundary rule: a Dirichlet far-field wall contributes a zero deviation,
-// periodic wraps.  The phantom cell c = nx of an odd-width lattice reads
-// nothing (its result is never stored).
+// periodic wraps, the channel wraps y, takes the source src_s * src_e[I] at
+// its left edge and the last column's own value at its right edge (outflow).
+// The phantom cell c = nx of an odd-width lattice reads nothing (its result
+// is never stored).
 template <typename T, int BC, int I>
 __device__ __forceinline__ float pull_one(const T* __restrict__ s, unsigned plane, int pitch,
-                                          int c, int y, int nx, int ny) {
+                                          int c, int y, int nx, int ny, double src_s = 0.0,
+                                          const double* src_e = nullptr) {
     if (c >= nx) return 0.0f;
     int sx = c - cx(I), sy = y - cy(I);
     if (BC == kPeriodic) {
         sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+    } else if (BC == kChannel) {
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        if (sx < 0) return static_cast<float>(src_s * src_e[I]);
+        if (sx >= nx) sx = nx - 1;
     } else if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
         return 0.0f;
     }
@@ -140,23 +147,25 @@ __device__ __forceinline__ float pull_one(const T* __restrict__ s, unsigned plan
 
 template <typename T, int BC, int I>
 __device__ __forceinline__ F2 pull_pair_one(const T* __restrict__ s, unsigned plane, int pitch,
-                                            int x, int y, int nx, int ny) {
-    return f2(pull_one<T, BC, I>(s, plane, pitch, x, y, nx, ny),
-              pull_one<T, BC, I>(s, plane, pitch, x + 1, y, nx, ny));
+                                            int x, int y, int nx, int ny, double src_s,
+                                            const double* src_e) {
+    return f2(pull_one<T, BC, I>(s, plane, pitch, x, y, nx, ny, src_s, src_e),
+              pull_one<T, BC, I>(s, plane, pitch, x + 1, y, nx, ny, src_s, src_e));
 }
 
 template <typename T, int BC>
 __device__ __forceinline__ void pull_pair_edge(const T* __restrict__ s, unsigned plane, int pitch,
-                                               int x, int y, int nx, int ny, F2 (&v)[9]) {
-    v[0] = pull_pair_one<T, BC, 0>(s, plane, pitch, x, y, nx, ny);
-    v[1] = pull_pair_one<T, BC, 1>(s, plane, pitch, x, y, nx, ny);
-    v[2] = pull_pair_one<T, BC, 2>(s, plane, pitch, x, y, nx, ny);
-    v[3] = pull_pair_one<T, BC, 3>(s, plane, pitch, x, y, nx, ny);
-    v[4] = pull_pair_one<T, BC, 4>(s, plane, pitch, x, y, nx, ny);
-    v[5] = pull_pair_one<T, BC, 5>(s, plane, pitch, x, y, nx, ny);
-    v[6] = pull_pair_one<T, BC, 6>(s, plane, pitch, x, y, nx, ny);
-    v[7] = pull_pair_one<T, BC, 7>(s, plane, pitch, x, y, nx, ny);
-    v[8] = pull_pair_one<T, BC, 8>(s, plane, pitch, x, y, nx, ny);
+                                               int x, int y, int nx, int ny, F2 (&v)[9],
+                                               double src_s = 0.0, const double* src_e = nullptr) {
+    v[0] = pull_pair_one<T, BC, 0>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[1] = pull_pair_one<T, BC, 1>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[2] = pull_pair_one<T, BC, 2>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[3] = pull_pair_one<T, BC, 3>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[4] = pull_pair_one<T, BC, 4>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[5] = pull_pair_one<T, BC, 5>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[6] = pull_pair_one<T, BC, 6>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[7] = pull_pair_one<T, BC, 7>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+    v[8] = pull_pair_one<T, BC, 8>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
 }
 
 template <typename T, int I>
@@ -237,7 +246,7 @@ template <typename T, int VAR, int BC>
 __global__ void __launch_bounds__(kPairBX* kPairBY)
     step2_kernel(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
                  unsigned plane, StepConst<F2> k, const AxisCoef<float>* __restrict__ tx,
-                 const AxisCoef<float>* __restrict__ ty) {
+                 const AxisCoef<float>* __restrict__ ty, LineSource ls) {
     const int x = 2 * (blockIdx.x * kPairBX + threadIdx.x);
     const int y = blockIdx.y * kPairBY + threadIdx.y;
     // Launched as a programmatic dependent of the previous step: wait until that
@@ -251,10 +260,13 @@ __global__ void __launch_bounds__(kPairBX* kPairBY)
     // per thread: both cells and all their sources inside the lattice
     const bool interior = x > 0 && x + 2 < nx && y > 0 && y + 1 < ny;
     F2 v[9];
-    if (interior)
+    if (interior) {
         pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch), o, v);
-    else
-        pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v);
+    } else {
+        // the channel's source edge: its deviation scale at this step
+        const double src_s = (BC == kChannel && x == 0) ? line_source_scale(ls) : 0.0;
+        pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v, src_s, ls.e);
+    }
     collide_pair<VAR>(v, x, y, nx, k, tx, ty);
     if (x + 1 < nx)
         store_pair<T>(dst, plane, o, v);
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(kPairBX* kPairBY)
 template <typename T>
 cudaError_t launch_step2_t(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
                            const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
-                           int bc, cudaStream_t st, int pdl) {
+                           int bc, cudaStream_t st, int pdl, const LineSource& ls) {
     if (9 * g.plane >= (1ll << 32)) return cudaErrorInvalidValue;
     const T* s = static_cast<const T*>(src);
     T* d = static_cast<T*>(dst);
@@ -288,7 +300,7 @@ cudaError_t launch_step2_t(const void* src, void* dst, const Geometry& g, const 
 #define LBM_STEP2_CASE(V, B)                                                                  \
     if (variant == V && bc == B)                                                              \
         return cudaLaunchKernelEx(&cfg, step2_kernel<T, V, B>, s, d, g.nx, g.ny, pitch, plane, k, \
-                                  tx, ty);
+                                  tx, ty, ls);
     LBM_STEP2_CASE(kNone, kDirichlet)
     LBM_STEP2_CASE(kTypeI, kDirichlet)
     LBM_STEP2_CASE(kTypeII, kDirichlet)
@@ -299,6 +311,11 @@ cudaError_t launch_step2_t(const void* src, void* dst, const Geometry& g, const 
     LBM_STEP2_CASE(kTypeII, kPeriodic)
     LBM_STEP2_CASE(kTypeIII, kPeriodic)
     LBM_STEP2_CASE(kViscous, kPeriodic)
+    LBM_STEP2_CASE(kNone, kChannel)
+    LBM_STEP2_CASE(kTypeI, kChannel)
+    LBM_STEP2_CASE(kTypeII, kChannel)
+    LBM_STEP2_CASE(kTypeIII, kChannel)
+    LBM_STEP2_CASE(kViscous, kChannel)
 #undef LBM_STEP2_CASE
     return cudaErrorInvalidValue;
 }

@@ -6,8 +6,8 @@ namespace lbm {
 
 cudaError_t launch_step2_f16(const void* src, void* dst, const Geometry& g, const StepConst<F2>& k,
                            const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
-                           int bc, cudaStream_t st, int pdl) {
-    return launch_step2_t<__half>(src, dst, g, k, tx, ty, variant, bc, st, pdl);
+                           int bc, cudaStream_t st, int pdl, const LineSource& ls) {
+    return launch_step2_t<__half>(src, dst, g, k, tx, ty, variant, bc, st, pdl, ls);
 }
 
 cudaError_t launch_step_tb2_f16(const void* src, void* dst, const Geometry& g,

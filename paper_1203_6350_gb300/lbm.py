@@ -31,7 +31,7 @@ LBM_ERR_TOO_LARGE = -6
 
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
 VARIANT = {"none": 0, "I": 1, "II": 2, "III": 3, "viscous": 4}
-BC = {"dirichlet": 0, "periodic": 1}
+BC = {"dirichlet": 0, "periodic": 1, "channel": 2}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 
 
@@ -77,6 +77,7 @@ SIGNATURES = [
     ("lbm_set_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, _i64]),
     ("lbm_time", _i64, [_vp]),
     ("lbm_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("lbm_set_source", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     ("lbm_set_launch_mode", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_set_cells_per_thread", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_cells_per_thread", ctypes.c_int, [_vp]),
@@ -219,6 +220,10 @@ def lbm_time(h) -> int:
 
 def lbm_set_stream(h, stream) -> int:
     return load().lbm_set_stream(h, stream)
+
+
+def lbm_set_source(h, amplitude, omega, phase) -> int:
+    return load().lbm_set_source(h, float(amplitude), float(omega), float(phase))
 
 
 LAUNCH_MODES = {"plain": 0, "pdl": 1, "graph": 2}
@@ -427,6 +432,8 @@ class Lattice:
         whose initial state is a pulse described by eps, b, x0, y0)."""
         lat = cls(w.nx, w.ny, storage or w.storage, w.rho0, w.u0, w.s, w.n, w.m, w.bc, **kw)
         lat.set_sponge(w.variant, w.chi_x, w.chi_y, w.rho_f, w.u_f)
+        if w.bc == "channel":
+            lat.set_source(*getattr(w, "source", (0.0, 0.0, 0.0)))
         if init == "pulse" and w.rho_dev is None:
             mt = w.meta
             lat.init_pulse(mt.get("eps", 0.0), mt.get("b", 1.0), mt.get("x0", 0.0),
@@ -434,6 +441,11 @@ class Lattice:
         else:
             lat.init_equilibrium(*w.initial_fields())
         return lat
+
+    def set_source(self, amplitude: float, omega: float, phase: float = 0.0) -> None:
+        """Line source of a channel lattice (Sec. 4.2): rho0 + amplitude
+        sin(omega t + phase) on the left edge."""
+        check(lbm_set_source(self.h, amplitude, omega, phase), self.h, "lbm_set_source")
 
     def set_stream(self, stream) -> None:
         """Issue later work on `stream` (a torch.cuda.Stream); the caller orders
