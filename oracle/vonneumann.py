@@ -95,3 +95,64 @@ def max_growth(variant: str, s: float, chi: float, u_f=(0.0, 0.0), theta: float 
         k = (kk * np.cos(theta), kk * np.sin(theta))
         best = max(best, float(np.max(np.abs(spectrum(k, J)))))
     return best
+
+
+# ---------------------------------------------------------------------------
+# Stability maps (the critical damping strength of Sec. 3.3 as a function of
+# the rates, the target flow and the wave direction).
+#
+# growth(): the largest |lambda| over the wave numbers
+#     k_j = (pi j / nk) (cos theta, sin theta),  j = 0 .. nk,
+# i.e. the uniform mode (which carries the chi <= 4/s limit of
+# Eq. criticalchi) and nk wave numbers up to the grid's cut-off pi.
+#
+# chi_crit(): the smallest damping strength at which the scheme turns
+# unstable, found the plain way.  chi is scanned on nscan equally spaced
+# values of [chi_lo, chi_hi]; "unstable" means growth > 1 + tol.  If the
+# first value is already unstable the result is -inf; if no value is, +inf.
+# Otherwise the interval between the last stable and the first unstable scan
+# value is halved `iters` times and its midpoint returned.
+# ---------------------------------------------------------------------------
+
+def wavenumbers(nk: int, theta: float) -> np.ndarray:
+    """[nk + 1, 2]: k_j = (pi j / nk)(cos theta, sin theta), j = 0..nk (k = 0 only
+    when nk = 0)."""
+    mag = np.array([0.0]) if nk == 0 else np.pi * np.arange(nk + 1) / nk
+    return mag[:, None] * np.array([np.cos(theta), np.sin(theta)])[None, :]
+
+
+def growth(variant: str, s9, chi: float, n: float = 0.5, m: float = 0.5, u_f=(0.0, 0.0),
+           theta: float = 0.0, nk: int = 400, rho_f: float = 1.0):
+    """(max_j max_i |lambda_i(G(k_j))|, |k_j| at which it occurs) over wavenumbers()."""
+    J = jacobian(variant, s9, chi, n, m, rho_f, u_f)
+    best, kbest = -1.0, 0.0
+    for k in wavenumbers(nk, theta):
+        g = float(np.max(np.abs(spectrum(k, J))))
+        if g > best:
+            best, kbest = g, float(np.hypot(*k))
+    return best, kbest
+
+
+def chi_crit(variant: str, s9, n: float = 0.5, m: float = 0.5, u_f=(0.0, 0.0),
+             theta: float = 0.0, nk: int = 400, chi_lo: float = 0.0, chi_hi: float = 8.0,
+             nscan: int = 17, iters: int = 40, tol: float = 1e-9) -> float:
+    """Critical damping strength by scan and bisection (see the block comment)."""
+    def unstable(chi):
+        return growth(variant, s9, chi, n, m, u_f, theta, nk)[0] > 1.0 + tol
+
+    grid = chi_lo + (chi_hi - chi_lo) * np.arange(nscan) / (nscan - 1)
+    if unstable(grid[0]):
+        return -np.inf
+    for g in range(1, nscan):
+        if unstable(grid[g]):
+            a, b = grid[g - 1], grid[g]
+            break
+    else:
+        return np.inf
+    for _ in range(iters):
+        mid = 0.5 * (a + b)
+        if unstable(mid):
+            b = mid
+        else:
+            a = mid
+    return 0.5 * (a + b)

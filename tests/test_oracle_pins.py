@@ -222,6 +222,73 @@ def test_von_neumann_small_k_matches_navier_stokes_modes():
         np.testing.assert_allclose(omega.imag, -nu * kk**2, rtol=0.05)
 
 
+def test_critical_chi_map_closed_forms():
+    """The stability map's critical chi (scan over [0, 8] then bisection, growth
+    over k_j = pi j / nk including the uniform mode) against what Sec. 3.3 fixes:
+    type II with equal rates turns unstable at 4/s (Eq. criticalchi), type I at
+    2 - s (Eq. effectrelax, Fig. 1a), type II keeps 4/s with u^f = (0.1, 0)
+    (Fig. 8), type III with u^f = (0.1, 0) lies between 2.5/s and 3/s (Fig. 9).
+    For type II both the uniform mode and the k = pi mode along x turn critical
+    at 4/s, so the coarse grid nk = 4 finds it as well as nk = 64."""
+    from oracle import vonneumann as vn
+
+    for s in (1.5, 1.9, 1.99):
+        for nk in (4, 64):
+            c = vn.chi_crit("II", vn.rates(s), nk=nk, iters=34)
+            assert abs(c - 4 / s) < 1e-6, (s, nk, c)
+        c = vn.chi_crit("I", vn.rates(s), nk=64, chi_hi=1.0, iters=34)
+        assert abs(c - (2 - s)) < 1e-6, (s, c)
+    c = vn.chi_crit("II", vn.rates(1.99), u_f=(0.1, 0.0), nk=64, iters=34)
+    assert abs(c - 4 / 1.99) < 1e-6, c
+    c = vn.chi_crit("III", vn.rates(1.99), u_f=(0.1, 0.0), nk=64, chi_hi=4.0, iters=34)
+    assert 2.5 / 1.99 < c < 3 / 1.99, c
+    # the s_c = 0 reading moves the threshold far above 4/s (reading C3)
+    assert vn.chi_crit("II", vn.rates(1.99, 0.0), nk=64, iters=20) > 4 / 1.99 + 0.1
+    # end cases of the scan
+    assert vn.chi_crit("I", vn.rates(1.99), nk=8, chi_lo=0.05, chi_hi=1.0) == -np.inf
+    assert vn.chi_crit("II", vn.rates(1.9), nk=8, chi_hi=2.0) == np.inf
+
+
+def test_growth_on_the_wavenumber_grid():
+    """k_j runs over pi j / nk along theta and includes k = 0: with chi = 0 the
+    conserved modes give growth exactly 1 (Eq. th:d at k = 0); for the uniform
+    mode alone (nk = 0) type II gives the closed form of Eq. criticalchi,
+    |1 + n chi - s n chi - chi| / (1 + n chi), reached at k = 0."""
+    from oracle import vonneumann as vn
+
+    k = vn.wavenumbers(4, np.pi / 6)
+    np.testing.assert_allclose(np.hypot(k[:, 0], k[:, 1]), np.pi * np.arange(5) / 4, atol=1e-15)
+    np.testing.assert_allclose(k[2], (np.pi / 2) * np.array([np.cos(np.pi / 6), np.sin(np.pi / 6)]))
+    for s in (1.2, 1.9):
+        g, _ = vn.growth("none", vn.rates(s), 0.0, u_f=(0.1, 0.05), theta=0.3, nk=32)
+        assert abs(g - 1) < 1e-12, g
+        for chi in (0.5, 4 / s + 0.2):
+            # k = 0: the conserved modes decay by lam, the others by 1 - s
+            g, kk = vn.growth("II", vn.rates(s), chi, nk=0)
+            lam = (1 + 0.5 * chi - s * 0.5 * chi - chi) / (1 + 0.5 * chi)
+            assert kk == 0.0 and abs(g - max(abs(lam), abs(1 - s))) < 1e-12, (s, chi, g, lam)
+
+
+def test_critical_chi_bounds_with_distinct_rates():
+    """Distinct MRT rates (App. A.1 S with s_e, s_eps, s_q, s_nu apart): the uniform
+    mode alone fixes upper bounds on the critical chi, so the map can never lie
+    above them: type II at most 4/s_c (Eq. criticalchi with the conserved rate),
+    type I at most 2 - max s_k over the non-conserved rates (Eq. effectrelax).
+    Checked on seeded random rates, target flows and directions."""
+    from oracle import vonneumann as vn
+
+    rng = np.random.default_rng(11)
+    for _ in range(6):
+        sc = rng.uniform(1.2, 1.99)
+        s9 = np.concatenate([[sc] * 3, rng.uniform(1.0, 1.99, 6)])
+        uf = tuple(rng.uniform(-0.1, 0.1, 2))
+        th = rng.uniform(0, np.pi / 2)
+        c2 = vn.chi_crit("II", s9, u_f=uf, theta=th, nk=32, iters=24)
+        assert c2 <= 4 / sc + 1e-6, (s9, c2)
+        c1 = vn.chi_crit("I", s9, u_f=uf, theta=th, nk=32, chi_hi=1.0, iters=24)
+        assert c1 <= 2 - s9[3:].max() + 1e-6, (s9, c1)
+
+
 @pytest.mark.parametrize("variant,s,chi,uf", [
     ("II", 1.99, 4 / 1.99 - 0.1, (0.0, 0.0)),
     ("I", 1.9, 0.1, (0.0, 0.0)),
