@@ -346,6 +346,7 @@ def run_native(args):
     roof_large = roofline_large(peaks)
     sweep = None if args.no_sweep else run_roofline_sweep(peaks)
     line_source = None if args.no_sweep else run_line_source(peaks)
+    stability_map = None if args.no_sweep else run_stability_map()
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -374,6 +375,7 @@ def run_native(args):
             "reflected_energy": {k: refl.get(k) for k in VARIANTS},
             "roofline_sweep": sweep,
             "line_source": line_source,
+            "stability_map": stability_map,
             "batched": batched,
             "serving": serving,
         }
@@ -524,6 +526,65 @@ def run_line_source(peaks):
             "interior_rel_l2_vs_unbounded": {
                 "no_layer": interior("none", 0), "viscosity_sponge_160": interior("viscous", 160),
                 "type_II_160": interior("II", 160), "type_II_58_one_wavelength": interior("II", 58)}}
+
+
+def run_stability_map(nk=128, nscan=17, iters=30, chi_hi=8.0):
+    """Critical damping strength over the map of workloads.stability_map (1215
+    cases: 3 shear rates x 9 bulk / heat-flux rate pairs x 5 target flows x 3
+    wave directions x types I-III), FP32 and FP64, timed with CUDA events
+    around the synchronous call; the oracle's scan-and-bisection timed on two
+    cases of the same map."""
+    import torch
+
+    from paper_1203_6350_gb300 import stability as st
+
+    variants, cases = wl.stability_map()
+    kw = dict(nk=nk, nscan=nscan, iters=iters, chi_hi=chi_hi)
+    step = chi_hi / (nscan - 1)
+    out = {"cases": len(variants), "nk": nk, "nscan": nscan, "iters": iters,
+           "chi_range": [0.0, chi_hi]}
+    res = {}
+    for prec in ("f32", "f64"):
+        st.chi_crit(variants[:304], cases[:304], precision=prec, **kw)  # warm-up
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record()
+        chi = st.chi_crit(variants, cases, precision=prec, **kw)
+        z.record()
+        z.synchronize()
+        t = a.elapsed_time(z) / 1e3
+        # growth evaluations: chi = 0, the scan up to the first unstable value, the bisection
+        evals = 0
+        for c in chi:
+            if c == -np.inf:
+                evals += 1
+            elif c == np.inf:
+                evals += nscan
+            else:
+                evals += 1 + int(c // step) + 1 + iters
+        eig = evals * (nk + 1)
+        res[prec] = chi
+        out[prec] = {"seconds": t, "cases_per_s": len(chi) / t, "eigenproblems": eig,
+                     "eigenproblems_per_s": eig / t}
+    fin = np.isfinite(res["f64"]) & np.isfinite(res["f32"])
+    out["f32_vs_f64_max_abs_chi"] = float(np.abs(res["f32"] - res["f64"])[fin].max())
+    # chi_crit * s summarised per variant and target flow (min, max over the rest)
+    summary = {}
+    for v in ("I", "II", "III"):
+        for u in sorted(set(cases[:, 11])):
+            sel = np.array([x == v for x in variants]) & (cases[:, 11] == u)
+            cs = res["f64"][sel] * cases[sel, 7]
+            summary[f"{v}/U={u:g}"] = [float(cs.min()), float(cs.max())]
+    out["chi_crit_times_s_min_max"] = summary
+    # the oracle on two cases of the map
+    from oracle import vonneumann as vn
+
+    t0 = time.perf_counter()
+    for i in (len(variants) // 3 + 1, 2 * len(variants) // 3 + 7):
+        c = cases[i]
+        vn.chi_crit(variants[i], c[:9], c[9], c[10], (c[11], c[12]), c[13], tol=1e-9, **kw)
+    out["oracle_seconds_per_case"] = (time.perf_counter() - t0) / 2
+    return out
 
 
 def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", "f16dev",

@@ -383,6 +383,58 @@ int lbm_diagnostics_noalloc(const void* state, lbm_storage storage, int nx, int 
                             double rho0, double ux0, double uy0, int x0, int y0, int x1, int y1,
                             double* out, int out_on_device, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Von Neumann stability maps (Secs. 3.2-3.3).  These calls need no lattice:
+ * they evaluate the scheme linearised about a uniform state f^eq(rho^f, u^f)
+ * (the result does not depend on rho^f).  A plane wave of wave vector k is
+ * multiplied per step by G(k) = diag(exp(-i k.c_i)) J (Eq. sec:matrix), J the
+ * Jacobian of the collision with the damping term of the chosen variant at
+ * strength chi (rho* and j* solved exactly, as in the step).
+ *
+ * A case is LBM_VN_FIELDS consecutive doubles:
+ *   s[0..8]  relaxation rates in the row order of M (App. A.1; s[0..2] = s_c),
+ *   n, m     Guo weights,  ux_f, uy_f  target velocity u^f,
+ *   theta    wave direction,  chi  damping strength (ignored by lbm_vn_chi_crit),
+ * and variant[c] is LBM_SPONGE_NONE, _I, _II or _III.  n, m, chi >= 0; every
+ * field finite.
+ *
+ * The growth of a case is max_j max_i |lambda_i(G(k_j))| over
+ *   k_j = (pi j / nk)(cos theta, sin theta),  j = 0 .. nk,
+ * (the uniform mode and nk wave numbers up to the cut-off pi), computed on
+ * the GPU in FP64 (precision = LBM_F64) or FP32 (LBM_F32): Householder
+ * reduction to Hessenberg form and the shifted complex QR iteration.
+ *
+ * Inputs and outputs are HOST arrays; each call copies them, runs on
+ * cuda_stream (a borrowed cudaStream_t, NULL = legacy default stream), and
+ * synchronises it before returning.  Device scratch is allocated and freed
+ * stream-ordered inside the call.
+ *
+ * Returns LBM_OK; LBM_ERR_ARG (nothing done: bad sizes, NULL arrays, variant,
+ * precision, non-finite or negative fields, bad scan parameters);
+ * LBM_ERR_OOM; LBM_ERR_CUDA; LBM_ERR_NONFINITE when the QR iteration of some
+ * wavenumber did not converge within 270 iterations (that case's output is
+ * NaN, the others are valid).  lbm_vn_last_error() gives the message of the
+ * last failing call on the calling thread. */
+#define LBM_VN_FIELDS 15
+
+/* growth[c] and (if k_at_max != NULL) the |k_j| at which it occurs (the
+ * smallest on ties), for c < ncases (0 <= nk <= 2^24). */
+int lbm_vn_growth(const int* variant, const double* cases, int ncases, int nk, int precision,
+                  double* growth, double* k_at_max, void* cuda_stream);
+
+/* Critical damping strength of each case: chi is scanned on nscan equally
+ * spaced values chi_lo .. chi_hi (2 <= nscan <= 4096, 0 <= chi_lo < chi_hi);
+ * a value is unstable when growth > 1 + tol.  chi_crit[c] = -INFINITY if
+ * chi_lo is already unstable, +INFINITY if no scanned value is, otherwise the
+ * midpoint of the interval between the last stable and the first unstable
+ * scan value after halving it `iters` times (0 <= iters <= 200).  The smallest
+ * unstable chi of Eq. criticalchi is 4/s for type II with equal rates. */
+int lbm_vn_chi_crit(const int* variant, const double* cases, int ncases, int nk, int precision,
+                    double chi_lo, double chi_hi, int nscan, int iters, double tol,
+                    double* chi_crit, void* cuda_stream);
+
+const char* lbm_vn_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,7 @@ LBM_ERR_CUDA = -3
 LBM_ERR_NONFINITE = -4
 LBM_ERR_STATE = -5
 LBM_ERR_TOO_LARGE = -6
+LBM_VN_FIELDS = 15
 
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
 VARIANT = {"none": 0, "I": 1, "II": 2, "III": 3, "viscous": 4}
@@ -116,6 +117,12 @@ SIGNATURES = [
     ("lbm_batch_set_stream", ctypes.c_int, [_vp, _vp]),
     ("lbm_batch_last_error", ctypes.c_char_p, [_vp]),
     ("lbm_batch_destroy", None, [_vp]),
+    ("lbm_vn_growth", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                     _vp]),
+    ("lbm_vn_chi_crit", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, _vp, _vp]),
+    ("lbm_vn_last_error", ctypes.c_char_p, []),
 ]
 
 
@@ -260,6 +267,23 @@ def lbm_diagnostics_noalloc(state_ptr, storage, nx, ny, bc, rho0, ux0, uy0, x0, 
     return load().lbm_diagnostics_noalloc(state_ptr, int(storage), int(nx), int(ny), int(bc),
                                           float(rho0), float(ux0), float(uy0), int(x0), int(y0),
                                           int(x1), int(y1), out_ptr, int(out_on_device), stream)
+
+
+def lbm_vn_growth(variant_ptr, cases_ptr, ncases, nk, precision, growth_ptr, k_ptr,
+                  stream=None) -> int:
+    return load().lbm_vn_growth(variant_ptr, cases_ptr, int(ncases), int(nk), int(precision),
+                                growth_ptr, k_ptr, stream)
+
+
+def lbm_vn_chi_crit(variant_ptr, cases_ptr, ncases, nk, precision, chi_lo, chi_hi, nscan, iters,
+                    tol, out_ptr, stream=None) -> int:
+    return load().lbm_vn_chi_crit(variant_ptr, cases_ptr, int(ncases), int(nk), int(precision),
+                                  float(chi_lo), float(chi_hi), int(nscan), int(iters),
+                                  float(tol), out_ptr, stream)
+
+
+def lbm_vn_last_error() -> str:
+    return load().lbm_vn_last_error().decode()
 
 
 def lbm_batch_instance_bytes(nx, ny, storage) -> int:

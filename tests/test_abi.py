@@ -5,6 +5,8 @@ import glob
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from conftest import ROOT
@@ -105,3 +107,54 @@ def test_autotuner_configurations_cover_every_batched_kernel():
     assert {(c, s) for c, s, _, _ in autotune.configurations("f64")} == {(1, 1)}
     # the signature ignores order and buckets sizes by powers of two
     assert autotune.signature([(100, 60), (64, 33)]) == autotune.signature([(70, 40), (127, 63)])
+
+
+def test_stability_map_calls_check_arguments_before_touching_the_device(lib):
+    """lbm_vn_growth / lbm_vn_chi_crit validate every argument on the host; an
+    empty case list is a no-op.  None of these reach the device."""
+    from paper_1203_6350_gb300 import lbm, stability
+
+    assert lbm.LBM_VN_FIELDS == len(stability.FIELDS) == 15
+    with open(os.path.join(ROOT, "include", "lbm.h")) as fh:
+        assert "#define LBM_VN_FIELDS 15" in fh.read()
+    good = stability.case(1.9, chi=0.5)
+    v = np.array([2], dtype=np.int32)
+    out = np.zeros(1)
+
+    def growth(variant=v, cases=good, n=1, nk=8, prec=0, dst=out):
+        c = np.ascontiguousarray(cases, dtype=np.float64)
+        return lbm.lbm_vn_growth(variant.ctypes.data, c.ctypes.data, n, nk, prec,
+                                 None if dst is None else dst.ctypes.data, None, None)
+
+    def crit(lo=0.0, hi=8.0, nscan=17, iters=40, tol=1e-9, n=1):
+        return lbm.lbm_vn_chi_crit(v.ctypes.data, good.ctypes.data, n, 8, 0, lo, hi, nscan, iters,
+                                   tol, out.ctypes.data, None)
+
+    assert growth(n=0) == lbm.LBM_OK and crit(n=0) == lbm.LBM_OK
+    assert growth(variant=np.array([4], dtype=np.int32)) == lbm.LBM_ERR_ARG  # viscosity sponge
+    assert "variant" in lbm.lbm_vn_last_error()
+    assert growth(variant=np.array([-1], dtype=np.int32)) == lbm.LBM_ERR_ARG
+    bad = good.copy()
+    bad[3] = np.nan
+    assert growth(cases=bad) == lbm.LBM_ERR_ARG
+    bad = good.copy()
+    bad[14] = -0.1
+    assert growth(cases=bad) == lbm.LBM_ERR_ARG
+    assert growth(nk=-1) == lbm.LBM_ERR_ARG
+    assert growth(prec=2) == lbm.LBM_ERR_ARG  # FP16 is not a precision of the map
+    assert growth(dst=None) == lbm.LBM_ERR_ARG
+    assert growth(n=-1) == lbm.LBM_ERR_ARG
+    assert crit(nscan=1) == lbm.LBM_ERR_ARG
+    assert crit(lo=1.0, hi=1.0) == lbm.LBM_ERR_ARG
+    assert crit(lo=-0.5) == lbm.LBM_ERR_ARG
+    assert crit(iters=201) == lbm.LBM_ERR_ARG
+    assert crit(tol=float("nan")) == lbm.LBM_ERR_ARG
+    # host-side marshalling
+    vv, cc = stability._marshal(["I", "III"], np.stack([good, good]))
+    assert vv.tolist() == [1, 3] and cc.shape == (2, 15)
+    with pytest.raises(ValueError):
+        stability._marshal("II", np.zeros((1, 14)))
+    np.testing.assert_array_equal(stability.case([1.0] * 3 + [1.5] * 6, 0.2, 0.3, 0.4, (0.1, -0.1),
+                                                 0.7),
+                                  [1, 1, 1, 1.5, 1.5, 1.5, 1.5, 1.5, 1.5, 0.3, 0.4, 0.1, -0.1, 0.7,
+                                   0.2])

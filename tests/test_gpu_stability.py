@@ -1,0 +1,194 @@
+"""Von Neumann stability maps on the GPU (lbm_vn_growth, lbm_vn_chi_crit)
+against the oracle's linearisation (oracle/vonneumann.py) and the paper.
+
+- growth over the wavenumber grid: FP64 within 1e-10 of the oracle's
+  numpy eigenvalues, FP32 within 2e-5 (the FP32 QR reaches about 10 eps32 on
+  these 9 x 9 matrices, eps32 = 1.2e-7, measured 2e-6 at worst in a CPU
+  emulation of the kernel's algorithm), on seeded random cases with distinct
+  MRT rates, target flows, directions and all four variants;
+- the |k| reported at the maximum attains the oracle's maximum;
+- the critical chi equals the oracle's scan-and-bisection result;
+- the closed forms and the twelve stability statements of Sec. 3.3;
+- the map agrees with the CUDA step itself: a small perturbation of a
+  periodic lattice grows per step by the largest growth over the lattice's
+  own wave numbers.
+"""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+from conftest import golden_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6350_gb300 import lbm
+
+    lbm.load()
+
+
+def _random_cases(seed, count):
+    from paper_1203_6350_gb300 import stability as st
+
+    rng = np.random.default_rng(seed)
+    variants, cases = [], []
+    for i in range(count):
+        sc = rng.uniform(1.0, 1.999)
+        s9 = np.concatenate([[sc] * 3, rng.uniform(0.8, 1.999, 6)]) if i % 2 else np.full(9, sc)
+        variants.append(("none", "I", "II", "III")[i % 4])
+        cases.append(st.case(s9, chi=rng.uniform(0, 3), n=rng.uniform(0.2, 0.8),
+                             m=rng.uniform(0.2, 0.8), u_f=tuple(rng.uniform(-0.15, 0.15, 2)),
+                             theta=rng.uniform(0, np.pi)))
+    return variants, np.array(cases)
+
+
+def _oracle_growth(v, c, nk):
+    from oracle import vonneumann as vn
+
+    return vn.growth(v, c[:9], c[14], c[9], c[10], (c[11], c[12]), c[13], nk)
+
+
+def test_growth_matches_the_oracle():
+    from oracle import vonneumann as vn
+    from paper_1203_6350_gb300 import stability as st
+
+    nk = 48
+    variants, cases = _random_cases(5, 64)
+    g64, k64 = st.growth(variants, cases, nk=nk, precision="f64")
+    g32, _ = st.growth(variants, cases, nk=nk, precision="f32")
+    for i, (v, c) in enumerate(zip(variants, cases)):
+        want, _ = _oracle_growth(v, c, nk)
+        assert abs(g64[i] - want) <= 1e-10, (i, v, g64[i], want)
+        assert abs(g32[i] - want) <= 2e-5, (i, v, g32[i], want)
+        # the reported |k| is on the grid and attains the maximum
+        j = k64[i] * nk / np.pi
+        assert abs(j - round(j)) < 1e-9 and 0 <= round(j) <= nk
+        kv = k64[i] * np.array([np.cos(c[13]), np.sin(c[13])])
+        J = vn.jacobian(v, c[:9], c[14], c[9], c[10], 1.0, (c[11], c[12]))
+        assert abs(np.abs(vn.spectrum(kv, J)).max() - want) <= 1e-10
+
+
+@pytest.mark.parametrize("nk", [0, 1, 31, 32, 33, 300])
+def test_growth_wavenumber_counts(nk):
+    """nk + 1 wavenumbers split over 32 lanes: one, a ragged last round, exactly
+    one round, one past it, and many rounds."""
+    from paper_1203_6350_gb300 import stability as st
+
+    variants, cases = _random_cases(nk + 100, 8)
+    g, _ = st.growth(variants, cases, nk=nk, precision="f64")
+    for i, (v, c) in enumerate(zip(variants, cases)):
+        assert abs(g[i] - _oracle_growth(v, c, nk)[0]) <= 1e-10, (nk, i)
+
+
+def test_critical_chi_matches_the_oracle():
+    from oracle import vonneumann as vn
+    from paper_1203_6350_gb300 import stability as st
+
+    variants, cases = _random_cases(9, 12)
+    kw = dict(nk=24, chi_lo=0.0, chi_hi=6.0, nscan=9, iters=24)
+    got = st.chi_crit(variants, cases, precision="f64", tol=1e-9, **kw)
+    width = (kw["chi_hi"] - kw["chi_lo"]) / (kw["nscan"] - 1) / 2 ** kw["iters"]
+    for i, (v, c) in enumerate(zip(variants, cases)):
+        want = vn.chi_crit(v, c[:9], c[9], c[10], (c[11], c[12]), c[13], tol=1e-9, **kw)
+        if np.isinf(want):
+            assert got[i] == want, (i, got[i], want)
+        else:
+            assert abs(got[i] - want) <= width, (i, v, got[i], want)
+
+
+def test_critical_chi_closed_forms_on_the_gpu():
+    """Eq. criticalchi (type II: 4/s, also with u^f = (0.1, 0), Fig. 8), Eq.
+    effectrelax (type I: 2 - s), type III with u^f = (0.1, 0) between 2.5/s and
+    3/s (Fig. 9), in FP64 and in FP32 (tol 1e-5: the threshold moves by at most
+    tol / |d growth / d chi| ~ 2e-5)."""
+    from paper_1203_6350_gb300 import stability as st
+
+    ss = [1.5, 1.9, 1.99, 1.99999]
+    cases = [st.case(s) for s in ss] + [st.case(1.99, u_f=(0.1, 0.0))]
+    for prec, tol in (("f64", 1e-6), ("f32", 5e-5)):
+        c2 = st.chi_crit("II", cases, nk=64, precision=prec)
+        np.testing.assert_allclose(c2, [4 / s for s in ss] + [4 / 1.99], atol=tol)
+        c1 = st.chi_crit("I", [st.case(s) for s in ss], nk=64, precision=prec, chi_hi=1.0)
+        np.testing.assert_allclose(c1, [2 - s for s in ss], atol=tol)
+        c3 = st.chi_crit("III", [st.case(1.99, u_f=(0.1, 0.0))], nk=64, precision=prec,
+                         chi_hi=4.0)
+        assert 2.5 / 1.99 < c3[0] < 3 / 1.99, c3
+    # end cases of the scan
+    assert st.chi_crit("I", [st.case(1.99)], nk=8, chi_lo=0.05, chi_hi=1.0)[0] == -np.inf
+    assert st.chi_crit("II", [st.case(1.9)], nk=8, chi_hi=2.0)[0] == np.inf
+
+
+def _chi_expr(expr, s):
+    return float(eval(expr, {"__builtins__": {}}, {"s": s}))
+
+
+def test_papers_stability_claims_on_the_gpu():
+    """The twelve statements of Sec. 3.3 (golden fixture) from the GPU map."""
+    from paper_1203_6350_gb300 import stability as st
+
+    rows = golden_rows("stability_claims.txt")
+    variants = [r[0] for r in rows]
+    cases = [st.case(float(r[1]), chi=_chi_expr(r[2], float(r[1])),
+                     u_f=(float(r[3]), float(r[4]))) for r in rows]
+    g, _ = st.growth(variants, cases, nk=300, precision="f64")
+    for r, gi in zip(rows, g):
+        if r[5] == "stable":
+            assert gi < 1 - 1e-6, (r, gi)
+        elif r[5] == "marginal":
+            assert abs(gi - 1) < 1e-9, (r, gi)
+        else:
+            assert gi > 1 + 1e-6, (r, gi)
+
+
+@pytest.mark.parametrize("variant,s,chi,ux", [("II", 1.99, 4 / 1.99 + 0.1, 0.05),
+                                              ("I", 1.99, 0.2, 0.05),
+                                              ("III", 1.99, 4 / 1.99 - 0.1, 0.1)])
+def test_map_predicts_the_growth_of_the_step_kernel(variant, s, chi, ux):
+    """A 1e-12 perturbation of a periodic 64 x 1 lattice (uniform chi, FP64 step)
+    grows per step, once its fastest modes dominate, by the map's growth over
+    the lattice's own wave numbers k = 2 pi p / 64, p = 0..32 (theta = 0,
+    nk = 32).  The run stops when the map predicts a 1e9-fold growth, so the
+    perturbation stays linear; the per-step rate over its last 40 steps is
+    compared.  The type III case is Fig. 9(a): unstable below 4/s with mean flow."""
+    from paper_1203_6350_gb300 import lbm
+    from paper_1203_6350_gb300 import stability as st
+
+    nx, u = 64, (ux, 0.0)
+    g, _ = st.growth(variant, [st.case(s, chi=chi, u_f=u)], nk=nx // 2, precision="f64")
+    assert g[0] > 1.04
+    steps = int(math.ceil(math.log(1e9) / math.log(g[0])))
+    rng = np.random.default_rng(3)
+    with lbm.Lattice(nx, 1, "f64", 1.0, u, s, 0.5, 0.5, "periodic") as lat:
+        with warnings.catch_warnings():  # chi beyond the stability limits the library checks
+            warnings.simplefilter("ignore", RuntimeWarning)
+            lat.set_sponge(variant, np.full(nx, chi), np.full(1, chi), 1.0, u)
+        lat.init_equilibrium(1.0 + 1e-12 * rng.standard_normal((1, nx)),
+                             u[0] + 1e-12 * rng.standard_normal((1, nx)),
+                             u[1] + 1e-12 * rng.standard_normal((1, nx)))
+        norms = []
+        for n in (steps - 40, 40):
+            lat.step(n)
+            buf, _ = lat.get_state()
+            norms.append(float(np.linalg.norm(np.frombuffer(buf, dtype=np.float64))))
+    rate = (norms[1] / norms[0]) ** (1 / 40)
+    assert norms[1] < 1e-2  # still linear
+    assert abs(rate - g[0]) < 2e-3 * g[0], (rate, g[0])
+
+
+def test_many_cases_in_one_call():
+    """2000 cases in one launch (far more than resident warps): a seeded sample
+    of 16 against the oracle."""
+    from paper_1203_6350_gb300 import stability as st
+
+    variants, cases = _random_cases(21, 2000)
+    g, _ = st.growth(variants, cases, nk=16, precision="f32")
+    assert np.isfinite(g).all()
+    for i in np.random.default_rng(0).choice(2000, 16, replace=False):
+        assert abs(g[i] - _oracle_growth(variants[i], cases[i], 16)[0]) <= 2e-5, i

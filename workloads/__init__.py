@@ -241,6 +241,31 @@ def line_source(nx: int = 800, ny: int = 200, variant: str = "II", width: int = 
                     meta={"period": period, "wavelength": (CS + u0[0]) * period})
 
 
+def stability_map(s_values=(1.9, 1.99, 1.999), bulk=(1.0, 1.5, None), heat=(1.2, 1.8, None),
+                  u_values=(0.0, 0.05, 0.1, 0.15, 0.2),
+                  thetas=(0.0, math.pi / 8, math.pi / 4), variants=("I", "II", "III"),
+                  n: float = 0.5, m: float = 0.5):
+    """Cases of the stability map: Sec. 3.3's Von Neumann study extended to
+    distinct MRT rates.  For each shear rate s (s_nu = s_c = s), bulk rate
+    s_e = s_eps in `bulk` and heat-flux rate s_q in `heat` (None: equal to s),
+    target flow u^f = (U, 0), wave direction theta and damping variant, one
+    record [s_0..s_8, n, m, u_x, u_y, theta, chi = 0] in the row order of M.
+    Returns (variants, cases[N, 15])."""
+    vs, cases = [], []
+    for v in variants:
+        for s in s_values:
+            for se in bulk:
+                for sq in heat:
+                    se_ = s if se is None else se
+                    sq_ = s if sq is None else sq
+                    s9 = [s, s, s, se_, se_, sq_, sq_, s, s]
+                    for u in u_values:
+                        for th in thetas:
+                            vs.append(v)
+                            cases.append(s9 + [n, m, u, 0.0, th, 0.0])
+    return vs, np.array(cases, dtype=np.float64)
+
+
 def batch_of_lattices(seed: int = 0, count: int = 256, lo: int = 64, hi: int = 1024,
                       steps: int = 1000, storage="f32") -> list[Workload]:
     """`count` independent lattices: sides log-uniform in [lo, hi] per axis, seeded pulse
