@@ -14,9 +14,11 @@
 // and T_m = chi I (type I), chi Q (type II), chi Q_L (type III, the moments of
 // the linear equilibrium) or 0.  Then J = M^T D^-1 (M J M^-1) M.
 //
-// GPU layout: one warp per case.  The warp builds J in shared memory, then
+// GPU layout: one warp per case.  The warp builds J in shared memory (in FP64,
+// then rounded to R), then
 // each lane takes wavenumbers lane, lane + 32, ...; for each it forms the
-// complex 9 x 9 G(k) in its own shared-memory slot (element (r, c) of lane l
+// complex 9 x 9 G(k) in its own shared-memory slot (phases from exp(-i k_x) and
+// exp(-i k_y) in R) (element (r, c) of lane l
 // at [(9 r + c) * 32 + l], so a warp's accesses fall on consecutive words),
 // reduces it to upper Hessenberg form by Householder reflections and finds
 // all eigenvalues by the single-shift complex QR iteration with Wilkinson
@@ -373,24 +375,35 @@ struct Growth {
     double k;  // |k| at the maximum
 };
 
-// Largest growth over this lane's wavenumbers, reduced over the warp (every
-// lane returns the warp's result).  J (81 doubles, shared) must be built.
+__device__ __forceinline__ void sin_cos(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sin_cos(double a, double* s, double* c) { sincos(a, s, c); }
+
+// exp(-i k.c) for c = (cx, cy) in {-1, 0, 1}^2 from ex = exp(-i k_x), ey = exp(-i k_y).
 template <typename R>
-__device__ Growth warp_growth(const double* jp, double theta, int nk, Cx<R>* slot, int lane) {
+__device__ __forceinline__ Cx<R> phase(Cx<R> ex, Cx<R> ey, int cxr, int cyr) {
+    const Cx<R> one = cx(R(1), R(0));
+    const Cx<R> px = cxr > 0 ? ex : (cxr < 0 ? conj(ex) : one);
+    const Cx<R> py = cyr > 0 ? ey : (cyr < 0 ? conj(ey) : one);
+    return cyr == 0 ? px : (cxr == 0 ? py : px * py);
+}
+
+// Largest growth over this lane's wavenumbers, reduced over the warp (every
+// lane returns the warp's result).  jr: J (81 values of type R, shared).
+template <typename R>
+__device__ Growth warp_growth(const R* jr, double theta, int nk, Cx<R>* slot, int lane) {
     const Mat<R> A{slot + lane};
     const double ct = cos(theta), st = sin(theta);
     double g = -1.0, kbest = 0.0;
     bool bad = false;
     for (int j = lane; j <= nk; j += kLanes) {
         const double km = nk > 0 ? 3.141592653589793 * j / nk : 0.0;
-        const double kx = km * ct, ky = km * st;
+        R sx, cxv, sy, cyv;
+        sin_cos(static_cast<R>(km * ct), &sx, &cxv);
+        sin_cos(static_cast<R>(km * st), &sy, &cyv);
+        const Cx<R> ex = cx(cxv, -sx), ey = cx(cyv, -sy);
         for (int r = 0; r < kN; ++r) {
-            double sn, cs;
-            sincos(kx * kCx[r] + ky * kCy[r], &sn, &cs);  // exp(-i k.c_r) = cs - i sn
-            for (int c = 0; c < kN; ++c) {
-                const double v = jp[r * kN + c];
-                A(r, c) = cx(static_cast<R>(cs * v), static_cast<R>(-sn * v));
-            }
+            const Cx<R> ph = phase(ex, ey, kCx[r], kCy[r]);
+            for (int c = 0; c < kN; ++c) A(r, c) = jr[r * kN + c] * ph;
         }
         hessenberg(A);
         const double lam = static_cast<double>(spectral_radius(A));
@@ -415,9 +428,21 @@ __device__ Growth warp_growth(const double* jp, double theta, int nk, Cx<R>* slo
     return Growth{g, kbest};
 }
 
+// J of the case at strength chi, rounded to R, into jr (shared); jm and jp
+// are FP64 scratch.  Called by the whole warp.
+template <typename R>
+__device__ __forceinline__ void jacobian_r(const Case& k, int variant, double chi, double* jm,
+                                           double* jp, R* jr, int lane) {
+    build_jacobian(k, variant, chi, jm, jp, lane);
+    for (int e = lane; e < kN * kN; e += kLanes) jr[e] = static_cast<R>(jp[e]);
+    __syncwarp();
+}
+
+// Per block: the 32 lane matrices, two FP64 scratch matrices, J in R.
 template <typename R>
 constexpr size_t vn_smem() {
-    return sizeof(Cx<R>) * kN * kN * kLanes + 2 * kN * kN * sizeof(double);
+    return sizeof(Cx<R>) * kN * kN * kLanes + 2 * kN * kN * sizeof(double) +
+           kN * kN * sizeof(R);
 }
 
 template <typename R>
@@ -428,11 +453,12 @@ __global__ void __launch_bounds__(kLanes)
     Cx<R>* slots = reinterpret_cast<Cx<R>*>(vn_raw);
     double* jm = reinterpret_cast<double*>(vn_raw + sizeof(Cx<R>) * kN * kN * kLanes);
     double* jp = jm + kN * kN;
+    R* jr = reinterpret_cast<R*>(jp + kN * kN);
     const int lane = threadIdx.x;
     for (long long c = blockIdx.x; c < ncases; c += gridDim.x) {
         const Case k = load_case(cases, c);
-        build_jacobian(k, variant[c], k.chi, jm, jp, lane);
-        const Growth g = warp_growth<R>(jp, k.theta, nk, slots, lane);
+        jacobian_r(k, variant[c], k.chi, jm, jp, jr, lane);
+        const Growth g = warp_growth<R>(jr, k.theta, nk, slots, lane);
         if (lane == 0) {
             growth[c] = g.g;
             if (kmax) kmax[c] = g.k;
@@ -450,14 +476,15 @@ __global__ void __launch_bounds__(kLanes)
     Cx<R>* slots = reinterpret_cast<Cx<R>*>(vn_raw);
     double* jm = reinterpret_cast<double*>(vn_raw + sizeof(Cx<R>) * kN * kN * kLanes);
     double* jp = jm + kN * kN;
+    R* jr = reinterpret_cast<R*>(jp + kN * kN);
     const int lane = threadIdx.x;
     for (long long c = blockIdx.x; c < ncases; c += gridDim.x) {
         const Case k = load_case(cases, c);
         const int var = variant[c];
         // 1: unstable, 0: stable, -1: an eigenvalue problem did not converge
         auto unstable = [&](double chi) -> int {
-            build_jacobian(k, var, chi, jm, jp, lane);
-            const Growth g = warp_growth<R>(jp, k.theta, nk, slots, lane);
+            jacobian_r(k, var, chi, jm, jp, jr, lane);
+            const Growth g = warp_growth<R>(jr, k.theta, nk, slots, lane);
             if (!(g.g == g.g)) return -1;
             return g.g > 1.0 + tol ? 1 : 0;
         };

@@ -151,12 +151,16 @@ def test_papers_stability_claims_on_the_gpu():
                                               ("I", 1.99, 0.2, 0.05),
                                               ("III", 1.99, 4 / 1.99 - 0.1, 0.1)])
 def test_map_predicts_the_growth_of_the_step_kernel(variant, s, chi, ux):
-    """A 1e-12 perturbation of a periodic 64 x 1 lattice (uniform chi, FP64 step)
-    grows per step, once its fastest modes dominate, by the map's growth over
-    the lattice's own wave numbers k = 2 pi p / 64, p = 0..32 (theta = 0,
-    nk = 32).  The run stops when the map predicts a 1e9-fold growth, so the
-    perturbation stays linear; the per-step rate over its last 40 steps is
-    compared.  The type III case is Fig. 9(a): unstable below 4/s with mean flow."""
+    """Random 1e-12 deviations in all nine populations of a periodic 64 x 1
+    lattice (uniform chi, FP64 step) grow per step, once the fastest modes
+    dominate, by the map's growth over the lattice's own wave numbers
+    k = 2 pi p / 64, p = 0..32 (theta = 0, nk = 32).  The run stops when the map
+    predicts a 1e9-fold growth, so the perturbation stays linear; the per-step
+    rate over its last 40 steps is compared (the oracle's own step, run the same
+    way, lands within 7e-4).  All nine populations are seeded because an
+    equilibrium seed barely excites type I's fastest modes, which carry no
+    density or momentum.  The type III case is Fig. 9(a): unstable below 4/s
+    with mean flow."""
     from paper_1203_6350_gb300 import lbm
     from paper_1203_6350_gb300 import stability as st
 
@@ -169,16 +173,16 @@ def test_map_predicts_the_growth_of_the_step_kernel(variant, s, chi, ux):
         with warnings.catch_warnings():  # chi beyond the stability limits the library checks
             warnings.simplefilter("ignore", RuntimeWarning)
             lat.set_sponge(variant, np.full(nx, chi), np.full(1, chi), 1.0, u)
-        lat.init_equilibrium(1.0 + 1e-12 * rng.standard_normal((1, nx)),
-                             u[0] + 1e-12 * rng.standard_normal((1, nx)),
-                             u[1] + 1e-12 * rng.standard_normal((1, nx)))
+        lat.init_equilibrium(np.ones((1, nx)), u[0], u[1])
+        seed = 1e-12 * rng.standard_normal(lat.state_bytes() // 8)
+        lat.set_state(seed.view(np.uint8), 0)
         norms = []
         for n in (steps - 40, 40):
             lat.step(n)
             buf, _ = lat.get_state()
             norms.append(float(np.linalg.norm(np.frombuffer(buf, dtype=np.float64))))
     rate = (norms[1] / norms[0]) ** (1 / 40)
-    assert norms[1] < 1e-2  # still linear
+    assert norms[1] < 0.1  # still linear: about 1e-3 per population
     assert abs(rate - g[0]) < 2e-3 * g[0], (rate, g[0])
 
 
