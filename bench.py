@@ -347,6 +347,7 @@ def run_native(args):
     sweep = None if args.no_sweep else run_roofline_sweep(peaks)
     line_source = None if args.no_sweep else run_line_source(peaks)
     stability_map = None if args.no_sweep else run_stability_map()
+    d3q15 = None if args.no_sweep else run_d3q15(peaks)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -376,6 +377,7 @@ def run_native(args):
             "roofline_sweep": sweep,
             "line_source": line_source,
             "stability_map": stability_map,
+            "d3q15": d3q15,
             "batched": batched,
             "serving": serving,
         }
@@ -526,6 +528,49 @@ def run_line_source(peaks):
             "interior_rel_l2_vs_unbounded": {
                 "no_layer": interior("none", 0), "viscosity_sponge_160": interior("viscous", 160),
                 "type_II_160": interior("II", 160), "type_II_58_one_wavelength": interior("II", 58)}}
+
+
+def run_d3q15(peaks, side=256, steps=100):
+    """The D3Q15 scheme (App. A.2) on the 3-D pulse: side^3 cells, type II
+    layer of 16 cells on every face, FP32 (120 B per cell-step: 15 populations
+    read and written) and FP64 at half the side (240 B), timed with CUDA events
+    after warm-up steps; the oracle timed on a 32^3 sample."""
+    import torch
+
+    from paper_1203_6350_gb300 import lbm
+
+    out = {}
+    for storage, n, bpc in (("f32", side, 120), ("f64", side // 2, 240)):
+        w = wl.pulse3d(n, storage=storage, steps=steps)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            lat = with_warn(lambda: lbm.Lattice3(w.nx, w.ny, w.nz, storage, w.rho0, w.u0, w.s,
+                                                 w.n, w.m, w.bc, stream=stream))
+            with_warn(lambda: lat.set_sponge(w.variant, w.chi_x, w.chi_y, w.chi_z))
+            lat.init_equilibrium(w.rho0 + w.rho_dev, *w.u0)
+            lat.step(5)
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lat.step(steps)
+            z.record(stream)
+            z.synchronize()
+            lat.close()
+        t = a.elapsed_time(z) / 1e3
+        gbs = bpc * w.cells * steps / t / 1e9
+        out[storage] = {"case": f"{n}^3 pulse, type II layer 16 cells, {steps} steps",
+                        "mlups": w.cells * steps / t / 1e6, "bytes_per_cell_step": bpc,
+                        "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
+    from oracle import d3q15 as d3
+
+    w = wl.pulse3d(32, steps=3, width=4)
+    prob = d3.Problem(w.nx, w.ny, w.nz, w.s, variant=w.variant, chi_x=w.chi_x, chi_y=w.chi_y,
+                      chi_z=w.chi_z)
+    st = d3.State(prob, 1.0 + w.rho_dev, [0.0, 0.0, 0.0])
+    t0 = time.perf_counter()
+    st.run(3)
+    out["oracle_mlups"] = w.cells * 3 / (time.perf_counter() - t0) / 1e6
+    return out
 
 
 def run_stability_map(nk=127, nscan=17, iters=30, chi_hi=8.0):

@@ -435,6 +435,48 @@ int lbm_vn_chi_crit(const int* variant, const double* cases, int ncases, int nk,
 
 const char* lbm_vn_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Three-dimensional scheme: D3Q15 MRT (transformation matrix of App. A.2)
+ * with the damping terms of Secs. 2.2.1-2.2.3, the same definition as the
+ * D2Q9 calls above carried to fifteen velocities:
+ *   c_i = (0,0,0), (+-1,0,0), (0,+-1,0), (0,0,+-1), then (+-1,+-1,+-1) with x
+ *   flipping fastest (rows 1-3 of M); weights 2/9, 1/9, 1/72; c_s^2 = 1/3;
+ *   the second-order f^eq and the linear equilibrium w_i (rho + 3 c_i.j).
+ * Fields are FP64 [nz][ny][nx] (x fastest), on the host.  Storage: LBM_F64 or
+ * LBM_F32 deviations from f^eq(rho0, u0), two buffers of 15 planes of nz x ny
+ * rows (pitch = nx rounded up to 128 bytes).  Boundaries: LBM_BC_DIRICHLET_EQ
+ * (populations from outside are f^eq(rho0, u0), also at t = 0) or
+ * LBM_BC_PERIODIC (all three axes).  Device memory comes from cudaMalloc; the
+ * stream is borrowed.  lbm3_step is asynchronous on it; the other calls
+ * synchronise it.
+ *
+ * Returns as above: LBM_OK, LBM_WARN_UNSTABLE_PARAMS (a rate outside (0, 2);
+ * chi > 4/s_c for types II/III, s + chi > 2 for type I), LBM_ERR_ARG,
+ * LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_STATE. */
+typedef struct lbm3_ctx* lbm3_handle;
+
+/* s: 15 rates in the row order of M (s[0..3] = s_c on rho and j).  One plane
+ * (pitch * ny * nz elements) must stay below 2^31; ny, nz <= 65535. */
+int lbm3_create(int nx, int ny, int nz, lbm_storage storage, double rho0, double ux0, double uy0,
+                double uz0, const double* s, double n, double m, lbm_bc bc, void* cuda_stream,
+                lbm3_handle* out);
+/* Damping variant (LBM_SPONGE_NONE .. LBM_SPONGE_III), per-axis strengths
+ * (chi = max of the three at a cell; finite, >= 0) and reference state q_ref. */
+int lbm3_set_sponge(lbm3_handle h, lbm_variant variant, const double* chi_x, const double* chi_y,
+                    const double* chi_z, double rho_ref, double ux_ref, double uy_ref,
+                    double uz_ref);
+/* f = f^eq(rho, u) at every cell (time 0). */
+int lbm3_init_equilibrium(lbm3_handle h, const double* rho, const double* ux, const double* uy,
+                          const double* uz);
+int lbm3_step(lbm3_handle h, int nsteps);
+/* rho - rho0 and u of the current (streamed, pre-collision) state. */
+int lbm3_moments(lbm3_handle h, double* rho_dev, double* ux, double* uy, double* uz);
+int64_t lbm3_time(lbm3_handle h);
+void lbm3_destroy(lbm3_handle h);
+/* Message of the handle's last failing call (NULL handle: the calling thread's
+ * last lbm3_create failure). */
+const char* lbm3_last_error(lbm3_handle h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,7 +114,11 @@ class Problem:
         self.lam = lambda_matrix(self.s)
 
     def chi(self) -> np.ndarray:
-        """chi[z, y, x] = max(chi_x[x], chi_y[y], chi_z[z])."""
+        """chi[z, y, x] = max(chi_x[x], chi_y[y], chi_z[z]); zero everywhere when
+        no damping term is selected (Gamma = 0 gives F = 0 in Eq. blbs, so also
+        rho* = rho, j* = j)."""
+        if self.variant == "none":
+            return np.zeros((self.nz, self.ny, self.nx))
         return np.maximum(np.maximum(self.chi_x[None, None, :], self.chi_y[None, :, None]),
                           self.chi_z[:, None, None])
 

@@ -123,6 +123,16 @@ SIGNATURES = [
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double, _vp, _vp]),
     ("lbm_vn_last_error", ctypes.c_char_p, []),
+    ("lbm3_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+     + [ctypes.c_double] * 4 + [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp,
+                                 ctypes.POINTER(_vp)]),
+    ("lbm3_set_sponge", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp] + [ctypes.c_double] * 4),
+    ("lbm3_init_equilibrium", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    ("lbm3_step", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm3_moments", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    ("lbm3_time", _i64, [_vp]),
+    ("lbm3_destroy", None, [_vp]),
+    ("lbm3_last_error", ctypes.c_char_p, [_vp]),
 ]
 
 
@@ -284,6 +294,43 @@ def lbm_vn_chi_crit(variant_ptr, cases_ptr, ncases, nk, precision, chi_lo, chi_h
 
 def lbm_vn_last_error() -> str:
     return load().lbm_vn_last_error().decode()
+
+
+def lbm3_create(nx, ny, nz, storage, rho0, u0, s15_ptr, n, m, bc, stream=None):
+    h = _vp()
+    rc = load().lbm3_create(int(nx), int(ny), int(nz), int(storage), float(rho0), float(u0[0]),
+                            float(u0[1]), float(u0[2]), s15_ptr, float(n), float(m), int(bc),
+                            stream, ctypes.byref(h))
+    return rc, h
+
+
+def lbm3_set_sponge(h, variant, cx_ptr, cy_ptr, cz_ptr, rho_ref, u_ref) -> int:
+    return load().lbm3_set_sponge(h, int(variant), cx_ptr, cy_ptr, cz_ptr, float(rho_ref),
+                                  float(u_ref[0]), float(u_ref[1]), float(u_ref[2]))
+
+
+def lbm3_init_equilibrium(h, rho_ptr, ux_ptr, uy_ptr, uz_ptr) -> int:
+    return load().lbm3_init_equilibrium(h, rho_ptr, ux_ptr, uy_ptr, uz_ptr)
+
+
+def lbm3_step(h, nsteps) -> int:
+    return load().lbm3_step(h, int(nsteps))
+
+
+def lbm3_moments(h, rho_ptr, ux_ptr, uy_ptr, uz_ptr) -> int:
+    return load().lbm3_moments(h, rho_ptr, ux_ptr, uy_ptr, uz_ptr)
+
+
+def lbm3_time(h) -> int:
+    return load().lbm3_time(h)
+
+
+def lbm3_destroy(h) -> None:
+    load().lbm3_destroy(h)
+
+
+def lbm3_last_error(h) -> str:
+    return load().lbm3_last_error(h).decode()
 
 
 def lbm_batch_instance_bytes(nx, ny, storage) -> int:
@@ -566,6 +613,81 @@ class Lattice:
     def close(self) -> None:
         if getattr(self, "h", None):
             lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Lattice3:
+    """One D3Q15 lattice behind an lbm3 handle (host FP64 fields [nz, ny, nx])."""
+
+    def __init__(self, nx: int, ny: int, nz: int, storage: str = "f32", rho0: float = 1.0,
+                 u0=(0.0, 0.0, 0.0), s=1.9, n: float = 0.5, m: float = 0.5,
+                 bc: str = "dirichlet", stream=None, device: int = 0):
+        import torch
+
+        torch.cuda.set_device(device)
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.rho0, self.u0 = float(rho0), tuple(float(v) for v in u0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        s15 = np.ascontiguousarray(np.broadcast_to(np.asarray(s, dtype=np.float64), (15,)))
+        rc, h = lbm3_create(nx, ny, nz, STORAGE[storage], rho0, u0, s15.ctypes.data, n, m, BC[bc],
+                            self.stream.cuda_stream)
+        if rc < 0:
+            raise LbmError(rc, lbm3_last_error(None))
+        self.h = h
+        if rc > 0:
+            warnings.warn(f"liblbm warning: {lbm3_last_error(h)}", RuntimeWarning, stacklevel=2)
+
+    def _check(self, rc: int, what: str) -> int:
+        if rc < 0:
+            raise LbmError(rc, f"{what}: {lbm3_last_error(self.h)}")
+        if rc > 0:
+            warnings.warn(f"liblbm warning in {what}: {lbm3_last_error(self.h)}", RuntimeWarning,
+                          stacklevel=3)
+        return rc
+
+    def set_sponge(self, variant: str, chi_x, chi_y, chi_z, rho_ref=None, u_ref=None) -> int:
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (chi_x, chi_y, chi_z)]
+        assert [a.shape for a in arrs] == [(self.nx,), (self.ny,), (self.nz,)]
+        rho_ref = self.rho0 if rho_ref is None else rho_ref
+        u_ref = self.u0 if u_ref is None else u_ref
+        return self._check(lbm3_set_sponge(self.h, VARIANT[variant], *(a.ctypes.data for a in arrs),
+                                           rho_ref, u_ref), "lbm3_set_sponge")
+
+    def init_equilibrium(self, rho, ux, uy, uz) -> None:
+        shp = (self.nz, self.ny, self.nx)
+        arrs = [np.ascontiguousarray(np.broadcast_to(a, shp), dtype=np.float64)
+                for a in (rho, ux, uy, uz)]
+        self._check(lbm3_init_equilibrium(self.h, *(a.ctypes.data for a in arrs)),
+                    "lbm3_init_equilibrium")
+
+    def step(self, nsteps: int) -> None:
+        self._check(lbm3_step(self.h, nsteps), "lbm3_step")
+
+    def moments(self):
+        shp = (self.nz, self.ny, self.nx)
+        out = [np.empty(shp) for _ in range(4)]
+        self._check(lbm3_moments(self.h, *(a.ctypes.data for a in out)), "lbm3_moments")
+        return tuple(out)
+
+    @property
+    def time(self) -> int:
+        return lbm3_time(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lbm3_destroy(self.h)
             self.h = None
 
     def __del__(self):

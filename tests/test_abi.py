@@ -158,3 +158,36 @@ def test_stability_map_calls_check_arguments_before_touching_the_device(lib):
                                                  0.7),
                                   [1, 1, 1, 1.5, 1.5, 1.5, 1.5, 1.5, 1.5, 0.3, 0.4, 0.1, -0.1, 0.7,
                                    0.2])
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(nx=0), "sizes"),
+    (dict(nz=70000), "65535"),
+    (dict(storage=2), "storage"),
+    (dict(bc=2), "bc"),
+    (dict(rho0=0.0), "rho0"),
+    (dict(s=float("nan")), "rates"),
+    (dict(n=-0.5), "Guo"),
+])
+def test_lbm3_create_rejects_bad_arguments_before_touching_the_device(lib, kw, frag):
+    from paper_1203_6350_gb300 import lbm
+
+    a = dict(nx=8, ny=8, nz=8, storage=1, rho0=1.0, s=1.9, n=0.5, bc=0)
+    a.update(kw)
+    s15 = np.full(15, a["s"])
+    rc, h = lbm.lbm3_create(a["nx"], a["ny"], a["nz"], a["storage"], a["rho0"], (0.0, 0.0, 0.0),
+                            s15.ctypes.data, a["n"], 0.5, a["bc"])
+    assert rc == lbm.LBM_ERR_ARG
+    assert not h.value
+    assert frag in lbm.lbm3_last_error(None)
+
+
+def test_lbm3_null_handle_calls_are_argument_errors(lib):
+    from paper_1203_6350_gb300 import lbm
+
+    assert lbm.lbm3_step(None, 1) == lbm.LBM_ERR_ARG
+    assert lbm.lbm3_moments(None, None, None, None, None) == lbm.LBM_ERR_ARG
+    assert lbm.lbm3_init_equilibrium(None, None, None, None, None) == lbm.LBM_ERR_ARG
+    assert lbm.lbm3_set_sponge(None, 2, None, None, None, 1.0, (0, 0, 0)) == lbm.LBM_ERR_ARG
+    assert lbm.lbm3_time(None) == -1
+    lbm.lbm3_destroy(None)

@@ -1,0 +1,140 @@
+"""The D3Q15 scheme on the GPU (lbm3_* C ABI) against the D3Q15 oracle
+(oracle/d3q15.py).
+
+- Ragged and tiny lattices (several x tiles, ragged tails in x and y, one-cell
+  axes), every damping variant, both boundaries, distinct MRT rates, mean flow
+  and a reference state different from the far field, 20 steps: FP64 within
+  1e-10 (plus the oracle's absolute floor), FP32 within 1e-5.
+- The 3-D pulse with a ramped layer on every face: FP32 and FP64 against the
+  oracle over 60 steps.
+- At the benchmark's size (256^3 FP32): the centred pulse keeps the cube's
+  symmetries, and a periodic lattice without damping conserves mass.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6350_gb300 import lbm
+
+    lbm.load()
+
+
+def _floor(steps, n):
+    # the oracle's own rounding on full populations ~ rho0 = 1
+    return 10 * (steps + 1) * 2.0**-53 * math.sqrt(n)
+
+
+def _close(got, ref, tol, steps, what=""):
+    err = float(np.linalg.norm(got - ref))
+    bound = tol * float(np.linalg.norm(ref)) + _floor(steps, ref.size)
+    assert err <= bound, (what, err, bound)
+
+
+def _oracle(w: "wl.Workload3", steps):
+    from oracle import d3q15 as d3
+
+    prob = d3.Problem(w.nx, w.ny, w.nz, w.s, w.n, w.m, w.variant, w.bc, w.rho0, w.u0, w.rho_f,
+                      w.u_f, w.chi_x, w.chi_y, w.chi_z)
+    st = d3.State(prob, w.rho0 + w.rho_dev, [np.full(w.rho_dev.shape, v) for v in w.u0])
+    return st.run(steps).moments()
+
+
+def _gpu(w: "wl.Workload3", storage, steps):
+    import warnings
+
+    from paper_1203_6350_gb300 import lbm
+
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", RuntimeWarning)
+        lat = lbm.Lattice3(w.nx, w.ny, w.nz, storage, w.rho0, w.u0, w.s, w.n, w.m, w.bc)
+        lat.set_sponge(w.variant, w.chi_x, w.chi_y, w.chi_z, w.rho_f, w.u_f)
+    with lat:
+        lat.init_equilibrium(w.rho0 + w.rho_dev, *w.u0)
+        lat.step(steps)
+        assert lat.time == steps
+        return lat.moments()
+
+
+def _random(nx, ny, nz, variant, bc, seed, steps=20):
+    rng = np.random.default_rng(seed)
+    s = np.concatenate([[1.7] * 4, rng.uniform(1.1, 1.95, 11)])
+    return wl.Workload3(name="random", nx=nx, ny=ny, nz=nz, s=s, variant=variant,
+                        chi_x=rng.uniform(0, 0.4, nx), chi_y=rng.uniform(0, 0.4, ny),
+                        chi_z=rng.uniform(0, 0.4, nz),
+                        rho_dev=1e-3 * rng.standard_normal((nz, ny, nx)), steps=steps, bc=bc,
+                        n=0.4, m=0.6, u0=(0.04, -0.02, 0.03), rho_f=1.002, u_f=(0.05, 0.0, -0.01))
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 4, 2), (70, 9, 5), (5, 13, 7), (130, 3, 3)])
+@pytest.mark.parametrize("variant", ["none", "I", "II", "III"])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_d3q15_against_the_oracle(shape, variant, bc):
+    w = _random(*shape, variant, bc, seed=sum(shape) * 7 + len(variant))
+    ref = _oracle(w, w.steps)
+    for storage in ("f64", "f32"):
+        got = _gpu(w, storage, w.steps)
+        for a, b, name in zip(got, ref, ("rho'", "u_x", "u_y", "u_z")):
+            _close(a, b, TOL[storage], w.steps, (storage, name))
+
+
+@pytest.mark.parametrize("variant", ["I", "II", "III"])
+def test_pulse_with_layers_against_the_oracle(variant):
+    """A 48 x 40 x 36 box, b = 4 pulse, 8-cell ramped layers (chi_max 0.3), mean
+    flow along x, 60 steps."""
+    w = wl.pulse3d(48, steps=60, width=8, chi_max=0.3, variant=variant, b=4.0, ny=40, nz=36,
+                   u0=(0.05, 0.0, 0.0))
+    ref = _oracle(w, w.steps)
+    for storage in ("f64", "f32"):
+        got = _gpu(w, storage, w.steps)
+        _close(got[0], ref[0], TOL[storage], w.steps, (storage, "rho'"))
+        _close(got[1], ref[1], TOL[storage], w.steps, (storage, "u_x"))
+
+
+def test_benchmark_size_symmetry_and_conservation():
+    """256^3 FP32, the benchmark's pulse and layer, 100 steps: rho' is invariant
+    under the mirrors and axis swaps of the cube (FP32: to 1e-5 of its maximum;
+    the kernel sums the mirrored cells' populations in another order).  A
+    periodic 256^3 lattice without damping keeps its total mass to FP32 rounding."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.pulse3d(256, steps=100)
+    r = _gpu(w, "f32", w.steps)[0]
+    scale = np.abs(r).max()
+    assert scale > 1e-5
+    for img in (r[::-1], r[:, ::-1], r[:, :, ::-1], r.transpose(0, 2, 1), r.transpose(2, 1, 0),
+                r.transpose(1, 0, 2)):
+        assert np.abs(img - r).max() <= 1e-5 * scale
+    with lbm.Lattice3(256, 256, 256, "f32", 1.0, (0.0, 0.0, 0.0), w.s, bc="periodic") as lat:
+        lat.init_equilibrium(1.0 + w.rho_dev, 0.0, 0.0, 0.0)
+        m0 = lat.moments()[0].sum(dtype=np.float64)
+        lat.step(50)
+        m1 = lat.moments()[0].sum(dtype=np.float64)
+    # FP32 deviations ~ 1e-3 in 16.8M cells: rounding of order 1e-10 each
+    assert abs(m1 - m0) <= 1e-4 * abs(m0), (m0, m1)
+
+
+def test_d3q15_api_rules():
+    from paper_1203_6350_gb300 import lbm
+
+    with lbm.Lattice3(8, 8, 8, "f32") as lat:
+        assert lbm.lbm3_step(lat.h, 1) == lbm.LBM_ERR_STATE
+        cx = np.zeros(8)
+        bad = np.full(8, -1.0)
+        assert lbm.lbm3_set_sponge(lat.h, 2, bad.ctypes.data, cx.ctypes.data, cx.ctypes.data,
+                                   1.0, (0, 0, 0)) == lbm.LBM_ERR_ARG
+        big = np.full(8, 3.0)
+        assert lbm.lbm3_set_sponge(lat.h, 2, big.ctypes.data, cx.ctypes.data, cx.ctypes.data,
+                                   1.0, (0, 0, 0)) == lbm.LBM_WARN_UNSTABLE_PARAMS

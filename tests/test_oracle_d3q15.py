@@ -157,7 +157,8 @@ def _brute_force(f, prob, steps):
             for y in range(ny):
                 for x in range(nx):
                     g = f[:, z, y, x]
-                    chi = max(prob.chi_x[x], prob.chi_y[y], prob.chi_z[z])
+                    chi = 0.0 if prob.variant == "none" else max(prob.chi_x[x], prob.chi_y[y],
+                                                                  prob.chi_z[z])
                     rho = g.sum()
                     j = [sum(c[i][a] * g[i] for i in range(15)) for a in range(3)]
                     rs = (rho + prob.n * chi * prob.rho_f) / (1 + prob.n * chi)
@@ -206,6 +207,23 @@ def test_oracle_equals_a_per_cell_loop(variant, bc):
     want = _brute_force(st.f.copy(), prob, 3)
     st.run(3)
     np.testing.assert_allclose(st.f, want, rtol=0, atol=1e-14)
+
+
+def test_no_damping_ignores_the_layer_arrays():
+    """Without a damping term the absorbing strengths and the reference state
+    play no part (Eq. blbs with Gamma = 0): a lattice with random chi arrays and
+    a reference state off the far field steps exactly like one with none."""
+    d3 = _d3()
+    rng = np.random.default_rng(8)
+    shp = (3, 4, 5)
+    rho = 1 + 1e-3 * rng.standard_normal(shp)
+    a = d3.Problem(5, 4, 3, d3.rates(1.8), variant="none", u0=(0.04, 0.0, -0.02), rho_f=1.01,
+                   u_f=(0.1, 0.0, 0.0), chi_x=rng.uniform(0, 0.5, 5), chi_y=rng.uniform(0, 0.5, 4),
+                   chi_z=rng.uniform(0, 0.5, 3))
+    b = d3.Problem(5, 4, 3, d3.rates(1.8), variant="none", u0=(0.04, 0.0, -0.02))
+    fa = d3.State(a, rho, [0.04, 0.0, -0.02]).run(5).f
+    fb = d3.State(b, rho, [0.04, 0.0, -0.02]).run(5).f
+    np.testing.assert_array_equal(fa, fb)
 
 
 def test_centred_pulse_keeps_the_cubes_symmetries():

@@ -241,6 +241,56 @@ def line_source(nx: int = 800, ny: int = 200, variant: str = "II", width: int = 
                     meta={"period": period, "wavelength": (CS + u0[0]) * period})
 
 
+@dataclass
+class Workload3:
+    """A D3Q15 lattice problem: sizes, rates (15, row order of M), damping,
+    per-axis strengths, far field, reference state, initial density deviation
+    (u = u0 everywhere) and step count."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    s: np.ndarray
+    variant: str
+    chi_x: np.ndarray
+    chi_y: np.ndarray
+    chi_z: np.ndarray
+    rho_dev: np.ndarray
+    steps: int
+    bc: str = "dirichlet"
+    n: float = 0.5
+    m: float = 0.5
+    rho0: float = 1.0
+    u0: tuple = (0.0, 0.0, 0.0)
+    rho_f: float = 1.0
+    u_f: tuple = (0.0, 0.0, 0.0)
+    storage: str = "f32"
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def pulse3d(side: int = 256, storage: str = "f32", steps: int = 100, width: int = 16,
+            chi_max: float = 0.1, variant: str = "II", eps: float = 1e-3, b: float = 5.0,
+            nu: float = 1e-3, u0=(0.0, 0.0, 0.0), ny: int | None = None,
+            nz: int | None = None) -> Workload3:
+    """The acoustic pulse of Sec. 4.1 in three dimensions: a Gaussian density
+    pulse (eps, half width b) at the centre of a side^3 box (ny, nz override the
+    other sides) with a quadratic ramp layer of `width` cells on every face,
+    rates of viscosity nu, Dirichlet far field."""
+    ny = side if ny is None else ny
+    nz = side if nz is None else nz
+    s = rate_from_viscosity(nu)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(side), indexing="ij")
+    r2 = (x - (side - 1) / 2) ** 2 + (y - (ny - 1) / 2) ** 2 + (z - (nz - 1) / 2) ** 2
+    return Workload3(name=f"pulse3d-{side}x{ny}x{nz}", nx=side, ny=ny, nz=nz, s=np.full(15, s),
+                     variant=variant, chi_x=ramp_profile(side, width, chi_max),
+                     chi_y=ramp_profile(ny, width, chi_max), chi_z=ramp_profile(nz, width, chi_max),
+                     rho_dev=eps * np.exp(-math.log(2.0) * r2 / b**2), steps=steps,
+                     storage=storage, u0=tuple(u0), u_f=tuple(u0))
+
+
 def stability_map(s_values=(1.9, 1.99, 1.999), bulk=(1.0, 1.5, None), heat=(1.2, 1.8, None),
                   u_values=(0.0, 0.05, 0.1, 0.15, 0.2),
                   thetas=(0.0, math.pi / 8, math.pi / 4), variants=("I", "II", "III"),
