@@ -3,8 +3,9 @@
 
 - Ragged and tiny lattices (several x tiles, ragged tails in x and y, one-cell
   axes), every damping variant, both boundaries, distinct MRT rates, mean flow
-  and a reference state different from the far field, 20 steps: FP64 within
-  1e-10 (plus the oracle's absolute floor), FP32 within 1e-5.
+  and a reference state different from the far field, 20 steps: each field of
+  the deviation state (rho', u - u0) within 1e-10 (FP64, plus the oracle's
+  absolute floor) or 1e-5 (FP32) of the state's norm.
 - The 3-D pulse with a ramped layer on every face: FP32 and FP64 against the
   oracle over 60 steps.
 - At the benchmark's size (256^3 FP32): the centred pulse keeps the cube's
@@ -41,6 +42,19 @@ def _close(got, ref, tol, steps, what=""):
     err = float(np.linalg.norm(got - ref))
     bound = tol * float(np.linalg.norm(ref)) + _floor(steps, ref.size)
     assert err <= bound, (what, err, bound)
+
+
+def _close_state(got, ref, u0, tol, steps, what=""):
+    """Each field of the deviation state (rho', u - u0) within tol times the
+    norm of the whole reference deviation state (a field that conservation or
+    symmetry keeps at zero is held to the state's scale, not to zero)."""
+    dev_got = [got[0]] + [g - u for g, u in zip(got[1:], u0)]
+    dev_ref = [ref[0]] + [r - u for r, u in zip(ref[1:], u0)]
+    scale = math.sqrt(sum(float(np.linalg.norm(r)) ** 2 for r in dev_ref))
+    for a, b, name in zip(dev_got, dev_ref, ("rho'", "u_x", "u_y", "u_z")):
+        err = float(np.linalg.norm(a - b))
+        bound = tol * scale + _floor(steps, b.size)
+        assert err <= bound, (what, name, err, bound)
 
 
 def _oracle(w: "wl.Workload3", steps):
@@ -86,21 +100,21 @@ def test_d3q15_against_the_oracle(shape, variant, bc):
     ref = _oracle(w, w.steps)
     for storage in ("f64", "f32"):
         got = _gpu(w, storage, w.steps)
-        for a, b, name in zip(got, ref, ("rho'", "u_x", "u_y", "u_z")):
-            _close(a, b, TOL[storage], w.steps, (storage, name))
+        _close_state(got, ref, w.u0, TOL[storage], w.steps, storage)
 
 
 @pytest.mark.parametrize("variant", ["I", "II", "III"])
 def test_pulse_with_layers_against_the_oracle(variant):
-    """A 48 x 40 x 36 box, b = 4 pulse, 8-cell ramped layers (chi_max 0.3), mean
-    flow along x, 60 steps."""
-    w = wl.pulse3d(48, steps=60, width=8, chi_max=0.3, variant=variant, b=4.0, ny=40, nz=36,
-                   u0=(0.05, 0.0, 0.0))
+    """A 48 x 40 x 36 box, b = 4 pulse, 8-cell ramped layers, mean flow along x,
+    60 steps.  chi_max = 0.3 for types II and III; 0.01 for type I, which is
+    unstable where s + chi > 2 (Sec. 2.2.1) and would amplify round-off."""
+    w = wl.pulse3d(48, steps=60, width=8, chi_max=0.01 if variant == "I" else 0.3,
+                   variant=variant, b=4.0, ny=40, nz=36, u0=(0.05, 0.0, 0.0))
     ref = _oracle(w, w.steps)
     for storage in ("f64", "f32"):
         got = _gpu(w, storage, w.steps)
         _close(got[0], ref[0], TOL[storage], w.steps, (storage, "rho'"))
-        _close(got[1], ref[1], TOL[storage], w.steps, (storage, "u_x"))
+        _close_state(got, ref, w.u0, TOL[storage], w.steps, storage)
 
 
 def test_benchmark_size_symmetry_and_conservation():
