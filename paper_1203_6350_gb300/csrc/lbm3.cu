@@ -18,6 +18,7 @@
 //   P(rho, j) - P(rho0, j0) = (u0 j'^T + j' u0^T + j' j'^T / rho0 - u0 u0^T rho') rho0 / rho.
 // The linear equilibrium has moments rho, j, -rho, rho, -7/3 j and zeros.
 // Back-transform g = M^T D^-1 m (M's rows are orthogonal, D = diag(M M^T)).
+// Both transforms run as butterflies over the axis pairs and the diagonals.
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -120,21 +121,70 @@ __device__ __forceinline__ void deq2(CT rp, const CT (&jp)[3], const D3Const<CT>
     out[14] = CT(0);
 }
 
+// m = M g by butterflies: the axis pairs (+-x, +-y, +-z) and the eight
+// diagonals, whose signed sums give every diagonal moment in 24 additions.
+template <typename CT>
+__device__ __forceinline__ void d3_forward(const CT (&g)[kQ], CT (&m)[kQ]) {
+    const CT p1 = g[7] + g[8], m1 = g[7] - g[8], p2 = g[9] + g[10], m2 = g[9] - g[10];
+    const CT p3 = g[11] + g[12], m3 = g[11] - g[12], p4 = g[13] + g[14], m4 = g[13] - g[14];
+    const CT q1 = p1 + p2, q2 = p1 - p2, q3 = p3 + p4, q4 = p3 - p4;
+    const CT r1 = m1 + m2, r2 = m1 - m2, r3 = m3 + m4, r4 = m3 - m4;
+    const CT S = q1 + q3, Dz = q1 - q3, Dy = q2 + q4, Dyz = q2 - q4;
+    const CT Dx = r1 + r3, Dxz = r1 - r3, Dxy = r2 + r4, Dxyz = r2 - r4;
+    const CT ax = g[1] + g[2], bx = g[1] - g[2], ay = g[3] + g[4], by = g[3] - g[4];
+    const CT az = g[5] + g[6], bz = g[5] - g[6];
+    const CT A = ax + ay + az;
+    m[0] = g[0] + A + S;
+    m[1] = bx + Dx;
+    m[2] = by + Dy;
+    m[3] = bz + Dz;
+    m[4] = S - A - CT(2) * g[0];
+    m[5] = S - CT(4) * A + CT(16) * g[0];
+    m[6] = Dx - CT(4) * bx;
+    m[7] = Dy - CT(4) * by;
+    m[8] = Dz - CT(4) * bz;
+    m[9] = CT(2) * ax - ay - az;
+    m[10] = ay - az;
+    m[11] = Dxy;
+    m[12] = Dyz;
+    m[13] = Dxz;
+    m[14] = Dxyz;
+}
+
+// g = M^T ph (ph = D^-1 m), the transpose of the butterflies above.
+template <typename CT>
+__device__ __forceinline__ void d3_backward(const CT (&ph)[kQ], CT (&g)[kQ]) {
+    g[0] = ph[0] - CT(2) * ph[4] + CT(16) * ph[5];
+    const CT base = ph[0] - ph[4] - CT(4) * ph[5];
+    const CT X = base + CT(2) * ph[9], Y = base - ph[9] + ph[10], Z = base - ph[9] - ph[10];
+    const CT vx = ph[1] - CT(4) * ph[6], vy = ph[2] - CT(4) * ph[7], vz = ph[3] - CT(4) * ph[8];
+    g[1] = X + vx;
+    g[2] = X - vx;
+    g[3] = Y + vy;
+    g[4] = Y - vy;
+    g[5] = Z + vz;
+    g[6] = Z - vz;
+    const CT D0 = ph[0] + ph[4] + ph[5];
+    const CT Ux = ph[1] + ph[6], Uy = ph[2] + ph[7], Uz = ph[3] + ph[8];
+    const CT t1 = D0 + ph[12], t2 = D0 - ph[12], u1 = Uy + Uz, u2 = Uy - Uz;
+    const CT cpp = t1 + u1, cmm = t1 - u1, cpm = t2 + u2, cmp = t2 - u2;  // (c_y, c_z) signs
+    const CT v1 = Ux + ph[14], v2 = Ux - ph[14], w1 = ph[11] + ph[13], w2 = ph[11] - ph[13];
+    const CT dpp = v1 + w1, dmm = v1 - w1, dpm = v2 + w2, dmp = v2 - w2;
+    g[7] = cpp + dpp;
+    g[8] = cpp - dpp;
+    g[9] = cmp + dmp;
+    g[10] = cmp - dmp;
+    g[11] = cpm + dpm;
+    g[12] = cpm - dpm;
+    g[13] = cmm + dmm;
+    g[14] = cmm - dmm;
+}
+
 // Collide the deviations g of one cell in place.
 template <typename CT, int VAR>
 __device__ __forceinline__ void d3_collide(CT (&g)[kQ], CT chi, const D3Const<CT>& k) {
     CT m[kQ];
-#pragma unroll
-    for (int r = 0; r < kQ; ++r) {
-        CT acc = CT(0);
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            if (d3m(r, i) == 1) acc += g[i];
-            else if (d3m(r, i) == -1) acc -= g[i];
-            else if (d3m(r, i) != 0) acc += CT(d3m(r, i)) * g[i];
-        }
-        m[r] = acc;
-    }
+    d3_forward(g, m);
     // rho*, j* (Guo weights, solved exactly); chi = 0 leaves rho, j
     CT rs = m[0];
     CT js[3] = {m[1], m[2], m[3]};
@@ -164,24 +214,22 @@ __device__ __forceinline__ void d3_collide(CT (&g)[kQ], CT chi, const D3Const<CT
     }
 #pragma unroll
     for (int r = 0; r < kQ; ++r) post[r] *= CT(1.0 / d3norm(r));
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        CT acc = CT(0);
-#pragma unroll
-        for (int r = 0; r < kQ; ++r) {
-            if (d3m(r, i) == 1) acc += post[r];
-            else if (d3m(r, i) == -1) acc -= post[r];
-            else if (d3m(r, i) != 0) acc += CT(d3m(r, i)) * post[r];
-        }
-        g[i] = acc;
-    }
+    d3_backward(post, g);
 }
 
 __device__ __forceinline__ int wrap(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
 constexpr int kBX = 64, kBY = 4;
 
-template <typename T, int VAR, int BC>
+// Element offset of plane i, position o: 32-bit when all 15 planes stay below
+// 2^32 elements (NARROW), else 64-bit.
+template <bool NARROW>
+__device__ __forceinline__ size_t plane_off(int i, unsigned plane, unsigned o) {
+    if (NARROW) return static_cast<unsigned>(i) * plane + o;
+    return static_cast<size_t>(i) * plane + o;
+}
+
+template <typename T, int VAR, int BC, bool NARROW>
 __global__ void __launch_bounds__(kBX * kBY)
     d3_step_kernel(const T* __restrict__ src, T* __restrict__ dst, D3Geom g, D3Const<T> k,
                    const T* __restrict__ chix, const T* __restrict__ chiy,
@@ -199,7 +247,7 @@ __global__ void __launch_bounds__(kBX * kBY)
         for (int i = 0; i < kQ; ++i) {
             const int d = d3cx(i) + d3cy(i) * static_cast<int>(row) +
                           d3cz(i) * static_cast<int>(slab);
-            f[i] = src[static_cast<size_t>(i) * g.plane + (o - d)];
+            f[i] = src[plane_off<NARROW>(i, g.plane, o - d)];
         }
     } else {
 #pragma unroll
@@ -213,15 +261,15 @@ __global__ void __launch_bounds__(kBX * kBY)
                 f[i] = T(0);
                 continue;
             }
-            f[i] = src[static_cast<size_t>(i) * g.plane +
-                       (static_cast<unsigned>(sz) * g.ny + sy) * row + sx];
+            f[i] = src[plane_off<NARROW>(i, g.plane,
+                                         (static_cast<unsigned>(sz) * g.ny + sy) * row + sx)];
         }
     }
     T chi = T(0);
     if (VAR != LBM_SPONGE_NONE) chi = fmax(fmax(chix[x], chiy[y]), chiz[z]);
     d3_collide<T, VAR>(f, chi, k);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) dst[static_cast<size_t>(i) * g.plane + o] = f[i];
+    for (int i = 0; i < kQ; ++i) dst[plane_off<NARROW>(i, g.plane, o)] = f[i];
 }
 
 // Slot x of plane i <- f^eq_i(rho, u at x + c_i) - f^eq_i(rho0, u0) (the
@@ -383,10 +431,16 @@ cudaError_t launch_step(lbm3_ctx* h) {
     const T* cx = static_cast<const T*>(h->chi[0]);
     const T* cy = static_cast<const T*>(h->chi[1]);
     const T* cz = static_cast<const T*>(h->chi[2]);
-#define LBM3_CASE(V, B)                                                                     \
-    if (h->variant == V && h->bc == B) {                                                    \
-        d3_step_kernel<T, V, B><<<grid, block, 0, h->stream>>>(s, d, h->g, k, cx, cy, cz); \
-        return cudaGetLastError();                                                          \
+    const bool narrow = static_cast<unsigned long long>(kQ) * h->g.plane < (1ull << 32);
+#define LBM3_CASE(V, B)                                                                          \
+    if (h->variant == V && h->bc == B) {                                                         \
+        if (narrow)                                                                              \
+            d3_step_kernel<T, V, B, true><<<grid, block, 0, h->stream>>>(s, d, h->g, k, cx, cy, \
+                                                                          cz);                   \
+        else                                                                                     \
+            d3_step_kernel<T, V, B, false><<<grid, block, 0, h->stream>>>(s, d, h->g, k, cx, cy, \
+                                                                           cz);                  \
+        return cudaGetLastError();                                                               \
     }
     LBM3_CASE(LBM_SPONGE_NONE, LBM_BC_DIRICHLET_EQ)
     LBM3_CASE(LBM_SPONGE_I, LBM_BC_DIRICHLET_EQ)
