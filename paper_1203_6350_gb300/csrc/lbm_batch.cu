@@ -202,10 +202,20 @@ struct PairTile {
     }
 };
 
+// Classes of instances for the two-step kernel: damping variant x boundary.
+// The tile table lists the tiles of each class together, and each class has
+// a kernel of its own, so that a kernel holds one collision body (a kernel
+// switching over all ten needed more registers than three blocks per SM
+// allow and spilled).
+constexpr int kClasses = 10;
+__host__ __device__ constexpr int batch_class(int variant, int bc) {
+    return (bc == kPeriodic ? 5 : 0) + variant;
+}
+
 // Two time steps per launch on 64 x 16 tiles through shared memory (the
 // single-lattice two-step tile), for the instances active at both global
 // steps; an instance whose budget ends after the first takes one step.
-template <typename T>
+template <typename T, int VAR, int BC>
 struct TwoStepTile {
     T* sm;
     __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<F2>& sd,
@@ -217,26 +227,8 @@ struct TwoStepTile {
         const int nx = sd.nx, ny = sd.ny, pitch = sd.pitch;
         const int rank = threadIdx.x;
         if (step + 1 < sd.end) {  // block-uniform
-#define LBM_TB2_TILE(V, B) \
-    tb2_tile<T, V, B>(src, dst, nx, ny, pitch, plane, sd.k, sd.tx, sd.ty, tile.x0, tile.y0, sm, rank)
-            if (sd.bc == kPeriodic) {
-                switch (sd.variant) {
-                    case kTypeI: LBM_TB2_TILE(kTypeI, kPeriodic); break;
-                    case kTypeII: LBM_TB2_TILE(kTypeII, kPeriodic); break;
-                    case kTypeIII: LBM_TB2_TILE(kTypeIII, kPeriodic); break;
-                    case kViscous: LBM_TB2_TILE(kViscous, kPeriodic); break;
-                    default: LBM_TB2_TILE(kNone, kPeriodic); break;
-                }
-            } else {
-                switch (sd.variant) {
-                    case kTypeI: LBM_TB2_TILE(kTypeI, kDirichlet); break;
-                    case kTypeII: LBM_TB2_TILE(kTypeII, kDirichlet); break;
-                    case kTypeIII: LBM_TB2_TILE(kTypeIII, kDirichlet); break;
-                    case kViscous: LBM_TB2_TILE(kViscous, kDirichlet); break;
-                    default: LBM_TB2_TILE(kNone, kDirichlet); break;
-                }
-            }
-#undef LBM_TB2_TILE
+            tb2_tile<T, VAR, BC>(src, dst, nx, ny, pitch, plane, sd.k, sd.tx, sd.ty, tile.x0,
+                                 tile.y0, sm, rank);
             return;
         }
         // the last step of the budget: one step on the tile's pairs
@@ -247,17 +239,9 @@ struct TwoStepTile {
             F2 v[9];
             if (x > 0 && x + 2 < nx && y > 0 && y + 1 < ny)
                 pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch), o, v);
-            else if (sd.bc == kPeriodic)
-                pull_pair_edge<T, kPeriodic>(src, plane, pitch, x, y, nx, ny, v);
             else
-                pull_pair_edge<T, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
-            switch (sd.variant) {
-                case kTypeI: collide_pair<kTypeI>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeII: collide_pair<kTypeII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeIII: collide_pair<kTypeIII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kViscous: collide_pair<kViscous>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                default: collide_pair<kNone>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-            }
+                pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v);
+            collide_pair<VAR>(v, x, y, nx, sd.k, sd.tx, sd.ty);
             if (x + 1 < nx)
                 store_pair<T>(dst, plane, o, v);
             else
@@ -304,20 +288,21 @@ __global__ void __launch_bounds__(256, 3)
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
-// Two steps of every active instance per launch (64 x 16 tiles, 256 threads,
-// tb_smem_bytes<T>() of dynamic shared memory).
-template <typename T>
+// Two steps of every active instance of class batch_class(VAR, BC) per launch
+// (64 x 16 tiles, 256 threads, tb_smem_bytes<T>() of dynamic shared memory).
+// table: [0] all tiles, [1 + 2c] first tile and [2 + 2c] tile count of class c.
+template <typename T, int VAR, int BC>
 __global__ void __launch_bounds__(kTbThreads, 3)
     batch_tb2_kernel(const BatchInst<F2>* __restrict__ insts, const BatchTile* __restrict__ tiles,
-                     const int* __restrict__ ntiles_p, const long long* __restrict__ counters,
+                     const int* __restrict__ table, const long long* __restrict__ counters,
                      int step_off, int launch_off) {
     __shared__ __align__(16) unsigned char raw[sizeof(BatchInst<F2>)];
     extern __shared__ __align__(16) unsigned char tb_raw[];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    TwoStepTile<T> body{reinterpret_cast<T*>(tb_raw)};
-    walk_tiles(insts, tiles, *ntiles_p, counters[0] + step_off,
-               (int)((counters[1] + launch_off) & 1), raw,
-               body);
+    constexpr int c = batch_class(VAR, BC);
+    TwoStepTile<T, VAR, BC> body{reinterpret_cast<T*>(tb_raw)};
+    walk_tiles(insts, tiles + table[1 + 2 * c], table[2 + 2 * c], counters[0] + step_off,
+               (int)((counters[1] + launch_off) & 1), raw, body);
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
@@ -330,7 +315,7 @@ __global__ void advance_counters_kernel(long long* counters, int steps, int laun
 // needs cells == 2).
 template <typename T>
 const void* batch_kernel_ptr(int cells, int spl) {
-    if (spl == 2) return reinterpret_cast<const void*>(&batch_tb2_kernel<T>);
+    if (spl == 2) return reinterpret_cast<const void*>(&batch_tb2_kernel<T, kTypeII, kDirichlet>);
     if (cells == 2) return reinterpret_cast<const void*>(&batch_step2_kernel<T>);
     return reinterpret_cast<const void*>(&batch_step_kernel<T>);
 }
@@ -344,11 +329,37 @@ size_t batch_smem(int spl) {
     return spl == 2 ? tb_smem_bytes<T>() : 0;
 }
 
+// The two-step kernel of class c.
+template <typename T>
+cudaError_t launch_tb2_class(int c, cudaLaunchConfig_t& cfg, const BatchInst<F2>* insts,
+                             const BatchTile* tiles, const int* table, const long long* counters,
+                             int step_off, int launch_off) {
+#define LBM_TB2_CLASS(V, B)                                                                    \
+    if (c == batch_class(V, B))                                                                \
+        return cudaLaunchKernelEx(&cfg, batch_tb2_kernel<T, V, B>, insts, tiles, table, counters, \
+                                  step_off, launch_off);
+    LBM_TB2_CLASS(kNone, kDirichlet)
+    LBM_TB2_CLASS(kTypeI, kDirichlet)
+    LBM_TB2_CLASS(kTypeII, kDirichlet)
+    LBM_TB2_CLASS(kTypeIII, kDirichlet)
+    LBM_TB2_CLASS(kViscous, kDirichlet)
+    LBM_TB2_CLASS(kNone, kPeriodic)
+    LBM_TB2_CLASS(kTypeI, kPeriodic)
+    LBM_TB2_CLASS(kTypeII, kPeriodic)
+    LBM_TB2_CLASS(kTypeIII, kPeriodic)
+    LBM_TB2_CLASS(kViscous, kPeriodic)
+#undef LBM_TB2_CLASS
+    return cudaErrorInvalidValue;
+}
+
 // One batched launch: step_off / launch_off added to the device counters.
+// Two-step launches run one kernel per class in class_mask, each a
+// programmatic dependent of the one before.
 template <typename T>
 cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int* ntiles,
                            const long long* counters, int step_off, int launch_off, int tile_x,
-                           int tile_y, int grid, int cells, int spl, cudaStream_t st, int pdl) {
+                           int tile_y, int grid, int cells, int spl, cudaStream_t st, int pdl,
+                           int class_mask) {
     using CT = typename Codec<T>::CT;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -362,9 +373,16 @@ cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int*
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     const auto* ip2 = static_cast<const BatchInst<F2>*>(insts);
-    if (spl == 2)
-        return cudaLaunchKernelEx(&cfg, batch_tb2_kernel<T>, ip2, tiles, ntiles, counters,
-                                  step_off, launch_off);
+    if (spl == 2) {
+        for (int c = 0; c < kClasses; ++c) {
+            if (!((class_mask >> c) & 1)) continue;
+            const cudaError_t e =
+                launch_tb2_class<T>(c, cfg, ip2, tiles, ntiles, counters, step_off, launch_off);
+            if (e != cudaSuccess) return e;
+            cfg.numAttrs = 1;  // the next class depends on this one
+        }
+        return cudaSuccess;
+    }
     if (cells == 2)
         return cudaLaunchKernelEx(&cfg, batch_step2_kernel<T>, ip2, tiles, ntiles, counters,
                                   step_off, launch_off, tile_y);
@@ -375,7 +393,7 @@ template <>
 cudaError_t launch_batch_t<double>(const void* insts, const BatchTile* tiles, const int* ntiles,
                                    const long long* counters, int step_off, int launch_off,
                                    int tile_x, int tile_y, int grid, int, int, cudaStream_t st,
-                                   int pdl) {
+                                   int pdl, int) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(tile_x, 256 / tile_x);
@@ -442,7 +460,7 @@ struct lbm_batch_ctx {
     size_t insts_cap = 0;  // bytes
     BatchTile* d_tiles = nullptr;
     size_t tiles_cap = 0;  // entries
-    int* d_ntiles = nullptr;
+    int* d_ntiles = nullptr;  // [0] tiles, [1 + 2c] first tile and [2 + 2c] tiles of class c
     long long* d_counters = nullptr;  // [0] global step, [1] global launch
     double* d_diag = nullptr;
     double* staging = nullptr;
@@ -452,7 +470,9 @@ struct lbm_batch_ctx {
     // host images of the device tables, kept as the source of their uploads
     std::vector<unsigned char> h_descs;
     std::vector<BatchTile> h_tiles;
-    int h_ntiles = 0;
+    int h_ntiles[1 + 2 * lbm::kClasses] = {};  // host image of d_ntiles (256 bytes allocated)
+    int class_mask = 0;  // classes with tiles
+    int graph_mask = 0;  // classes the captured graph launches
     // buffers of removed instances, freed once the launches issued before the
     // removal have completed (their event), so that removal never waits
     struct Retired {
@@ -590,19 +610,20 @@ cudaError_t launch_batch(lbm_batch_ctx* b, cudaStream_t st, int steps, int step_
         case LBM_F64:
             return lbm::launch_batch_t<double>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
                                                step_off, launch_off, tx, ty, b->grid, 1, 1, st,
-                                               pdl);
+                                               pdl, b->class_mask);
         case LBM_F32:
             return lbm::launch_batch_t<float>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
                                               step_off, launch_off, tx, ty, b->grid, b->cpt, spl,
-                                              st, pdl);
+                                              st, pdl, b->class_mask);
         case LBM_F16DEV:
             return lbm::launch_batch_t<__half>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
                                                step_off, launch_off, tx, ty, b->grid, b->cpt, spl,
-                                               st, pdl);
+                                               st, pdl, b->class_mask);
         default:
             return lbm::launch_batch_t<__nv_bfloat16>(b->d_insts, b->d_tiles, b->d_ntiles,
                                                       b->d_counters, step_off, launch_off, tx, ty,
-                                                      b->grid, b->cpt, spl, st, pdl);
+                                                      b->grid, b->cpt, spl, st, pdl,
+                                                      b->class_mask);
     }
 }
 
@@ -654,6 +675,7 @@ int sync_tables(lbm_batch_ctx* b) {
     std::vector<BatchTile>& tiles = b->h_tiles;
     descs.clear();
     tiles.clear();
+    std::vector<BatchTile> per_class[lbm::kClasses];
     const size_t ds = desc_size(b->storage, b->cpt);
     for (auto& kv : b->insts) {
         const Instance& in = kv.second;
@@ -674,9 +696,20 @@ int sync_tables(lbm_batch_ctx* b) {
         if (!in.initialised) continue;
         const int tx = b->spl == 2 ? lbm::kTbW : b->tile_x;
         const int ty = b->spl == 2 ? lbm::kTbH : b->tile_y;
+        std::vector<BatchTile>& out = per_class[lbm::batch_class(in.variant, in.bc)];
         for (int y0 = 0; y0 < in.ny; y0 += ty)
-            for (int x0 = 0; x0 < in.nx; x0 += tx) tiles.push_back(BatchTile{di, x0, y0, 0});
+            for (int x0 = 0; x0 < in.nx; x0 += tx) out.push_back(BatchTile{di, x0, y0, 0});
     }
+    // the tiles of each class together (the two-step launch runs a kernel per class)
+    int mask = 0;
+    for (int c = 0; c < lbm::kClasses; ++c) {
+        b->h_ntiles[1 + 2 * c] = static_cast<int>(tiles.size());
+        b->h_ntiles[2 + 2 * c] = static_cast<int>(per_class[c].size());
+        if (!per_class[c].empty()) mask |= 1 << c;
+        tiles.insert(tiles.end(), per_class[c].begin(), per_class[c].end());
+    }
+    b->class_mask = mask;
+    if (b->graph && b->spl == 2 && mask != b->graph_mask) drop_batch_graph(b);
     bool realloc = false;
     if (descs.size() > b->insts_cap) {
         cudaStreamSynchronize(b->stream);
@@ -701,9 +734,10 @@ int sync_tables(lbm_batch_ctx* b) {
     if (e == cudaSuccess && !tiles.empty())
         e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile),
                             cudaMemcpyHostToDevice, b->stream);
-    b->h_ntiles = static_cast<int>(tiles.size());
+    b->h_ntiles[0] = static_cast<int>(tiles.size());
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_ntiles, &b->h_ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+        e = cudaMemcpyAsync(b->d_ntiles, b->h_ntiles, sizeof(b->h_ntiles), cudaMemcpyHostToDevice,
+                            b->stream);
     // Stream-ordered after the launches that read the old tables.  The host
     // images live in the context, so nothing here waits for the device.
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(e));
@@ -732,6 +766,7 @@ cudaError_t ensure_batch_graph(lbm_batch_ctx* b) {
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
     if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) b->graph_mask = b->class_mask;
     return e;
 }
 
@@ -794,6 +829,7 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
         delete b;
         return LBM_ERR_CUDA;
     }
+    static_assert(sizeof(b->h_ntiles) <= 256, "tile counts must fit their allocation");
     b->d_ntiles = static_cast<int*>(bd_alloc(b, 256));
     b->d_counters = static_cast<long long*>(bd_alloc(b, 256));
     b->d_diag = static_cast<double*>(bd_alloc(b, sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag)));
@@ -801,7 +837,7 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
         lbm_batch_destroy(b);
         return LBM_ERR_OOM;
     }
-    e = cudaMemsetAsync(b->d_ntiles, 0, sizeof(int), b->stream);
+    e = cudaMemsetAsync(b->d_ntiles, 0, sizeof(b->h_ntiles), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(long long), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
