@@ -428,14 +428,17 @@ def profiled_traffic():
 STEP_KERNEL = {1: "lbm::step_kernel<float, variant, Dirichlet> (one cell per thread)",
                2: "lbm::step2_kernel<float, variant, Dirichlet> (two cells per thread, packed FP32)",
                "tb2": "lbm::step_tb2_kernel<float, variant, Dirichlet> (two cells per thread, "
-                      "two time steps per launch through shared memory)"}
+                      "two time steps per launch through shared memory)",
+               "tb2_tma": "lbm::step_tb2_tma_kernel<variant> (two time steps per launch, each "
+                          "tile's input staged by one TMA bulk tensor copy)"}
 
 
-def timed_steps(w, steps: int, cells=None, per_launch=None, warm: int = 10):
-    """(seconds, steps per launch) for `steps` steps of workload w (device pulse
-    init, `warm` untimed steps first), through the graph-replayed lbm_step on a
-    side stream; cells = cells per thread, per_launch = time steps per launch
-    (None: the library's default for the lattice)."""
+def timed_steps(w, steps: int, cells=None, per_launch=None, warm: int = 10, tma=None):
+    """(seconds, steps per launch, TMA staging) for `steps` steps of workload w
+    (device pulse init, `warm` untimed steps first), through the graph-replayed
+    lbm_step on a side stream; cells = cells per thread, per_launch = time
+    steps per launch, tma = TMA staging of two-step launches (None: the
+    library's default for the lattice)."""
     import torch
 
     from paper_1203_6350_gb300 import lbm
@@ -447,7 +450,10 @@ def timed_steps(w, steps: int, cells=None, per_launch=None, warm: int = 10):
             lat.cells_per_thread = cells
         if per_launch is not None:
             lat.steps_per_launch = per_launch
+        if tma is not None:
+            lat.tma_staging = tma
         spl = lat.steps_per_launch
+        staged = spl == 2 and lat.tma_staging
         lat.step(warm)
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
@@ -456,7 +462,7 @@ def timed_steps(w, steps: int, cells=None, per_launch=None, warm: int = 10):
         z.record(stream)
         z.synchronize()
         lat.close()
-    return a.elapsed_time(z) / 1e3, spl
+    return a.elapsed_time(z) / 1e3, spl, staged
 
 
 def roofline_large(peaks, side: int = 4096, steps: int = 100):
@@ -467,20 +473,24 @@ def roofline_large(peaks, side: int = 4096, steps: int = 100):
     written once), whether the launch advances one step or two."""
     w = wl.quiescent(side, storage="f32", steps=steps, width=128, pulse=True)
     out = {}
-    for key, cells, per_launch in (("default", None, None), ("one_step_per_launch", 2, 1),
-                                   ("one_cell_per_thread", 1, 1)):
-        t, spl = timed_steps(w, steps, cells=cells, per_launch=per_launch)
+    for key, cells, per_launch, tma in (("default", None, None, None),
+                                        ("two_steps_plain_loads", 2, 2, False),
+                                        ("one_step_per_launch", 2, 1, None),
+                                        ("one_cell_per_thread", 1, 1, None)):
+        t, spl, staged = timed_steps(w, steps, cells=cells, per_launch=per_launch, tma=tma)
         per_launch_s = t / (steps / spl)
         out[key] = {"steps_per_launch": spl, "avg_launch_us": per_launch_s * 1e6,
                     "mlups": w.cells * steps / t / 1e6,
                     "achieved": BYTES_PER_CELL["f32"] * w.cells / per_launch_s / 1e9,
-                    "kernel": STEP_KERNEL["tb2" if spl == 2 else (cells or 2)]}
+                    "kernel": STEP_KERNEL[("tb2_tma" if staged else "tb2") if spl == 2
+                                          else (cells or 2)]}
     d = out["default"]
     return {"bound": "hbm", "achieved": d["achieved"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": d["achieved"] / peaks["hbm_gbs"], "case": f"{side}x{side} FP32, 128-cell layer",
             "kernel": d["kernel"], "steps_per_launch": d["steps_per_launch"],
             "avg_launch_us": d["avg_launch_us"], "mlups": d["mlups"],
             "bytes_per_launch": BYTES_PER_CELL["f32"] * w.cells,
+            "two_steps_plain_loads": out["two_steps_plain_loads"],
             "one_step_per_launch": out["one_step_per_launch"],
             "one_cell_per_thread": out["one_cell_per_thread"],
             "traffic_profile": "profiles/step_tb2_kernel_f32_4096x4096_full.md"}
@@ -655,11 +665,12 @@ def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", 
         for st in storages:
             w = wl.quiescent(side, storage=st, steps=steps, width=128)
             for cells, per_launch in ((None, None), (2, 1), (1, 1)):
-                t, spl = timed_steps(w, steps, cells=cells, per_launch=per_launch)
+                t, spl, staged = timed_steps(w, steps, cells=cells, per_launch=per_launch)
                 launches = steps / spl
                 gbs = BYTES_PER_CELL[st] * w.cells * launches / t / 1e9
                 rows.append({"side": side, "storage": st, "cells_per_thread": cells or 2,
-                             "steps_per_launch": spl, "library_default": cells is None,
+                             "steps_per_launch": spl, "tma_staging": staged,
+                             "library_default": cells is None,
                              "bytes_per_cell_launch": BYTES_PER_CELL[st],
                              "bytes_per_cell_step": BYTES_PER_CELL[st] / spl,
                              "mlups": w.cells * steps / t / 1e6, "gbs": gbs,

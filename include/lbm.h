@@ -216,6 +216,22 @@ int lbm_set_steps_per_launch(lbm_handle h, int steps);
 int lbm_steps_per_launch(lbm_handle h);
 
 /* Replace the handle's stream (borrowed; NULL = legacy default stream). */
+/* Staging of the two-step launches' input by the Tensor Memory Accelerator.
+ * With it (1), each 64 x 16 tile's input -- the nine planes of the 72 x 20
+ * cells around it -- arrives in shared memory as one bulk tensor copy whose
+ * out-of-lattice elements read as zero (the Dirichlet far-field deviation);
+ * the copy of a CTA's next tile overlaps the current tile's second step.
+ * The results are bit-identical to those without it (0).  Available for
+ * LBM_F32 storage with LBM_BC_DIRICHLET_EQ, and then the default (the
+ * environment variable LBM_TMA=0 at lbm_create turns the default off);
+ * LBM_ERR_ARG for other handles or values.  A staged copy that has not
+ * completed after a bounded wait stops its CTA and makes the next
+ * lbm_moments / lbm_diagnostics / lbm_get_state on the host return
+ * LBM_ERR_CUDA.  Waits for the handle's stream.  lbm_tma_staging returns 1
+ * or 0. */
+int lbm_set_tma_staging(lbm_handle h, int on);
+int lbm_tma_staging(lbm_handle h);
+
 int lbm_set_stream(lbm_handle h, void* cuda_stream);
 
 /* The line source of an LBM_BC_CHANNEL lattice (Sec. 4.2): density

@@ -48,6 +48,11 @@ struct lbm_ctx {
     int64_t time = 0;
     int launch_mode = 2;              // kLaunchGraph; LBM_LAUNCH=plain|pdl|graph overrides
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphChunk steps from buffer 0 / 1
+    bool tma = false;                 // two-step launches stage their input by TMA (FP32, Dirichlet)
+    bool tma_ready = false;           // tmap / tma_grid / tma_err are set up
+    CUtensorMap tmap[2];              // tensor maps of buf[0], buf[1]
+    int tma_grid = 0;                 // persistent CTAs of the TMA kernel
+    int* tma_err = nullptr;           // set on the device when a staged copy timed out
     cudaStream_t capture_stream = nullptr;
     std::string err;
 };
@@ -204,12 +209,51 @@ cudaError_t launch_two_steps(lbm_ctx* h, const void* src, void* dst, cudaStream_
     const int p = pdl ? 1 : 0;
     const auto* tx = static_cast<const lbm::AxisCoef<float>*>(h->chi_x);
     const auto* ty = static_cast<const lbm::AxisCoef<float>*>(h->chi_y);
+    if (h->tma)
+        return lbm::launch_step_tb2_tma_f32(h->tmap[src == h->buf[0] ? 0 : 1], dst, h->geo, h->k2,
+                                            tx, ty, h->variant, h->tma_grid, h->tma_err, st, p);
     switch (h->storage) {
         case LBM_F32: return lbm::launch_step_tb2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
         case LBM_F16DEV: return lbm::launch_step_tb2_f16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
         case LBM_BF16DEV: return lbm::launch_step_tb2_bf16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Tensor maps, persistent grid and error flag of the TMA two-step kernel;
+// LBM_OK, or the reason it is not available for this handle.
+int setup_tma(lbm_ctx* h) {
+    if (h->tma_ready) return LBM_OK;
+    if (h->storage != LBM_F32 || h->bc != LBM_BC_DIRICHLET_EQ)
+        return fail(h, LBM_ERR_ARG, "TMA staging needs FP32 storage and the Dirichlet boundary");
+    int per_sm = 0, sms = 0;
+    cudaError_t e = lbm::prepare_step_tb2_tma_f32(&per_sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "TMA kernel set-up");
+    if (per_sm < 1) return fail(h, LBM_ERR_CUDA, "the TMA kernel does not fit an SM");
+    if (!lbm::encode_tma_map_f32(&h->tmap[0], h->buf[0], h->geo) ||
+        !lbm::encode_tma_map_f32(&h->tmap[1], h->buf[1], h->geo))
+        return fail(h, LBM_ERR_CUDA, "the driver did not encode the tensor maps");
+    if (!h->tma_err) {
+        h->tma_err = static_cast<int*>(dev_alloc(h, 256));
+        if (!h->tma_err) return fail(h, LBM_ERR_OOM, "TMA error flag allocation failed");
+        e = cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "TMA error flag");
+    }
+    h->tma_grid = per_sm * sms;
+    h->tma_ready = true;
+    return LBM_OK;
+}
+
+// After the stream is synchronised: LBM_ERR_CUDA if a staged copy timed out.
+int check_tma(lbm_ctx* h) {
+    if (!h->tma_err) return LBM_OK;
+    int flag = 0;
+    const cudaError_t e = cudaMemcpy(&flag, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "TMA error flag");
+    if (flag) return fail(h, LBM_ERR_CUDA, "a TMA-staged copy did not complete within its wait");
+    return LBM_OK;
 }
 
 void drop_graphs(lbm_ctx* h) {
@@ -359,6 +403,12 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
         if (!std::strcmp(c, "1")) h->spl = 1;
     }
     if (bc == LBM_BC_CHANNEL) h->spl = 1;  // the two-step tiles have no channel edges
+    // FP32 Dirichlet lattices stage the two-step tiles' input by TMA
+    // (LBM_TMA=0 keeps the plain-load kernel); without it they keep the other kernel.
+    const char* tma_env = std::getenv("LBM_TMA");
+    if (storage == LBM_F32 && bc == LBM_BC_DIRICHLET_EQ && !(tma_env && !std::strcmp(tma_env, "0")))
+        h->tma = setup_tma(h) == LBM_OK;
+    h->err.clear();
     set_source_shape(h);
     if (const char* m = std::getenv("LBM_LAUNCH")) {
         if (!std::strcmp(m, "plain")) h->launch_mode = kLaunchPlain;
@@ -553,7 +603,7 @@ int lbm_moments(lbm_handle h, double* rho_dev, double* ux, double* uy, int on_de
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_moments");
-    return LBM_OK;
+    return on_device ? LBM_OK : check_tma(h);
 }
 
 int lbm_diagnostics(lbm_handle h, int x0, int y0, int x1, int y1, double out[6]) {
@@ -570,6 +620,7 @@ int lbm_diagnostics(lbm_handle h, int x0, int y0, int x1, int y1, double out[6])
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, lbm::kDiag * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_diagnostics");
+    if (const int rc = check_tma(h)) return rc;
     if (out[5] > 0) return fail(h, LBM_ERR_NONFINITE, "the state holds non-finite values");
     return LBM_OK;
 }
@@ -585,7 +636,7 @@ int lbm_get_state(lbm_handle h, void* dst, size_t bytes, int on_device, int64_t*
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_state");
     if (time) *time = h->time;
-    return LBM_OK;
+    return on_device ? LBM_OK : check_tma(h);
 }
 
 int lbm_set_state(lbm_handle h, const void* src, size_t bytes, int on_device, int64_t time) {
@@ -647,6 +698,23 @@ int lbm_set_steps_per_launch(lbm_handle h, int steps) {
 
 int lbm_steps_per_launch(lbm_handle h) { return h ? h->spl : LBM_ERR_ARG; }
 
+int lbm_set_tma_staging(lbm_handle h, int on) {
+    if (!h) return LBM_ERR_ARG;
+    if (on != 0 && on != 1) return fail(h, LBM_ERR_ARG, "on must be 0 or 1");
+    if (on == (h->tma ? 1 : 0)) return LBM_OK;
+    DeviceGuard dg(h->device);
+    if (on) {
+        const int rc = setup_tma(h);
+        if (rc != LBM_OK) return rc;
+    }
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);  // the captured launches name the other kernel
+    h->tma = on == 1;
+    return LBM_OK;
+}
+
+int lbm_tma_staging(lbm_handle h) { return h ? (h->tma ? 1 : 0) : LBM_ERR_ARG; }
+
 int lbm_set_source(lbm_handle h, double amplitude, double omega, double phase) {
     if (!h) return LBM_ERR_ARG;
     if (h->bc != LBM_BC_CHANNEL) return fail(h, LBM_ERR_ARG, "a line source needs the channel boundary");
@@ -681,6 +749,7 @@ void lbm_destroy(lbm_handle h) {
     dev_free(h, h->chi_y, h->chi_bytes_y);
     dev_free(h, h->diag, h->diag_bytes);
     dev_free(h, h->d_time, 256);
+    dev_free(h, h->tma_err, 256);
     dev_free(h, h->staging, h->staging_bytes);
     delete h;
 }

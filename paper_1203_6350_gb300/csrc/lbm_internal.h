@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -230,6 +231,20 @@ cudaError_t launch_step_tb2_bf16(const void* src, void* dst, const Geometry& g,
                                  const StepConst<F2>& k, const AxisCoef<float>* tx,
                                  const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
                                  int pdl);
+
+// Two steps per launch with the tile's input staged by TMA (FP32, Dirichlet):
+// src_map describes the buffer holding time t (extent nx x ny x 9 planes,
+// box 72 x 20 x 9 floats); a persistent grid of `grid` CTAs; *err is set when
+// a copy did not complete within the bounded wait.
+cudaError_t launch_step_tb2_tma_f32(const CUtensorMap& src_map, void* dst, const Geometry& g,
+                                   const StepConst<F2>& k, const AxisCoef<float>* tx,
+                                   const AxisCoef<float>* ty, int variant, int grid, int* err,
+                                   cudaStream_t st, int pdl);
+// Shared-memory attributes of the TMA kernels; per_sm receives CTAs per SM.
+cudaError_t prepare_step_tb2_tma_f32(int* per_sm);
+// The tensor map of one FP32 population buffer for the TMA kernel; false when
+// the driver cannot encode it.
+bool encode_tma_map_f32(CUtensorMap* map, void* base, const Geometry& g);
 
 // Base-state parameters of the auxiliary kernels (always FP64).
 struct BaseState {

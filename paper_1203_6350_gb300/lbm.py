@@ -84,6 +84,8 @@ SIGNATURES = [
     ("lbm_cells_per_thread", ctypes.c_int, [_vp]),
     ("lbm_set_steps_per_launch", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_steps_per_launch", ctypes.c_int, [_vp]),
+    ("lbm_set_tma_staging", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_tma_staging", ctypes.c_int, [_vp]),
     ("lbm_destroy", None, [_vp]),
     ("lbm_last_error", ctypes.c_char_p, [_vp]),
     ("lbm_version", ctypes.c_char_p, []),
@@ -264,6 +266,14 @@ def lbm_set_steps_per_launch(h, steps) -> int:
 
 def lbm_steps_per_launch(h) -> int:
     return load().lbm_steps_per_launch(h)
+
+
+def lbm_set_tma_staging(h, on) -> int:
+    return load().lbm_set_tma_staging(h, int(on))
+
+
+def lbm_tma_staging(h) -> int:
+    return load().lbm_tma_staging(h)
 
 
 def lbm_destroy(h) -> None:
@@ -512,6 +522,15 @@ class Lattice:
         else:
             lat.init_equilibrium(*w.initial_fields())
         return lat
+
+    @property
+    def tma_staging(self) -> bool:
+        """Whether two-step launches stage their input by TMA (FP32, Dirichlet)."""
+        return lbm_tma_staging(self.h) == 1
+
+    @tma_staging.setter
+    def tma_staging(self, on: bool) -> None:
+        check(lbm_set_tma_staging(self.h, 1 if on else 0), self.h, "lbm_set_tma_staging")
 
     def set_source(self, amplitude: float, omega: float, phase: float = 0.0) -> None:
         """Line source of a channel lattice (Sec. 4.2): rho0 + amplitude

@@ -1,0 +1,100 @@
+"""The two-step kernel with TMA-staged input (FP32, Dirichlet) against the
+same two-step arithmetic on plain loads: bit-identical stored states on
+ragged, tiny and large lattices, every damping variant, odd step counts (the
+one-step remainder) and graph-replayed chunks; where it is available.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6350_gb300 import lbm
+
+    lbm.load()
+
+
+def _state(w, tma, steps, chunks=None):
+    from paper_1203_6350_gb300 import lbm
+
+    with lbm.Lattice.from_workload(w, storage="f32") as lat:
+        lat.cells_per_thread = 2
+        lat.steps_per_launch = 2
+        lat.tma_staging = tma
+        assert lat.tma_staging == tma
+        for n in (chunks or [steps]):
+            lat.step(n)
+        buf, t = lat.get_state()
+        assert t == steps
+        return buf
+
+
+def _random(nx, ny, variant, seed, steps):
+    rng = np.random.default_rng(seed)
+    return wl.Workload(name=f"tma-{nx}x{ny}", nx=nx, ny=ny,
+                       s=np.array([1.6, 1.6, 1.6, 1.1, 1.2, 1.3, 1.3, 1.9, 1.9]),
+                       variant=variant, bc="dirichlet", n=0.4, m=0.6, rho0=1.0,
+                       u0=(0.04, -0.02), rho_f=1.002, u_f=(0.05, -0.01),
+                       chi_x=rng.uniform(0, 0.5, nx), chi_y=rng.uniform(0, 0.5, ny),
+                       rho_dev=1e-3 * rng.standard_normal((ny, nx)), steps=steps, storage="f32")
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (3, 5), (64, 16), (65, 17), (129, 33),
+                                   (1025, 40), (300, 200)])
+@pytest.mark.parametrize("variant", ["none", "I", "II", "III", "viscous"])
+def test_tma_staging_is_bit_identical_to_plain_loads(shape, variant):
+    w = _random(*shape, variant, seed=shape[0] * 7 + shape[1], steps=11)
+    a = _state(w, True, w.steps)
+    b = _state(w, False, w.steps)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_tma_staging_across_graph_chunks():
+    """150 steps as 64 + 64 + 22: graph replays of 32 two-step launches and a
+    one-step remainder."""
+    w = _random(333, 97, "II", seed=5, steps=150)
+    a = _state(w, True, w.steps, chunks=[64, 64, 22])
+    b = _state(w, False, w.steps, chunks=[150])
+    np.testing.assert_array_equal(a, b)
+
+
+def test_tma_staging_availability():
+    from paper_1203_6350_gb300 import lbm
+
+    w = _random(64, 16, "II", seed=1, steps=2)
+    with lbm.Lattice.from_workload(w, storage="f32") as lat:
+        assert lat.tma_staging  # the default for FP32 with the Dirichlet boundary
+    with lbm.Lattice.from_workload(w.with_(bc="periodic"), storage="f32") as lat:
+        assert not lat.tma_staging
+        with pytest.raises(lbm.LbmError):
+            lat.tma_staging = True
+    with lbm.Lattice.from_workload(w, storage="f16dev") as lat:
+        assert not lat.tma_staging
+        assert lbm.lbm_set_tma_staging(lat.h, 1) == lbm.LBM_ERR_ARG
+        assert lbm.lbm_set_tma_staging(lat.h, 0) == lbm.LBM_OK
+        assert lbm.lbm_set_tma_staging(lat.h, 2) == lbm.LBM_ERR_ARG
+
+
+def test_tma_staging_at_2048_is_bit_identical_to_plain_loads():
+    """The 2048^2 pulse with its 128-cell layer, 200 steps in the library's
+    default launch configuration there (two steps per launch, TMA staging:
+    the configuration whose result test_gpu_parity holds to 1e-5 of the
+    oracle), against plain loads."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.quiescent(2048, storage="f32", steps=200, pulse=True)
+    states = []
+    for tma in (True, False):
+        with lbm.Lattice.from_workload(w) as lat:
+            assert lat.steps_per_launch == 2 and lat.tma_staging
+            lat.tma_staging = tma
+            lat.step(w.steps)
+            states.append(lat.get_state()[0])
+    np.testing.assert_array_equal(states[0], states[1])
