@@ -222,9 +222,10 @@ int lbm_steps_per_launch(lbm_handle h);
  * out-of-lattice elements read as zero (the Dirichlet far-field deviation);
  * the copy of a CTA's next tile overlaps the current tile's second step.
  * The results are bit-identical to those without it (0).  Available for
- * LBM_F32 storage with LBM_BC_DIRICHLET_EQ, and then the default (the
- * environment variable LBM_TMA=0 at lbm_create turns the default off);
- * LBM_ERR_ARG for other handles or values.  A staged copy that has not
+ * LBM_F32 storage with LBM_BC_DIRICHLET_EQ; the default where both
+ * population buffers together exceed four times the L2 size (the environment
+ * variable LBM_TMA=0 or 1 at lbm_create overrides that choice); LBM_ERR_ARG
+ * for other handles or values.  A staged copy that has not
  * completed after a bounded wait stops its CTA and makes the next
  * lbm_moments / lbm_diagnostics / lbm_get_state on the host return
  * LBM_ERR_CUDA.  Waits for the handle's stream.  lbm_tma_staging returns 1

@@ -403,10 +403,13 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
         if (!std::strcmp(c, "1")) h->spl = 1;
     }
     if (bc == LBM_BC_CHANNEL) h->spl = 1;  // the two-step tiles have no channel edges
-    // FP32 Dirichlet lattices stage the two-step tiles' input by TMA
-    // (LBM_TMA=0 keeps the plain-load kernel); without it they keep the other kernel.
+    // FP32 Dirichlet lattices whose state exceeds four times L2 stage the
+    // two-step tiles' input by TMA: measured 2-8 % ahead of plain loads from
+    // 4096^2 up, 3 % behind at 2048^2 (LBM_TMA=0 or 1 overrides the choice).
     const char* tma_env = std::getenv("LBM_TMA");
-    if (storage == LBM_F32 && bc == LBM_BC_DIRICHLET_EQ && !(tma_env && !std::strcmp(tma_env, "0")))
+    bool want_tma = h->spl == 2 && 2 * h->buf_bytes > 4 * static_cast<size_t>(l2);
+    if (tma_env) want_tma = std::strcmp(tma_env, "0") != 0;
+    if (storage == LBM_F32 && bc == LBM_BC_DIRICHLET_EQ && want_tma)
         h->tma = setup_tma(h) == LBM_OK;
     h->err.clear();
     set_source_shape(h);

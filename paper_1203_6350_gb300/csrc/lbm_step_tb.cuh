@@ -64,18 +64,18 @@ __device__ __forceinline__ void pull_lanes(const T* __restrict__ s, unsigned pla
               pull_one<T, BC, 8>(s, plane, pitch, cb, y, nx, ny));
 }
 
-// Two steps on the tile at (x0, y0) by a block of kTbThreads threads (any
-// shape, numbered by thread_rank): src holds time t, dst receives time t + 2;
+// Two steps on the tile at (x0, y0) by a block of NT threads (any shape,
+// numbered by thread_rank): src holds time t, dst receives time t + 2;
 // sm is the block's tb_smem_bytes<T>() of shared memory.  Ends with a block
 // barrier, so the caller may reuse sm for the next tile right away.
-template <typename T, int VAR, int BC>
+template <typename T, int VAR, int BC, int NT = kTbThreads>
 __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restrict__ dst, int nx,
                                          int ny, int pitch, unsigned plane, const StepConst<F2>& k,
                                          const AxisCoef<float>* __restrict__ tx,
                                          const AxisCoef<float>* __restrict__ ty, int x0, int y0,
                                          T* sm, int thread_rank) {
     // ---- step 1: time t (HBM) -> time t + 1 on R1 (shared memory) ----
-    for (int p = thread_rank; p < kR1Pairs * kR1H; p += kTbThreads) {
+    for (int p = thread_rank; p < kR1Pairs * kR1H; p += NT) {
         const int px = p % kR1Pairs, py = p / kR1Pairs;
         const int x = x0 - 2 + 2 * px, y = y0 - 1 + py;
         F2 v[9];
@@ -112,7 +112,7 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
     __syncthreads();
 
     // ---- step 2: time t + 1 (shared memory) -> time t + 2 on the tile (HBM) ----
-    for (int p = thread_rank; p < (kTbW / 2) * kTbH; p += kTbThreads) {
+    for (int p = thread_rank; p < (kTbW / 2) * kTbH; p += NT) {
         const int qx = p % (kTbW / 2), qy = p / (kTbW / 2);
         const int x = x0 + 2 * qx, y = y0 + qy;
         if (x >= nx || y >= ny) continue;

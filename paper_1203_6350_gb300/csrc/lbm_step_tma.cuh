@@ -12,7 +12,7 @@
 //    (16 bytes) left of the tile, the alignment a tiled copy needs.
 //  - Step one pulls from the staged box; step two from the R1 ring, as in
 //    tb2_tile.  The copy of the next tile is issued as soon as step one has
-//    read the box, so it overlaps step two.  Two CTAs of 384 threads per SM
+//    read the box, so it overlaps step two.  Two CTAs of 320 threads per SM
 //    (96 KB of shared memory each) overlap one another's waits.
 //  - Every wait on the mbarrier gives up after a bounded number of polls; the
 //    CTA then agrees (a barrier vote) to stop, waits once more (bounded) for
@@ -31,7 +31,10 @@ constexpr int kTmaH = kTbH + 4;             // 20: y0 - 2 .. y0 + 17
 constexpr int kTmaPlane = kTmaW * kTmaH;    // elements per plane of the staged box
 constexpr unsigned kTmaBoxBytes = 9u * kTmaPlane * sizeof(float);
 constexpr int kTmaPolls = 1 << 20;          // mbarrier polls before a wait gives up
-constexpr int kTmaThreads = 384;            // 12 warps; two CTAs (96 KB each) per SM
+// 10 warps, two CTAs (96 KB each) per SM: step one's 612 pairs and step
+// two's 512 then take two rounds each at 96 % and 80 % use (256 threads need
+// three rounds for step one; 384 leave a half-empty second round in both).
+constexpr int kTmaThreads = 320;
 
 constexpr unsigned kTmaRingBytes = 9u * kR1Plane * sizeof(float);  // R1 ring (tb_smem_bytes)
 constexpr size_t tma_smem_bytes() {

@@ -70,7 +70,9 @@ def test_tma_staging_availability():
 
     w = _random(64, 16, "II", seed=1, steps=2)
     with lbm.Lattice.from_workload(w, storage="f32") as lat:
-        assert lat.tma_staging  # the default for FP32 with the Dirichlet boundary
+        assert not lat.tma_staging  # the default only above four times L2
+        lat.tma_staging = True
+        assert lat.tma_staging
     with lbm.Lattice.from_workload(w.with_(bc="periodic"), storage="f32") as lat:
         assert not lat.tma_staging
         with pytest.raises(lbm.LbmError):
@@ -83,18 +85,37 @@ def test_tma_staging_availability():
 
 
 def test_tma_staging_at_2048_is_bit_identical_to_plain_loads():
-    """The 2048^2 pulse with its 128-cell layer, 200 steps in the library's
-    default launch configuration there (two steps per launch, TMA staging:
-    the configuration whose result test_gpu_parity holds to 1e-5 of the
-    oracle), against plain loads."""
+    """The 2048^2 pulse with its 128-cell layer, 200 steps of two steps per
+    launch (the library's default there, with plain loads: the configuration
+    whose result test_gpu_parity holds to 1e-5 of the oracle), against TMA
+    staging."""
     from paper_1203_6350_gb300 import lbm
 
     w = wl.quiescent(2048, storage="f32", steps=200, pulse=True)
     states = []
     for tma in (True, False):
         with lbm.Lattice.from_workload(w) as lat:
-            assert lat.steps_per_launch == 2 and lat.tma_staging
+            assert lat.steps_per_launch == 2 and not lat.tma_staging
             lat.tma_staging = tma
+            lat.step(w.steps)
+            states.append(lat.get_state()[0])
+    np.testing.assert_array_equal(states[0], states[1])
+
+
+def test_tma_staging_is_the_default_at_4096_and_matches_plain_loads():
+    """4096^2 (1.2 GB of state, above four times L2): TMA staging by default,
+    20 steps bit-identical to plain loads; the quiescent lattice stays exactly
+    at rest."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.quiescent(4096, storage="f32", steps=20, pulse=True)
+    states = []
+    for tma in (None, False):
+        with lbm.Lattice.from_workload(w) as lat:
+            if tma is None:
+                assert lat.steps_per_launch == 2 and lat.tma_staging
+            else:
+                lat.tma_staging = tma
             lat.step(w.steps)
             states.append(lat.get_state()[0])
     np.testing.assert_array_equal(states[0], states[1])
