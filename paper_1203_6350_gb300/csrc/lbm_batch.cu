@@ -81,12 +81,15 @@ struct BatchMinBlocks<double> {
 // the G blocks sweep one compact stretch of it (a contiguous run per block
 // spreads the DRAM accesses and measured 27 % slower).  The table lists each
 // instance's tiles together: the block copies an instance descriptor to
-// shared memory only when its next tile belongs to another instance, and it
-// fetches the next tile entry while it processes the current one.
+// shared memory only when its next tile belongs to another instance.  It
+// fetches the next tile entry, and the next tile's descriptor when that
+// differs (one word per thread, held in a register), while it processes the
+// current tile, so a switch costs two barriers and a shared-memory store.
 // body(tile, descriptor, step, lpar) runs for the tiles of instances active
 // at `step` (start <= step < end), the first global step of this launch
 // (lpar = parity of the global launch index); every branch on the descriptor
-// is block-uniform.
+// is block-uniform.  Blocks have at most 256 threads, as many as the largest
+// descriptor has words.
 template <typename Inst, typename Body>
 __device__ __forceinline__ void walk_tiles(const Inst* __restrict__ insts,
                                            const BatchTile* __restrict__ tiles, int ntiles,
@@ -95,21 +98,29 @@ __device__ __forceinline__ void walk_tiles(const Inst* __restrict__ insts,
     const Inst& sd = *reinterpret_cast<const Inst*>(raw);
     constexpr int kWords = (int)(sizeof(Inst) / 4);
     static_assert(sizeof(Inst) % 4 == 0, "descriptor must be word-sized");
+    static_assert(kWords <= 256, "one descriptor word per thread");
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthr = blockDim.x * blockDim.y;
     const int G = gridDim.x;
-    int held = -1;  // instance whose descriptor is in shared memory
+    int held = -1;      // instance whose descriptor is in shared memory
+    int fetched = -1;   // instance whose descriptor word this thread holds in `word`
+    unsigned word = 0;
     BatchTile next = (int)blockIdx.x < ntiles ? tiles[blockIdx.x] : BatchTile{};
     for (int t = blockIdx.x; t < ntiles; t += G) {
         const BatchTile tile = next;
         if (t + G < ntiles) next = tiles[t + G];
         if (tile.inst != held) {  // block-uniform
-            __syncthreads();      // everyone is done with the previous descriptor
-            const unsigned* srcw = reinterpret_cast<const unsigned*>(insts + tile.inst);
-            unsigned* dstw = reinterpret_cast<unsigned*>(raw);
-            for (int w = tid; w < kWords; w += nthr) dstw[w] = __ldg(srcw + w);
+            if (fetched != tile.inst && tid < kWords)
+                word = __ldg(reinterpret_cast<const unsigned*>(insts + tile.inst) + tid);
+            __syncthreads();  // everyone is done with the previous descriptor
+            if (tid < kWords) reinterpret_cast<unsigned*>(raw)[tid] = word;
             __syncthreads();
             held = tile.inst;
+        }
+        fetched = -1;
+        if (t + G < ntiles && next.inst != tile.inst) {  // block-uniform
+            if (tid < kWords)
+                word = __ldg(reinterpret_cast<const unsigned*>(insts + next.inst) + tid);
+            fetched = next.inst;
         }
         if (step < sd.start || step >= sd.end) continue;  // block-uniform
         body(tile, sd, step, lpar);
