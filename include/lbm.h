@@ -309,6 +309,13 @@ int lbm_batch_cells_per_thread(lbm_batch b);
 int lbm_batch_set_steps_per_launch(lbm_batch b, int steps);
 /* The current choice (LBM_ERR_ARG for a NULL batch). */
 int lbm_batch_steps_per_launch(lbm_batch b);
+/* 1 when the batch's two-step launches stage the input of its Dirichlet
+ * instances by TMA (as lbm_set_tma_staging does for one lattice; results
+ * bit-identical to plain loads): the default for LBM_F32 batches, chosen at
+ * lbm_batch_create (the environment variable LBM_BATCH_TMA=0 keeps plain
+ * loads).  A staged copy that times out makes the next lbm_batch_moments /
+ * lbm_batch_diagnostics on the host return LBM_ERR_CUDA. */
+int lbm_batch_tma_staging(lbm_batch b);
 
 /* Add an instance (arguments as lbm_create and lbm_set_sponge; chi arrays are
  * host arrays, copied) with a budget of nsteps >= 0 steps.  Allocates its

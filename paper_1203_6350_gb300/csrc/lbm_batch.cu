@@ -24,10 +24,11 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm.h"
-#include "lbm_step_tb.cuh"
+#include "lbm_step_tma.cuh"
 
 namespace lbm {
 
@@ -317,6 +318,142 @@ __global__ void __launch_bounds__(kTbThreads, 3)
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
+// Two steps per launch on the Dirichlet instances of damping variant VAR,
+// each tile's input staged by TMA as in step_tb2_tma_kernel: maps[2 i + p] is
+// the tensor map of buffer p of dense instance i.  Thread 0 plans each tile
+// from the instance's window -- skip (inactive), two staged steps, or the one
+// step that ends a budget (pulled from global memory) -- and issues the next
+// tile's copy as soon as step one has read the box.  Waits are bounded as in
+// the single-lattice kernel; a CTA that gives up sets *err.
+template <int VAR>
+__global__ void __launch_bounds__(kTmaThreads, 2)
+    batch_tb2_tma_kernel(const BatchInst<F2>* __restrict__ insts,
+                         const CUtensorMap* __restrict__ maps, const BatchTile* __restrict__ tiles,
+                         const int* __restrict__ table, const long long* __restrict__ counters,
+                         int step_off, int launch_off, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char tma_raw[];
+    float* box = reinterpret_cast<float*>(tma_raw);
+    float* r1 = reinterpret_cast<float*>(tma_raw + kTmaBoxBytes);
+    auto* bar = reinterpret_cast<unsigned long long*>(tma_raw + kTmaBoxBytes + kTmaRingBytes);
+    auto* mode_sm = reinterpret_cast<int*>(tma_raw + kTmaBoxBytes + kTmaRingBytes + 8);
+    unsigned char* desc_raw = tma_raw + kTmaBoxBytes + kTmaRingBytes + 16;
+    const BatchInst<F2>& sd = *reinterpret_cast<const BatchInst<F2>*>(desc_raw);
+    constexpr int kWords = (int)(sizeof(BatchInst<F2>) / 4);
+    static_assert(kWords <= kTmaThreads, "one descriptor word per thread");
+    constexpr int c = batch_class(VAR, kDirichlet);
+    const int tid = threadIdx.x, G = gridDim.x;
+    if (tid == 0) mbar_init(bar);
+    __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const BatchTile* ct = tiles + table[1 + 2 * c];
+    const int count = table[2 + 2 * c];
+    const long long step = counters[0] + step_off;
+    const int lpar = (int)((counters[1] + launch_off) & 1);
+    // 0: inactive, 1: two staged steps (copy issued), 2: the budget's last step
+    auto plan_and_issue = [&](int i) -> int {
+        const BatchTile tl = ct[i];
+        const BatchInst<F2>& d = insts[tl.inst];
+        const long long st = d.start, en = d.end;
+        if (step < st || step >= en) return 0;
+        if (step + 1 >= en) return 2;
+        const int parity = lpar ^ (int)(d.l0 & 1);
+        tma_box_load(box, maps + 2 * tl.inst + parity, bar, tl.x0 - kTmaPad, tl.y0 - 2);
+        return 1;
+    };
+    if (tid == 0) *mode_sm = (int)blockIdx.x < count ? plan_and_issue(blockIdx.x) : 0;
+    __syncthreads();
+    int held = -1;
+    unsigned phase = 0;
+    for (int t = blockIdx.x; t < count; t += G) {
+        const int mode = *mode_sm;  // block-uniform
+        const BatchTile tile = ct[t];
+        if (tile.inst != held) {  // block-uniform
+            unsigned w = 0;
+            if (tid < kWords) w = __ldg(reinterpret_cast<const unsigned*>(insts + tile.inst) + tid);
+            __syncthreads();
+            if (tid < kWords) reinterpret_cast<unsigned*>(desc_raw)[tid] = w;
+            __syncthreads();
+            held = tile.inst;
+        }
+        const int parity = lpar ^ (int)(sd.l0 & 1);
+        const int nx = sd.nx, ny = sd.ny, pitch = sd.pitch;
+        const unsigned plane = static_cast<unsigned>(sd.plane);
+        float* dst = static_cast<float*>(sd.buf[1 - parity]);
+        const int x0 = tile.x0, y0 = tile.y0;
+        if (mode == 1) {
+            const bool ok = mbar_wait(bar, phase);
+            phase ^= 1u;
+            if (!__syncthreads_and(ok)) {  // the whole CTA stops together
+                if (tid == 0) {
+                    mbar_wait(bar, phase ^ 1u);  // the copy in flight, once more (bounded)
+                    atomicExch(err, 1);
+                }
+                return;
+            }
+            for (int p = tid; p < kR1Pairs * kR1H; p += kTmaThreads) {
+                const int px = p % kR1Pairs, py = p / kR1Pairs;
+                const int x = x0 - 2 + 2 * px, y = y0 - 1 + py;
+                F2 v[9];
+                pull_pair_interior<float, true>(
+                    box, kTmaPlane, kTmaW,
+                    static_cast<unsigned>((py + 1) * kTmaW + kTmaPad - 2 + 2 * px), v);
+                const bool row_in = y >= 0 && y < ny;
+                const bool keep_a = row_in && x >= 0 && x < nx;
+                const bool keep_b = row_in && x + 1 >= 0 && x + 1 < nx;
+                collide_lanes<VAR>(v, min(max(x, 0), nx - 1), min(max(x + 1, 0), nx - 1),
+                                   min(max(y, 0), ny - 1), sd.k, sd.tx, sd.ty);
+                if (!(keep_a && keep_b)) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        v[i] = f2(keep_a ? f2_lo(v[i]) : 0.0f, keep_b ? f2_hi(v[i]) : 0.0f);
+                }
+                store_pair<float>(r1, kR1Plane, static_cast<unsigned>(py * kR1W + 2 * px), v);
+            }
+        }
+        __syncthreads();  // the box is read (and *mode_sm with it)
+        if (tid == 0) *mode_sm = t + G < count ? plan_and_issue(t + G) : 0;
+        if (mode == 1) {
+            for (int p = tid; p < (kTbW / 2) * kTbH; p += kTmaThreads) {
+                const int qx = p % (kTbW / 2), qy = p / (kTbW / 2);
+                const int x = x0 + 2 * qx, y = y0 + qy;
+                if (x >= nx || y >= ny) continue;
+                F2 v[9];
+                pull_pair_interior<float, true>(
+                    r1, kR1Plane, kR1W, static_cast<unsigned>((qy + 1) * kR1W + 2 * qx + 2), v);
+                collide_pair<VAR>(v, x, y, nx, sd.k, sd.tx, sd.ty);
+                const unsigned o = static_cast<unsigned>(y * pitch + x);
+                if (x + 1 < nx)
+                    store_pair<float>(dst, plane, o, v);
+                else
+                    store_lo<float>(dst, plane, o, v);
+            }
+        } else if (mode == 2) {  // the last step of the budget: one step from global memory
+            const float* src = static_cast<const float*>(sd.buf[parity]);
+            for (int p = tid; p < (kTbW / 2) * kTbH; p += kTmaThreads) {
+                const int x = x0 + 2 * (p % (kTbW / 2)), y = y0 + p / (kTbW / 2);
+                if (x >= nx || y >= ny) continue;
+                const unsigned o = static_cast<unsigned>(y * pitch + x);
+                F2 v[9];
+                if (x > 0 && x + 2 < nx && y > 0 && y + 1 < ny)
+                    pull_pair_interior<float>(src, plane, static_cast<unsigned>(pitch), o, v);
+                else
+                    pull_pair_edge<float, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
+                collide_pair<VAR>(v, x, y, nx, sd.k, sd.tx, sd.ty);
+                if (x + 1 < nx)
+                    store_pair<float>(dst, plane, o, v);
+                else
+                    store_lo<float>(dst, plane, o, v);
+            }
+        }
+        __syncthreads();  // R1 and the descriptor are read; *mode_sm is written
+    }
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+constexpr size_t batch_tma_smem_bytes() {
+    return kTmaBoxBytes + kTmaRingBytes + 16 + sizeof(BatchInst<F2>);
+}
+
 __global__ void advance_counters_kernel(long long* counters, int steps, int launches) {
     counters[0] += steps;
     counters[1] += launches;
@@ -338,6 +475,48 @@ const void* batch_kernel_ptr<double>(int, int) {
 template <typename T>
 size_t batch_smem(int spl) {
     return spl == 2 ? tb_smem_bytes<T>() : 0;
+}
+
+// The TMA-staged two-step kernel of Dirichlet class c (FP32 batches).
+inline cudaError_t launch_tb2_tma_class(int c, cudaLaunchConfig_t cfg, const BatchInst<F2>* insts,
+                                        const CUtensorMap* maps, const BatchTile* tiles,
+                                        const int* table, const long long* counters, int step_off,
+                                        int launch_off, int* err, int grid) {
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTmaThreads);
+    cfg.dynamicSmemBytes = batch_tma_smem_bytes();
+#define LBM_TB2_TMA_CLASS(V)                                                                  \
+    if (c == batch_class(V, kDirichlet))                                                      \
+        return cudaLaunchKernelEx(&cfg, batch_tb2_tma_kernel<V>, insts, maps, tiles, table,   \
+                                  counters, step_off, launch_off, err);
+    LBM_TB2_TMA_CLASS(kNone)
+    LBM_TB2_TMA_CLASS(kTypeI)
+    LBM_TB2_TMA_CLASS(kTypeII)
+    LBM_TB2_TMA_CLASS(kTypeIII)
+    LBM_TB2_TMA_CLASS(kViscous)
+#undef LBM_TB2_TMA_CLASS
+    return cudaErrorInvalidValue;
+}
+
+// Shared-memory limits of the batched TMA kernels (outside any capture) and
+// their CTAs per SM.
+inline cudaError_t prepare_batch_tma(int* per_sm) {
+    const int bytes = static_cast<int>(batch_tma_smem_bytes());
+    cudaError_t e = cudaSuccess;
+#define LBM_TB2_TMA_ATTR(V)                                                                 \
+    if (e == cudaSuccess)                                                                   \
+        e = cudaFuncSetAttribute(batch_tb2_tma_kernel<V>,                                   \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    LBM_TB2_TMA_ATTR(kNone)
+    LBM_TB2_TMA_ATTR(kTypeI)
+    LBM_TB2_TMA_ATTR(kTypeII)
+    LBM_TB2_TMA_ATTR(kTypeIII)
+    LBM_TB2_TMA_ATTR(kViscous)
+#undef LBM_TB2_TMA_ATTR
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_tb2_tma_kernel<kTypeII>,
+                                                          kTmaThreads, batch_tma_smem_bytes());
+    return e;
 }
 
 // The two-step kernel of class c.
@@ -366,11 +545,19 @@ cudaError_t launch_tb2_class(int c, cudaLaunchConfig_t& cfg, const BatchInst<F2>
 // One batched launch: step_off / launch_off added to the device counters.
 // Two-step launches run one kernel per class in class_mask, each a
 // programmatic dependent of the one before.
+// Staging of the two-step input by TMA in a batched launch: the Dirichlet
+// classes of an FP32 batch use it when maps is set.
+struct BatchTma {
+    const CUtensorMap* maps = nullptr;
+    int* err = nullptr;
+    int grid = 0;
+};
+
 template <typename T>
 cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int* ntiles,
                            const long long* counters, int step_off, int launch_off, int tile_x,
                            int tile_y, int grid, int cells, int spl, cudaStream_t st, int pdl,
-                           int class_mask) {
+                           int class_mask, const BatchTma& tma = BatchTma{}) {
     using CT = typename Codec<T>::CT;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -387,8 +574,12 @@ cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int*
     if (spl == 2) {
         for (int c = 0; c < kClasses; ++c) {
             if (!((class_mask >> c) & 1)) continue;
+            const bool staged = std::is_same<T, float>::value && tma.maps && c < 5;
             const cudaError_t e =
-                launch_tb2_class<T>(c, cfg, ip2, tiles, ntiles, counters, step_off, launch_off);
+                staged ? launch_tb2_tma_class(c, cfg, ip2, tma.maps, tiles, ntiles, counters,
+                                              step_off, launch_off, tma.err, tma.grid)
+                       : launch_tb2_class<T>(c, cfg, ip2, tiles, ntiles, counters, step_off,
+                                             launch_off);
             if (e != cudaSuccess) return e;
             cfg.numAttrs = 1;  // the next class depends on this one
         }
@@ -404,7 +595,7 @@ template <>
 cudaError_t launch_batch_t<double>(const void* insts, const BatchTile* tiles, const int* ntiles,
                                    const long long* counters, int step_off, int launch_off,
                                    int tile_x, int tile_y, int grid, int, int, cudaStream_t st,
-                                   int pdl, int) {
+                                   int pdl, int, const BatchTma&) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(tile_x, 256 / tile_x);
@@ -484,6 +675,13 @@ struct lbm_batch_ctx {
     int h_ntiles[1 + 2 * lbm::kClasses] = {};  // host image of d_ntiles (256 bytes allocated)
     int class_mask = 0;  // classes with tiles
     int graph_mask = 0;  // classes the captured graph launches
+    // TMA staging of the two-step input (FP32 batches, Dirichlet instances)
+    bool tma = false;
+    int tma_grid = 0;
+    CUtensorMap* d_maps = nullptr;  // 2 per dense instance
+    size_t maps_cap = 0;            // entries
+    std::vector<CUtensorMap> h_maps;
+    int* d_tma_err = nullptr;
     // buffers of removed instances, freed once the launches issued before the
     // removal have completed (their event), so that removal never waits
     struct Retired {
@@ -623,9 +821,10 @@ cudaError_t launch_batch(lbm_batch_ctx* b, cudaStream_t st, int steps, int step_
                                                step_off, launch_off, tx, ty, b->grid, 1, 1, st,
                                                pdl, b->class_mask);
         case LBM_F32:
-            return lbm::launch_batch_t<float>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
-                                              step_off, launch_off, tx, ty, b->grid, b->cpt, spl,
-                                              st, pdl, b->class_mask);
+            return lbm::launch_batch_t<float>(
+                b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters, step_off, launch_off, tx, ty,
+                b->grid, b->cpt, spl, st, pdl, b->class_mask,
+                lbm::BatchTma{b->tma ? b->d_maps : nullptr, b->d_tma_err, b->tma_grid});
         case LBM_F16DEV:
             return lbm::launch_batch_t<__half>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
                                                step_off, launch_off, tx, ty, b->grid, b->cpt, spl,
@@ -711,6 +910,17 @@ int sync_tables(lbm_batch_ctx* b) {
         for (int y0 = 0; y0 < in.ny; y0 += ty)
             for (int x0 = 0; x0 < in.nx; x0 += tx) out.push_back(BatchTile{di, x0, y0, 0});
     }
+    // tensor maps of both buffers of every Dirichlet instance (FP32 two-step batches)
+    if (b->tma && b->spl == 2) {
+        b->h_maps.assign(2 * b->dense.size(), CUtensorMap{});
+        for (size_t di = 0; di < b->dense.size(); ++di) {
+            const Instance& in = b->insts.at(b->dense[di]);
+            if (in.bc != LBM_BC_DIRICHLET_EQ) continue;
+            for (int p = 0; p < 2; ++p)
+                if (!lbm::encode_tma_map_f32(&b->h_maps[2 * di + p], in.buf[p], in.geo))
+                    return bfail(b, LBM_ERR_CUDA, "the driver did not encode a tensor map");
+        }
+    }
     // the tiles of each class together (the two-step launch runs a kernel per class)
     int mask = 0;
     for (int c = 0; c < lbm::kClasses; ++c) {
@@ -738,9 +948,20 @@ int sync_tables(lbm_batch_ctx* b) {
         if (!b->d_tiles) return bfail(b, LBM_ERR_OOM, "tile table allocation failed");
         realloc = true;
     }
+    if (b->tma && b->spl == 2 && b->h_maps.size() > b->maps_cap) {
+        cudaStreamSynchronize(b->stream);
+        bd_free(b, b->d_maps, b->maps_cap * sizeof(CUtensorMap));
+        b->maps_cap = std::max(b->h_maps.size(), 2 * b->maps_cap);
+        b->d_maps = static_cast<CUtensorMap*>(bd_alloc(b, b->maps_cap * sizeof(CUtensorMap)));
+        if (!b->d_maps) return bfail(b, LBM_ERR_OOM, "tensor map table allocation failed");
+        realloc = true;
+    }
     if (realloc) drop_batch_graph(b);
     cudaError_t e = cudaSuccess;
-    if (!descs.empty())
+    if (b->tma && b->spl == 2 && !b->h_maps.empty())
+        e = cudaMemcpyAsync(b->d_maps, b->h_maps.data(), b->h_maps.size() * sizeof(CUtensorMap),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !descs.empty())
         e = cudaMemcpyAsync(b->d_insts, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && !tiles.empty())
         e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile),
@@ -779,6 +1000,16 @@ cudaError_t ensure_batch_graph(lbm_batch_ctx* b) {
     if (g) cudaGraphDestroy(g);
     if (e == cudaSuccess) b->graph_mask = b->class_mask;
     return e;
+}
+
+// After the stream is synchronised: LBM_ERR_CUDA if a staged copy timed out.
+int check_batch_tma(lbm_batch_ctx* b) {
+    if (!b->d_tma_err) return LBM_OK;
+    int flag = 0;
+    const cudaError_t e = cudaMemcpy(&flag, b->d_tma_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("TMA error flag: ") + cudaGetErrorString(e));
+    if (flag) return bfail(b, LBM_ERR_CUDA, "a TMA-staged copy did not complete within its wait");
+    return LBM_OK;
 }
 
 Instance* find(lbm_batch_ctx* b, int id) {
@@ -859,6 +1090,22 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
         int tx = 0, ty = 0;
         if (std::sscanf(t, "%dx%d", &tx, &ty) == 2) lbm_batch_set_tiling(b, tx, ty);
     }
+    // FP32 batches stage the two-step input of their Dirichlet instances by TMA
+    // (LBM_BATCH_TMA=0 keeps plain loads)
+    const char* tma_env = std::getenv("LBM_BATCH_TMA");
+    if (storage == LBM_F32 && !(tma_env && !std::strcmp(tma_env, "0"))) {
+        int per_sm = 0, sms = 0;
+        e = lbm::prepare_batch_tma(&per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        b->d_tma_err = static_cast<int*>(bd_alloc(b, 256));
+        if (e == cudaSuccess && per_sm > 0 && b->d_tma_err &&
+            cudaMemsetAsync(b->d_tma_err, 0, sizeof(int), b->stream) == cudaSuccess &&
+            cudaStreamSynchronize(b->stream) == cudaSuccess) {
+            b->tma = true;
+            b->tma_grid = per_sm * sms;
+        }
+        cudaGetLastError();
+    }
     *out = b;
     return LBM_OK;
 }
@@ -912,6 +1159,8 @@ int lbm_batch_set_steps_per_launch(lbm_batch b, int steps) {
 }
 
 int lbm_batch_steps_per_launch(lbm_batch b) { return b ? b->spl : LBM_ERR_ARG; }
+
+int lbm_batch_tma_staging(lbm_batch b) { return b ? (b->tma ? 1 : 0) : LBM_ERR_ARG; }
 
 int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double uy0,
                   const lbm_rates* rates, lbm_bc bc, lbm_variant variant, const double* chi_x,
@@ -1137,7 +1386,7 @@ int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* 
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     }
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_moments: ") + cudaGetErrorString(e));
-    return LBM_OK;
+    return on_device ? LBM_OK : check_batch_tma(b);
 }
 
 int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, double out[6]) {
@@ -1156,6 +1405,7 @@ int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, d
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, lbm::kDiag * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_diagnostics: ") + cudaGetErrorString(e));
+    if (const int rc = check_batch_tma(b)) return rc;
     if (out[5] > 0) return bfail(b, LBM_ERR_NONFINITE, "the instance holds non-finite values");
     return LBM_OK;
 }
@@ -1209,6 +1459,8 @@ void lbm_batch_destroy(lbm_batch b) {
     bd_free(b, b->d_insts, b->insts_cap);
     bd_free(b, b->d_tiles, b->tiles_cap * sizeof(BatchTile));
     bd_free(b, b->d_ntiles, 256);
+    bd_free(b, b->d_maps, b->maps_cap * sizeof(CUtensorMap));
+    bd_free(b, b->d_tma_err, 256);
     bd_free(b, b->d_counters, 256);
     bd_free(b, b->d_diag, sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag));
     bd_free(b, b->staging, b->staging_bytes);

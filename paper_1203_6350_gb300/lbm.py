@@ -101,6 +101,7 @@ SIGNATURES = [
     ("lbm_batch_cells_per_thread", ctypes.c_int, [_vp]),
     ("lbm_batch_set_steps_per_launch", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_batch_steps_per_launch", ctypes.c_int, [_vp]),
+    ("lbm_batch_tma_staging", ctypes.c_int, [_vp]),
     ("lbm_batch_add", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(lbm_rates),
                                      ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double,
@@ -373,6 +374,10 @@ def lbm_batch_set_steps_per_launch(b, steps) -> int:
 
 def lbm_batch_steps_per_launch(b) -> int:
     return load().lbm_batch_steps_per_launch(b)
+
+
+def lbm_batch_tma_staging(b) -> int:
+    return load().lbm_batch_tma_staging(b)
 
 
 def lbm_batch_add(b, nx, ny, rho0, ux0, uy0, rates: lbm_rates, bc, variant, chi_x_ptr,

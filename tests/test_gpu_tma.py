@@ -119,3 +119,32 @@ def test_tma_staging_is_the_default_at_4096_and_matches_plain_loads():
             lat.step(w.steps)
             states.append(lat.get_state()[0])
     np.testing.assert_array_equal(states[0], states[1])
+
+
+def test_tma_staging_in_batches_is_bit_identical(monkeypatch):
+    """A batch of mixed lattices (Dirichlet and periodic, every variant, odd
+    budgets that end on a one-step launch, 131 steps) with two steps per launch:
+    TMA-staged input for the Dirichlet instances (the FP32 default) against
+    plain loads, bit for bit."""
+    from test_gpu_batch import _mixed_workloads
+
+    from paper_1203_6350_gb300 import lbm
+    from paper_1203_6350_gb300.batch import Batch
+
+    works = _mixed_workloads("f32")
+    out = []
+    for env in (None, "0"):
+        if env is None:
+            monkeypatch.delenv("LBM_BATCH_TMA", raising=False)
+        else:
+            monkeypatch.setenv("LBM_BATCH_TMA", env)
+        with Batch("f32") as b:
+            assert lbm.lbm_batch_tma_staging(b.b) == (1 if env is None else 0)
+            b.cells_per_thread = 2
+            b.steps_per_launch = 2
+            ids = [b.add_workload(w) for w in works]
+            b.step(131)
+            out.append([b.moments(i) for i in ids])
+    for a, c in zip(*out):
+        for x, y in zip(a, c):
+            np.testing.assert_array_equal(x, y)
