@@ -117,6 +117,26 @@ def cpu_baseline(works, budget_s: float = 15.0):
     }
 
 
+def oracle_timings():
+    """The FP64 oracle on one thread and on every core: the 100^2 pulse
+    (300 steps, timed in full) and the 2048^2 pulse with its 128-cell layer
+    (10 steps timed, the 200-step run extrapolated from them)."""
+    from oracle import core
+
+    core.build()
+    cores = core.omp_threads()
+    out = []
+    for w, steps, full in ((wl.small_pulse("II", "f64"), 300, 300),
+                           (wl.quiescent(2048, storage="f64", steps=200, pulse=True), 10, 200)):
+        for threads in (1, cores):
+            cells, t = time_oracle([w], steps, threads)
+            out.append({"case": f"{w.nx}x{w.ny} type II", "threads": threads,
+                        "steps_timed": steps, "seconds": t, "mlups": cells / t / 1e6,
+                        f"seconds_for_{full}_steps": t * full / steps,
+                        "extrapolated": steps != full})
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
@@ -242,6 +262,7 @@ def run_native(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(works)
+        cpu["timings"] = oracle_timings()
 
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
