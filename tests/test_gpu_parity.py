@@ -310,10 +310,11 @@ def test_roofline_sweep_2048_error(storage):
 
 
 @pytest.mark.parametrize("side,storage", [(16384, "f32"), (8192, "f16dev"), (4096, "bf16dev"),
-                                          (2048, "f32")])
+                                          (4096, "f32"), (2048, "f32")])
 def test_full_size_sweep_lattice_window_against_the_oracle(side, storage):
     """Roofline-sweep lattices at full size, in the launch configuration the
-    library picks for them (two steps per launch, as the sweep times them):
+    library picks for them (two steps per launch, TMA staging for FP32 from
+    4096^2 up, as the sweep times them):
     the centred eps = 1e-3, b = 5 pulse after 60 steps, compared in the central
     200 x 200 window with the oracle on a 400 x 400 lattice holding the same
     pulse at its centre.  A signal moves at most one cell per step, so after 60
@@ -327,6 +328,8 @@ def test_full_size_sweep_lattice_window_against_the_oracle(side, storage):
     big = wl.quiescent(side, storage=storage, steps=steps, width=128, pulse=True)
     with lbm.Lattice.from_workload(big, init="pulse") as lat:
         assert lat.steps_per_launch == (2 if side >= 2048 else 1)
+        # FP32 from 4096^2 up: each tile's input staged by TMA
+        assert lat.tma_staging == (storage == "f32" and side >= 4096)
         lat.step(steps)
         fields = lat.moments(device=True)
         c = side // 2
