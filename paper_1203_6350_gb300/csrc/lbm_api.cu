@@ -44,6 +44,8 @@ struct lbm_ctx {
     int spl = 1;                      // time steps per launch: 1, or 2 (needs cpt == 2)
     lbm::LineSource src{};            // channel boundary: the line source (amp 0 until lbm_set_source)
     long long* d_time = nullptr;      // channel boundary: device copy of the step counter
+    double* d_src_table = nullptr;    // channel boundary: source scales of the next kGraphChunk steps,
+                                      // then their FP32 source populations (9 per step)
     bool initialised = false;
     int64_t time = 0;
     int launch_mode = 2;              // kLaunchGraph; LBM_LAUNCH=plain|pdl|graph overrides
@@ -157,10 +159,14 @@ bool is_finite(double v) { return std::isfinite(v); }
 
 // The line source as a step launch sees it: the device step counter plus
 // t_off launches issued since it was last advanced.
+// The line source as the step kernels see it: the scale of step t_off of the
+// current chunk, from the table source_table_kernel filled at its start.
 lbm::LineSource launch_source(const lbm_ctx* h, long long t_off) {
     lbm::LineSource ls = h->src;
     ls.time = h->d_time;
     ls.t_off = t_off;
+    ls.table = h->d_src_table;
+    ls.pop = h->d_src_table ? reinterpret_cast<const float*>(h->d_src_table + kGraphChunk) : nullptr;
     return ls;
 }
 
@@ -169,10 +175,37 @@ lbm::LineSource readout_source(const lbm_ctx* h) {
     lbm::LineSource ls = h->src;
     ls.time = nullptr;
     ls.t_off = h->time;
+    ls.table = nullptr;
+    ls.pop = nullptr;
     return ls;
 }
 
 __global__ void advance_time_kernel(long long* t, int by) { *t += by; }
+
+// table[k] = the source scale of step k of the chunk starting at the device
+// clock, k < n, and pop[9 k + i] = float(table[k] e_i) its FP32 source
+// populations: the FP64 sine and products evaluated once per step here
+// instead of in the edge threads of every step kernel (on the critical path
+// of each launch).
+__global__ void source_table_kernel(const long long* time, double* table, float* pop, int n,
+                                    lbm::LineSource ls) {
+    const int k = threadIdx.x;
+    if (k >= n) return;
+    ls.time = time;
+    ls.t_off = k;
+    ls.table = nullptr;
+    const double scale = lbm::line_source_scale(ls);
+    table[k] = scale;
+    for (int i = 0; i < 9; ++i) pop[9 * k + i] = static_cast<float>(scale * ls.e[i]);
+}
+
+// Fill the table for the next n <= kGraphChunk steps (channel boundary only).
+cudaError_t launch_source_table(lbm_ctx* h, cudaStream_t st, int n) {
+    source_table_kernel<<<1, kGraphChunk, 0, st>>>(
+        h->d_time, h->d_src_table, reinterpret_cast<float*>(h->d_src_table + kGraphChunk), n,
+        h->src);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_one_step(lbm_ctx* h, const void* src, void* dst, cudaStream_t st, bool pdl,
                             long long t_off = 0) {
@@ -275,6 +308,7 @@ cudaError_t ensure_graph(lbm_ctx* h, int parity) {
     }
     e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
+    if (h->bc == LBM_BC_CHANNEL) e = launch_source_table(h, h->capture_stream, kGraphChunk);
     int c = parity;
     for (int t = 0; t < kGraphChunk && e == cudaSuccess; t += h->spl) {
         if (h->spl == 2)
@@ -371,7 +405,11 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     h->chi_y = dev_alloc(h, h->chi_bytes_y);
     h->diag = static_cast<double*>(dev_alloc(h, h->diag_bytes));
     h->d_time = static_cast<long long*>(dev_alloc(h, 256));
-    if (!h->buf[0] || !h->buf[1] || !h->chi_x || !h->chi_y || !h->diag || !h->d_time) {
+    if (bc == LBM_BC_CHANNEL)
+        h->d_src_table = static_cast<double*>(
+            dev_alloc(h, kGraphChunk * (sizeof(double) + 9 * sizeof(float))));
+    if (!h->buf[0] || !h->buf[1] || !h->chi_x || !h->chi_y || !h->diag || !h->d_time ||
+        (bc == LBM_BC_CHANNEL && !h->d_src_table)) {
         lbm_destroy(h);
         return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
     }
@@ -565,21 +603,31 @@ int lbm_step(lbm_handle h, int nsteps) {
             }
         }
     }
-    int issued = 0;
+    // the channel issues at most kGraphChunk launches per source table
     while (nsteps > 0) {
-        const int n = (h->spl == 2 && nsteps >= 2) ? 2 : 1;
-        e = n == 2 ? launch_two_steps(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl)
-                   : launch_one_step(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl, issued);
-        if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step launch");
-        h->cur = 1 - h->cur;
-        h->time += n;
-        nsteps -= n;
-        issued += n;
-    }
-    if (issued > 0 && h->bc == LBM_BC_CHANNEL) {  // the line source's clock
-        advance_time_kernel<<<1, 1, 0, h->stream>>>(h->d_time, issued);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step clock");
+        const bool channel = h->bc == LBM_BC_CHANNEL;
+        const int chunk = channel && nsteps > kGraphChunk ? kGraphChunk : nsteps;
+        if (channel) {
+            e = launch_source_table(h, h->stream, chunk);
+            if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step source table");
+        }
+        int issued = 0;
+        while (issued < chunk) {
+            const int n = (h->spl == 2 && chunk - issued >= 2) ? 2 : 1;
+            e = n == 2 ? launch_two_steps(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl)
+                       : launch_one_step(h, h->buf[h->cur], h->buf[1 - h->cur], h->stream, pdl,
+                                         issued);
+            if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step launch");
+            h->cur = 1 - h->cur;
+            h->time += n;
+            issued += n;
+        }
+        nsteps -= chunk;
+        if (channel) {  // the line source's clock
+            advance_time_kernel<<<1, 1, 0, h->stream>>>(h->d_time, issued);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step clock");
+        }
     }
     return LBM_OK;
 }
@@ -752,6 +800,7 @@ void lbm_destroy(lbm_handle h) {
     dev_free(h, h->chi_y, h->chi_bytes_y);
     dev_free(h, h->diag, h->diag_bytes);
     dev_free(h, h->d_time, 256);
+    dev_free(h, h->d_src_table, kGraphChunk * (sizeof(double) + 9 * sizeof(float)));
     dev_free(h, h->tma_err, 256);
     dev_free(h, h->staging, h->staging_bytes);
     delete h;

@@ -173,11 +173,14 @@ struct LineSource {
     long long t_off;
     double amp, omega, phase;
     double e[9];
+    const double* table;    // device: scales of the steps time .. time + n - 1 (or nullptr)
+    const float* pop;       // device: float(scale * e_i) of those steps, 9 per step (or nullptr)
 };
 
 // Source deviation scale of the state that a pull with source `s` yields.
 __host__ __device__ inline double line_source_scale(const LineSource& s) {
 #ifdef __CUDA_ARCH__
+    if (s.table) return s.table[s.t_off];  // filled by source_table_kernel for this chunk
     const long long tau = (s.time ? *s.time : 0) + s.t_off;
 #else
     const long long tau = s.t_off;

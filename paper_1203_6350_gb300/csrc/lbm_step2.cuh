@@ -122,14 +122,14 @@ __device__ __forceinline__ void pull_pair_interior(const T* __restrict__ s, unsi
 
 // Population I of cell (c, y) pulled from (c - c_ix, y - c_iy) with the
 // boundary rule: a Dirichlet far-field wall contributes a zero deviation,
-// periodic wraps, the channel wraps y, takes the source src_s * src_e[I] at
+// periodic wraps, the channel wraps y, takes the source population src_pop[I] at
 // its left edge and the last column's own value at its right edge (outflow).
 // The phantom cell c = nx of an odd-width lattice reads nothing (its result
 // is never stored).
 template <typename T, int BC, int I>
 __device__ __forceinline__ float pull_one(const T* __restrict__ s, unsigned plane, int pitch,
-                                          int c, int y, int nx, int ny, double src_s = 0.0,
-                                          const double* src_e = nullptr) {
+                                          int c, int y, int nx, int ny,
+                                          const float* src_pop = nullptr) {
     if (c >= nx) return 0.0f;
     int sx = c - cx(I), sy = y - cy(I);
     if (BC == kPeriodic) {
@@ -137,7 +137,7 @@ __device__ __forceinline__ float pull_one(const T* __restrict__ s, unsigned plan
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
     } else if (BC == kChannel) {
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        if (sx < 0) return static_cast<float>(src_s * src_e[I]);
+        if (sx < 0) return src_pop[I];
         if (sx >= nx) sx = nx - 1;
     } else if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
         return 0.0f;
@@ -147,25 +147,24 @@ __device__ __forceinline__ float pull_one(const T* __restrict__ s, unsigned plan
 
 template <typename T, int BC, int I>
 __device__ __forceinline__ F2 pull_pair_one(const T* __restrict__ s, unsigned plane, int pitch,
-                                            int x, int y, int nx, int ny, double src_s,
-                                            const double* src_e) {
-    return f2(pull_one<T, BC, I>(s, plane, pitch, x, y, nx, ny, src_s, src_e),
-              pull_one<T, BC, I>(s, plane, pitch, x + 1, y, nx, ny, src_s, src_e));
+                                            int x, int y, int nx, int ny, const float* src_pop) {
+    return f2(pull_one<T, BC, I>(s, plane, pitch, x, y, nx, ny, src_pop),
+              pull_one<T, BC, I>(s, plane, pitch, x + 1, y, nx, ny, src_pop));
 }
 
 template <typename T, int BC>
 __device__ __forceinline__ void pull_pair_edge(const T* __restrict__ s, unsigned plane, int pitch,
                                                int x, int y, int nx, int ny, F2 (&v)[9],
-                                               double src_s = 0.0, const double* src_e = nullptr) {
-    v[0] = pull_pair_one<T, BC, 0>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[1] = pull_pair_one<T, BC, 1>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[2] = pull_pair_one<T, BC, 2>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[3] = pull_pair_one<T, BC, 3>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[4] = pull_pair_one<T, BC, 4>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[5] = pull_pair_one<T, BC, 5>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[6] = pull_pair_one<T, BC, 6>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[7] = pull_pair_one<T, BC, 7>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
-    v[8] = pull_pair_one<T, BC, 8>(s, plane, pitch, x, y, nx, ny, src_s, src_e);
+                                               const float* src_pop = nullptr) {
+    v[0] = pull_pair_one<T, BC, 0>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[1] = pull_pair_one<T, BC, 1>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[2] = pull_pair_one<T, BC, 2>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[3] = pull_pair_one<T, BC, 3>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[4] = pull_pair_one<T, BC, 4>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[5] = pull_pair_one<T, BC, 5>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[6] = pull_pair_one<T, BC, 6>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[7] = pull_pair_one<T, BC, 7>(s, plane, pitch, x, y, nx, ny, src_pop);
+    v[8] = pull_pair_one<T, BC, 8>(s, plane, pitch, x, y, nx, ny, src_pop);
 }
 
 template <typename T, int I>
@@ -264,8 +263,8 @@ __global__ void __launch_bounds__(kPairBX* kPairBY)
         pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch), o, v);
     } else {
         // the channel's source edge: its deviation scale at this step
-        const double src_s = (BC == kChannel && x == 0) ? line_source_scale(ls) : 0.0;
-        pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v, src_s, ls.e);
+        const float* src_pop = (BC == kChannel && x == 0) ? ls.pop + 9 * ls.t_off : nullptr;
+        pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v, src_pop);
     }
     collide_pair<VAR>(v, x, y, nx, k, tx, ty);
     if (x + 1 < nx)
