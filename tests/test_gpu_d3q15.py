@@ -8,8 +8,9 @@
   absolute floor) or 1e-5 (FP32) of the state's norm.
 - The 3-D pulse with a ramped layer on every face: FP32 and FP64 against the
   oracle over 60 steps.
-- At the benchmark's size (256^3 FP32): the centred pulse keeps the cube's
-  symmetries, and a periodic lattice without damping conserves mass.
+- At the benchmark's size (256^3 FP32): the central window against the
+  oracle on a smaller box, the cube's symmetries of the centred pulse, and
+  mass conservation on a periodic lattice without damping.
 """
 import math
 
@@ -138,6 +139,28 @@ def test_benchmark_size_symmetry_and_conservation():
         m1 = lat.moments()[0].sum(dtype=np.float64)
     # FP32 deviations ~ 1e-3 in 16.8M cells: rounding of order 1e-10 each
     assert abs(m1 - m0) <= 1e-4 * abs(m0), (m0, m1)
+
+
+def test_benchmark_size_window_against_the_oracle():
+    """The benchmark's 256^3 FP32 pulse (16-cell type II layer), 30 steps, in
+    the central 32^3 window against the oracle on a 96^3 box holding the same
+    pulse at its centre, no layer.  A signal moves at most one cell per step,
+    so after 30 steps the window depends only on cells within 46 of the
+    centre: inside the big lattice's chi = 0 core and 32 cells from the small
+    box's edge, with the same initial data on both."""
+    from oracle import d3q15 as d3
+
+    steps, half, win = 30, 48, 16
+    big = wl.pulse3d(256, steps=steps)
+    got = _gpu(big, "f32", steps)
+    c = 128
+    got = [g[c - win:c + win, c - win:c + win, c - win:c + win] for g in got]
+    small = wl.pulse3d(2 * half, steps=steps, width=0, chi_max=0.0)
+    prob = d3.Problem(small.nx, small.ny, small.nz, small.s, variant="none")
+    ref = d3.State(prob, 1.0 + small.rho_dev, [0.0, 0.0, 0.0]).run(steps).moments()
+    ref = [r[half - win:half + win, half - win:half + win, half - win:half + win] for r in ref]
+    # the same pulse: centred at (n - 1)/2 on both lattices, so the windows align
+    _close_state(got, ref, (0.0, 0.0, 0.0), TOL["f32"], steps, "window")
 
 
 def test_d3q15_api_rules():
