@@ -495,6 +495,20 @@ int lbm3_init_equilibrium(lbm3_handle h, const double* rho, const double* ux, co
 int lbm3_step(lbm3_handle h, int nsteps);
 /* rho - rho0 and u of the current (streamed, pre-collision) state. */
 int lbm3_moments(lbm3_handle h, double* rho_dev, double* ux, double* uy, double* uz);
+/* FP64 sums over the cells x0 <= ix < x1, y0 <= iy < y1, z0 <= iz < z1 of the
+ * current (streamed) state, in a fixed order (deterministic):
+ *   out[0] sum rho'   out[1..3] sum (j - rho0 u0)
+ *   out[4] acoustic energy sum [c_s^2 rho'^2 / (2 rho0) + rho0 |u - u0|^2 / 2]
+ *   out[5] sum rho'^2   out[6] cells holding a non-finite value.
+ * Synchronises the stream.  LBM_ERR_NONFINITE when out[6] > 0 (out filled). */
+int lbm3_diagnostics(lbm3_handle h, int x0, int y0, int z0, int x1, int y1, int z1,
+                     double out[7]);
+/* Checkpoint: the current state buffer (lbm3_state_bytes of them, the layout
+ * above) copied to or from HOST memory with its time; synchronises the
+ * stream.  lbm3_set_state makes the handle ready to step. */
+size_t lbm3_state_bytes(lbm3_handle h);
+int lbm3_get_state(lbm3_handle h, void* dst, size_t bytes, int64_t* time);
+int lbm3_set_state(lbm3_handle h, const void* src, size_t bytes, int64_t time);
 int64_t lbm3_time(lbm3_handle h);
 void lbm3_destroy(lbm3_handle h);
 /* Message of the handle's last failing call (NULL handle: the calling thread's

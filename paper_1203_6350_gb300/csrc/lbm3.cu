@@ -316,17 +316,11 @@ __global__ void d3_init_kernel(T* __restrict__ dst, D3Geom g, double rho0, doubl
     }
 }
 
-// rho' and u of the pulled (pre-collision) state, FP64 [nz][ny][nx].
+// Deviations (rho', j - rho0 u0) of the pulled (pre-collision) state at a cell.
 template <typename T>
-__global__ void d3_moments_kernel(const T* __restrict__ src, D3Geom g, double rho0, double ux0,
-                                  double uy0, double uz0, int bc, double* __restrict__ rho,
-                                  double* __restrict__ ux, double* __restrict__ uy,
-                                  double* __restrict__ uz) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    const int z = blockIdx.z;
-    if (x >= g.nx) return;
-    double m[4] = {0, 0, 0, 0};
+__device__ __forceinline__ void d3_pulled_moments(const T* __restrict__ src, const D3Geom& g,
+                                                  int bc, int x, int y, int z, double (&m)[4]) {
+    m[0] = m[1] = m[2] = m[3] = 0.0;
     for (int i = 0; i < kQ; ++i) {
         int sx = x - d3cx(i), sy = y - d3cy(i), sz = z - d3cz(i);
         double v = 0.0;
@@ -343,6 +337,20 @@ __global__ void d3_moments_kernel(const T* __restrict__ src, D3Geom g, double rh
         m[2] += d3cy(i) * v;
         m[3] += d3cz(i) * v;
     }
+}
+
+// rho' and u of the pulled (pre-collision) state, FP64 [nz][ny][nx].
+template <typename T>
+__global__ void d3_moments_kernel(const T* __restrict__ src, D3Geom g, double rho0, double ux0,
+                                  double uy0, double uz0, int bc, double* __restrict__ rho,
+                                  double* __restrict__ ux, double* __restrict__ uy,
+                                  double* __restrict__ uz) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx) return;
+    double m[4];
+    d3_pulled_moments(src, g, bc, x, y, z, m);
     // deviations of rho and j from the base f^eq(rho0, u0), whose moments are rho0, rho0 u0
     const double r = rho0 + m[0];
     const size_t c = (static_cast<size_t>(z) * g.ny + y) * g.nx + x;
@@ -350,6 +358,84 @@ __global__ void d3_moments_kernel(const T* __restrict__ src, D3Geom g, double rh
     ux[c] = (rho0 * ux0 + m[1]) / r;
     uy[c] = (rho0 * uy0 + m[2]) / r;
     uz[c] = (rho0 * uz0 + m[3]) / r;
+}
+
+constexpr int kD3Diag = 7;           // sums of lbm3_diagnostics
+constexpr int kD3DiagThreads = 256;
+constexpr int kD3DiagBlocks = 608;   // fixed, so that the summation order is fixed
+
+__device__ __forceinline__ double d3_warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// First pass: thread t of block b takes the region's cells b * 256 + t,
+// + 608 * 256, ... in x-fastest order and writes the block's kD3Diag sums to
+// partial[b].
+template <typename T>
+__global__ void __launch_bounds__(kD3DiagThreads)
+    d3_diag_partial_kernel(const T* __restrict__ src, D3Geom g, int bc, double rho0, double ux0,
+                           double uy0, double uz0, int x0, int y0, int z0, int wx, int wy,
+                           long long ncell, double* __restrict__ partial) {
+    double acc[kD3Diag] = {0, 0, 0, 0, 0, 0, 0};
+    const double u0[3] = {ux0, uy0, uz0};
+    for (long long c = static_cast<long long>(blockIdx.x) * kD3DiagThreads + threadIdx.x;
+         c < ncell; c += static_cast<long long>(gridDim.x) * kD3DiagThreads) {
+        const int x = x0 + static_cast<int>(c % wx);
+        const int y = y0 + static_cast<int>((c / wx) % wy);
+        const int z = z0 + static_cast<int>(c / (static_cast<long long>(wx) * wy));
+        double m[4];
+        d3_pulled_moments(src, g, bc, x, y, z, m);
+        // u - u0 = (j' - rho' u0) / rho
+        const double inv = 1.0 / (rho0 + m[0]);
+        double du2 = 0.0;
+        bool finite = isfinite(m[0]);
+        for (int a = 0; a < 3; ++a) {
+            const double du = (m[1 + a] - m[0] * u0[a]) * inv;
+            du2 += du * du;
+            finite = finite && isfinite(du);
+        }
+        acc[0] += m[0];
+        acc[1] += m[1];
+        acc[2] += m[2];
+        acc[3] += m[3];
+        acc[4] += m[0] * m[0] / (6.0 * rho0) + 0.5 * rho0 * du2;  // c_s^2 = 1/3
+        acc[5] += m[0] * m[0];
+        acc[6] += finite ? 0.0 : 1.0;
+    }
+    __shared__ double red[kD3Diag][kD3DiagThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < kD3Diag; ++q) {
+        const double v = d3_warp_sum(acc[q]);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kD3Diag) {
+        double s = 0.0;
+        for (int k = 0; k < kD3DiagThreads / 32; ++k) s += red[threadIdx.x][k];
+        partial[blockIdx.x * kD3Diag + threadIdx.x] = s;
+    }
+}
+
+// Second pass: one block adds the partials in a fixed order.
+__global__ void __launch_bounds__(kD3DiagThreads)
+    d3_diag_final_kernel(const double* __restrict__ partial, double* __restrict__ out) {
+    __shared__ double red[kD3Diag][kD3DiagThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < kD3Diag; ++q) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < kD3DiagBlocks; k += kD3DiagThreads)
+            s += partial[k * kD3Diag + q];
+        s = d3_warp_sum(s);
+        if (lane == 0) red[q][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < kD3Diag) {
+        double s = 0.0;
+        for (int k = 0; k < kD3DiagThreads / 32; ++k) s += red[threadIdx.x][k];
+        out[threadIdx.x] = s;
+    }
 }
 
 }  // namespace
@@ -664,6 +750,81 @@ int lbm3_moments(lbm3_handle h, double* rho_dev, double* ux, double* uy, double*
     const cudaError_t e2 = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess || e2 != cudaSuccess)
         return fail3(h, LBM_ERR_CUDA, cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return LBM_OK;
+}
+
+int lbm3_diagnostics(lbm3_handle h, int x0, int y0, int z0, int x1, int y1, int z1,
+                     double out[7]) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (!out) return fail3(h, LBM_ERR_ARG, "NULL out");
+    if (!h->ready) return fail3(h, LBM_ERR_STATE, "diagnostics before lbm3_init_equilibrium");
+    if (x0 < 0 || y0 < 0 || z0 < 0 || x1 > h->nx || y1 > h->ny || z1 > h->nz || x0 > x1 ||
+        y0 > y1 || z0 > z1)
+        return fail3(h, LBM_ERR_ARG, "region outside the lattice");
+    const long long ncell = static_cast<long long>(x1 - x0) * (y1 - y0) * (z1 - z0);
+    double* d = nullptr;
+    const size_t bytes = (kD3DiagBlocks + 1) * kD3Diag * sizeof(double);
+    if (cudaMallocAsync(&d, bytes, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail3(h, LBM_ERR_OOM, "device allocation failed");
+    }
+    double* res = d + kD3DiagBlocks * kD3Diag;
+    cudaError_t e = cudaSuccess;
+    if (ncell == 0) {
+        e = cudaMemsetAsync(res, 0, kD3Diag * sizeof(double), h->stream);
+    } else {
+        const int wx = x1 - x0, wy = y1 - y0;
+        if (h->storage == LBM_F64)
+            d3_diag_partial_kernel<double><<<kD3DiagBlocks, kD3DiagThreads, 0, h->stream>>>(
+                static_cast<const double*>(h->buf[h->cur]), h->g, h->bc, h->rho0, h->u0[0],
+                h->u0[1], h->u0[2], x0, y0, z0, wx, wy, ncell, d);
+        else
+            d3_diag_partial_kernel<float><<<kD3DiagBlocks, kD3DiagThreads, 0, h->stream>>>(
+                static_cast<const float*>(h->buf[h->cur]), h->g, h->bc, h->rho0, h->u0[0],
+                h->u0[1], h->u0[2], x0, y0, z0, wx, wy, ncell, d);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            d3_diag_final_kernel<<<1, kD3DiagThreads, 0, h->stream>>>(d, res);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, res, kD3Diag * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail3(h, LBM_ERR_CUDA, cudaGetErrorString(e != cudaSuccess ? e : e2));
+    if (out[6] > 0) return fail3(h, LBM_ERR_NONFINITE, "the state holds non-finite values");
+    return LBM_OK;
+}
+
+size_t lbm3_state_bytes(lbm3_handle h) {
+    return h ? static_cast<size_t>(h->g.plane) * kQ * elem_size(h->storage) : 0;
+}
+
+int lbm3_get_state(lbm3_handle h, void* dst, size_t bytes, int64_t* time) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (!dst || bytes != lbm3_state_bytes(h))
+        return fail3(h, LBM_ERR_ARG, "dst / bytes do not match lbm3_state_bytes");
+    if (!h->ready) return fail3(h, LBM_ERR_STATE, "no state before lbm3_init_equilibrium");
+    cudaError_t e = cudaMemcpyAsync(dst, h->buf[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail3(h, LBM_ERR_CUDA, cudaGetErrorString(e));
+    if (time) *time = h->time;
+    return LBM_OK;
+}
+
+int lbm3_set_state(lbm3_handle h, const void* src, size_t bytes, int64_t time) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (!src || bytes != lbm3_state_bytes(h))
+        return fail3(h, LBM_ERR_ARG, "src / bytes do not match lbm3_state_bytes");
+    if (time < 0) return fail3(h, LBM_ERR_ARG, "time < 0");
+    cudaError_t e = cudaMemcpyAsync(h->buf[0], src, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail3(h, LBM_ERR_CUDA, cudaGetErrorString(e));
+    h->cur = 0;
+    h->time = time;
+    h->ready = true;
     return LBM_OK;
 }
 

@@ -133,6 +133,10 @@ SIGNATURES = [
     ("lbm3_init_equilibrium", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("lbm3_step", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm3_moments", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    ("lbm3_diagnostics", ctypes.c_int, [_vp] + [ctypes.c_int] * 6 + [_vp]),
+    ("lbm3_state_bytes", ctypes.c_size_t, [_vp]),
+    ("lbm3_get_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(_i64)]),
+    ("lbm3_set_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _i64]),
     ("lbm3_time", _i64, [_vp]),
     ("lbm3_destroy", None, [_vp]),
     ("lbm3_last_error", ctypes.c_char_p, [_vp]),
@@ -330,6 +334,25 @@ def lbm3_step(h, nsteps) -> int:
 
 def lbm3_moments(h, rho_ptr, ux_ptr, uy_ptr, uz_ptr) -> int:
     return load().lbm3_moments(h, rho_ptr, ux_ptr, uy_ptr, uz_ptr)
+
+
+def lbm3_diagnostics(h, x0, y0, z0, x1, y1, z1, out_ptr) -> int:
+    return load().lbm3_diagnostics(h, int(x0), int(y0), int(z0), int(x1), int(y1), int(z1),
+                                   out_ptr)
+
+
+def lbm3_state_bytes(h) -> int:
+    return load().lbm3_state_bytes(h)
+
+
+def lbm3_get_state(h, dst_ptr, nbytes):
+    t = _i64(0)
+    rc = load().lbm3_get_state(h, dst_ptr, nbytes, ctypes.byref(t))
+    return rc, t.value
+
+
+def lbm3_set_state(h, src_ptr, nbytes, time) -> int:
+    return load().lbm3_set_state(h, src_ptr, nbytes, int(time))
 
 
 def lbm3_time(h) -> int:
@@ -704,6 +727,27 @@ class Lattice3:
         out = [np.empty(shp) for _ in range(4)]
         self._check(lbm3_moments(self.h, *(a.ctypes.data for a in out)), "lbm3_moments")
         return tuple(out)
+
+    def diagnostics(self, region=None) -> np.ndarray:
+        """FP64 sums over region (x0, y0, z0, x1, y1, z1) (default: all cells):
+        sum rho', sum (j - rho0 u0) (3), acoustic energy, sum rho'^2, non-finite
+        cells."""
+        r = region if region is not None else (0, 0, 0, self.nx, self.ny, self.nz)
+        out = np.zeros(7)
+        rc = lbm3_diagnostics(self.h, *r, out.ctypes.data)
+        if rc != LBM_ERR_NONFINITE:
+            self._check(rc, "lbm3_diagnostics")
+        return out
+
+    def get_state(self):
+        buf = np.empty(lbm3_state_bytes(self.h), dtype=np.uint8)
+        rc, t = lbm3_get_state(self.h, buf.ctypes.data, buf.nbytes)
+        self._check(rc, "lbm3_get_state")
+        return buf, t
+
+    def set_state(self, buf: np.ndarray, time: int) -> None:
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(lbm3_set_state(self.h, buf.ctypes.data, buf.nbytes, time), "lbm3_set_state")
 
     @property
     def time(self) -> int:
