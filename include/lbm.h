@@ -215,7 +215,6 @@ int lbm_set_steps_per_launch(lbm_handle h, int steps);
 /* The current choice (LBM_ERR_ARG for a NULL handle). */
 int lbm_steps_per_launch(lbm_handle h);
 
-/* Replace the handle's stream (borrowed; NULL = legacy default stream). */
 /* Staging of the two-step launches' input by the Tensor Memory Accelerator.
  * With it (1), each 64 x 16 tile's input -- the nine planes of the 72 x 20
  * cells around it -- arrives in shared memory as one bulk tensor copy whose
@@ -233,6 +232,7 @@ int lbm_steps_per_launch(lbm_handle h);
 int lbm_set_tma_staging(lbm_handle h, int on);
 int lbm_tma_staging(lbm_handle h);
 
+/* Replace the handle's stream (borrowed; NULL = legacy default stream). */
 int lbm_set_stream(lbm_handle h, void* cuda_stream);
 
 /* The line source of an LBM_BC_CHANNEL lattice (Sec. 4.2): density
