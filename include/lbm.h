@@ -168,7 +168,15 @@ int lbm_diagnostics(lbm_handle h, int x0, int y0, int x1, int y1, double out[6])
 
 /* Checkpoint: the raw population buffer of the current time (bytes =
  * lbm_state_bytes) and the step counter.  on_device selects device or host
- * memory for dst/src; host transfers synchronise. */
+ * memory for dst/src; host transfers synchronise.  The buffer holds 9 planes
+ * of ny rows of pitch elements (pitch = nx rounded up to 128 bytes).
+ *
+ * Padding canaries (a debugging aid): with the environment variable
+ * LBM_CANARY=1 at lbm_create (lbm_batch_create, lbm3_create), the padding of
+ * every row -- elements nx .. pitch - 1 -- of both population buffers is set
+ * to all-one bytes, a NaN in every storage format.  No kernel reads or writes
+ * padding, so the padding of the state returned here stays all-one bytes and
+ * the cells' values equal those of a run without canaries. */
 size_t lbm_state_bytes(lbm_handle h);
 int lbm_get_state(lbm_handle h, void* dst, size_t bytes, int on_device, int64_t* time);
 int lbm_set_state(lbm_handle h, const void* src, size_t bytes, int on_device, int64_t time);
@@ -347,6 +355,14 @@ int64_t lbm_batch_time(lbm_batch b, int id);
  * and lbm_diagnostics. */
 int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* uy, int on_device);
 int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, double out[6]);
+
+/* The raw population buffer of instance id at its current time, in the
+ * layout of lbm_get_state (bytes = lbm_batch_state_bytes, 0 for an unknown
+ * id); on_device selects device or host memory for dst, host transfers
+ * synchronise the batch's stream.  LBM_ERR_ARG for an unknown id or a size
+ * mismatch. */
+size_t lbm_batch_state_bytes(lbm_batch b, int id);
+int lbm_batch_get_state(lbm_batch b, int id, void* dst, size_t bytes, int on_device);
 
 /* Remove instance id.  Its buffers are released once the launches issued
  * before the call have completed (an event recorded now, checked on later

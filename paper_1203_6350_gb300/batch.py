@@ -146,6 +146,13 @@ class Batch:
             self._check(rc, "lbm_batch_diagnostics")
         return out
 
+    def get_state(self, i) -> np.ndarray:
+        """Raw population buffer of instance i (layout of Lattice.get_state)."""
+        buf = np.empty(lbm.lbm_batch_state_bytes(self.b, i), dtype=np.uint8)
+        self._check(lbm.lbm_batch_get_state(self.b, i, buf.ctypes.data, buf.nbytes, 0),
+                    "lbm_batch_get_state")
+        return buf
+
     def remove(self, i) -> None:
         self._check(lbm.lbm_batch_remove(self.b, i), "lbm_batch_remove")
         self.shapes.pop(i, None)

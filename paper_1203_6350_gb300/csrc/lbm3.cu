@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm.h"
+#include "lbm_internal.h"
 
 namespace {
 
@@ -625,6 +626,9 @@ int lbm3_create(int nx, int ny, int nz, lbm_storage storage, double rho0, double
         cudaMemsetAsync(h->chi[0], 0, nx * es, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->chi[1], 0, ny * es, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->chi[2], 0, nz * es, h->stream) != cudaSuccess ||
+        (lbm::canary_requested() &&
+         (lbm::paint_canary(h->buf[0], es, nx, pitch, 1ll * kQ * ny * nz, h->stream) != cudaSuccess ||
+          lbm::paint_canary(h->buf[1], es, nx, pitch, 1ll * kQ * ny * nz, h->stream) != cudaSuccess)) ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         lbm3_destroy(h);
         return fail3(nullptr, LBM_ERR_CUDA, "clearing the buffers failed");

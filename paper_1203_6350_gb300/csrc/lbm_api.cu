@@ -419,6 +419,8 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, h->buf_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->buf_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_time, 0, sizeof(long long), h->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess && lbm::canary_requested(); ++i)
+        e = lbm::paint_canary(h->buf[i], es, nx, h->geo.pitch, 9ll * ny, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         lbm_destroy(h);

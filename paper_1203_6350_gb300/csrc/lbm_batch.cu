@@ -678,6 +678,7 @@ struct lbm_batch_ctx {
     // TMA staging of the two-step input (FP32 batches, Dirichlet instances)
     bool tma = false;
     int tma_grid = 0;
+    bool canary = false;  // LBM_CANARY=1 at creation: instances' row padding holds NaN canaries
     CUtensorMap* d_maps = nullptr;  // 2 per dense instance
     size_t maps_cap = 0;            // entries
     std::vector<CUtensorMap> h_maps;
@@ -1052,6 +1053,7 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
     if (alloc && (!alloc->alloc || !alloc->free)) return LBM_ERR_ARG;
     lbm_batch_ctx* b = new lbm_batch_ctx();
     b->storage = storage;
+    b->canary = lbm::canary_requested();
     // 16-bit batches are issue-bound and gain from the packed pair (1.2x measured);
     // FP32 batches are memory-latency-bound and the one-cell kernel's higher
     // occupancy wins (1.04x).
@@ -1244,6 +1246,9 @@ int lbm_batch_add(lbm_batch b, int nx, int ny, double rho0, double ux0, double u
         }
     }
     e = cudaMemcpyAsync(in.tabs, in.tabs_host.data(), in.tab_bytes, cudaMemcpyHostToDevice, b->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess && b->canary; ++i)
+        e = lbm::paint_canary(in.buf[i], storage_size(b->storage), nx, in.geo.pitch, 9ll * ny,
+                              b->stream);
     if (e != cudaSuccess) {
         bd_free(b, in.buf[0], in.buf_bytes);
         bd_free(b, in.buf[1], in.buf_bytes);
@@ -1386,6 +1391,28 @@ int lbm_batch_moments(lbm_batch b, int id, double* rho_dev, double* ux, double* 
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     }
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_moments: ") + cudaGetErrorString(e));
+    return on_device ? LBM_OK : check_batch_tma(b);
+}
+
+size_t lbm_batch_state_bytes(lbm_batch b, int id) {
+    const Instance* in = b ? find(b, id) : nullptr;
+    return in ? in->buf_bytes : 0;
+}
+
+int lbm_batch_get_state(lbm_batch b, int id, void* dst, size_t bytes, int on_device) {
+    if (!b) return LBM_ERR_ARG;
+    Instance* in = find(b, id);
+    if (!in) return bfail(b, LBM_ERR_ARG, "unknown instance");
+    if (!dst || bytes != in->buf_bytes)
+        return bfail(b, LBM_ERR_ARG, "dst / bytes do not match lbm_batch_state_bytes");
+    BDeviceGuard dg(b->device);
+    const int cur = (int)(in->launched & 1);
+    cudaError_t e = cudaMemcpyAsync(dst, in->buf[cur], bytes,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    b->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess)
+        return bfail(b, LBM_ERR_CUDA, std::string("lbm_batch_get_state: ") + cudaGetErrorString(e));
     return on_device ? LBM_OK : check_batch_tma(b);
 }
 

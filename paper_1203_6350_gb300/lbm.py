@@ -115,6 +115,8 @@ SIGNATURES = [
     ("lbm_batch_moments", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]),
     ("lbm_batch_diagnostics", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_int, _vp]),
+    ("lbm_batch_state_bytes", ctypes.c_size_t, [_vp, ctypes.c_int]),
+    ("lbm_batch_get_state", ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int]),
     ("lbm_batch_remove", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_batch_count", ctypes.c_int, [_vp]),
     ("lbm_batch_set_stream", ctypes.c_int, [_vp, _vp]),
@@ -440,6 +442,14 @@ def lbm_batch_moments(b, i, rho_ptr, ux_ptr, uy_ptr, on_device) -> int:
 
 def lbm_batch_diagnostics(b, i, x0, y0, x1, y1, out_ptr) -> int:
     return load().lbm_batch_diagnostics(b, int(i), int(x0), int(y0), int(x1), int(y1), out_ptr)
+
+
+def lbm_batch_state_bytes(b, i) -> int:
+    return int(load().lbm_batch_state_bytes(b, int(i)))
+
+
+def lbm_batch_get_state(b, i, dst_ptr, nbytes, on_device) -> int:
+    return load().lbm_batch_get_state(b, int(i), dst_ptr, int(nbytes), int(on_device))
 
 
 def lbm_batch_remove(b, i) -> int:
