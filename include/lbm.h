@@ -360,7 +360,7 @@ int lbm_batch_diagnostics(lbm_batch b, int id, int x0, int y0, int x1, int y1, d
  * layout of lbm_get_state (bytes = lbm_batch_state_bytes, 0 for an unknown
  * id); on_device selects device or host memory for dst, host transfers
  * synchronise the batch's stream.  LBM_ERR_ARG for an unknown id or a size
- * mismatch. */
+ * mismatch, LBM_ERR_STATE before the instance is initialised. */
 size_t lbm_batch_state_bytes(lbm_batch b, int id);
 int lbm_batch_get_state(lbm_batch b, int id, void* dst, size_t bytes, int on_device);
 

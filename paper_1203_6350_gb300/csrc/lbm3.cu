@@ -714,6 +714,7 @@ int lbm3_init_equilibrium(lbm3_handle h, const double* rho, const double* ux, co
 }
 
 int lbm3_step(lbm3_handle h, int nsteps) {
+    const lbm::NvtxRange nvtx("lbm3_step");
     if (!h) return fail3(nullptr, LBM_ERR_ARG, "NULL handle");
     if (nsteps < 0) return fail3(h, LBM_ERR_ARG, "nsteps < 0");
     if (!h->ready) return fail3(h, LBM_ERR_STATE, "step before lbm3_init_equilibrium");

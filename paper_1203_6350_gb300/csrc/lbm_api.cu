@@ -584,6 +584,7 @@ int lbm_init_pulse(lbm_handle h, double eps, double half_width, double x0, doubl
 }
 
 int lbm_step(lbm_handle h, int nsteps) {
+    const lbm::NvtxRange nvtx("lbm_step");
     if (!h) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
     if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init_equilibrium / lbm_set_state");

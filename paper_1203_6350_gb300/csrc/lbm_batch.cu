@@ -1317,6 +1317,7 @@ int lbm_batch_init_pulse(lbm_batch b, int id, double eps, double half_width, dou
 }
 
 int lbm_batch_step(lbm_batch b, int nsteps) {
+    const lbm::NvtxRange nvtx("lbm_batch_step");
     if (!b) return LBM_ERR_ARG;
     if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
     BDeviceGuard dg(b->device);
@@ -1403,6 +1404,7 @@ int lbm_batch_get_state(lbm_batch b, int id, void* dst, size_t bytes, int on_dev
     if (!b) return LBM_ERR_ARG;
     Instance* in = find(b, id);
     if (!in) return bfail(b, LBM_ERR_ARG, "unknown instance");
+    if (!in->initialised) return bfail(b, LBM_ERR_STATE, "instance not initialised");
     if (!dst || bytes != in->buf_bytes)
         return bfail(b, LBM_ERR_ARG, "dst / bytes do not match lbm_batch_state_bytes");
     BDeviceGuard dg(b->device);

@@ -10,8 +10,19 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace lbm {
+
+// An NVTX range over one API call, so that profilers can group its launches
+// (e.g. ncu --nvtx --nvtx-include "lbm_step/").  Without a tool attached a
+// push or pop is one check of a function pointer.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Padding canaries, a debugging aid (environment variable LBM_CANARY=1 when a
 // lattice, batch or 3-D lattice is created): the padding of every row --

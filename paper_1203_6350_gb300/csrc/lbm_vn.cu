@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm.h"
+#include "lbm_internal.h"
 
 namespace {
 
@@ -610,6 +611,7 @@ extern "C" {
 
 int lbm_vn_growth(const int* variant, const double* cases, int ncases, int nk, int precision,
                   double* growth, double* k_at_max, void* cuda_stream) {
+    const lbm::NvtxRange nvtx("lbm_vn_growth");
     int rc = check_cases(variant, cases, ncases, nk, precision);
     if (rc != LBM_OK) return rc;
     if (ncases > 0 && !growth) return fail(LBM_ERR_ARG, "NULL growth");
@@ -646,6 +648,7 @@ int lbm_vn_growth(const int* variant, const double* cases, int ncases, int nk, i
 int lbm_vn_chi_crit(const int* variant, const double* cases, int ncases, int nk, int precision,
                     double chi_lo, double chi_hi, int nscan, int iters, double tol,
                     double* chi_crit, void* cuda_stream) {
+    const lbm::NvtxRange nvtx("lbm_vn_chi_crit");
     int rc = check_cases(variant, cases, ncases, nk, precision);
     if (rc != LBM_OK) return rc;
     if (!std::isfinite(chi_lo) || !std::isfinite(chi_hi) || chi_lo < 0 || !(chi_hi > chi_lo))

@@ -181,3 +181,24 @@ def test_d3q15_leaves_padding_alone(monkeypatch, storage, bc):
     cells, _ = _split(states[1], 15 * ny * nz, nx, es)
     assert pad_c.size > 0 and np.all(pad_c == 0xFF)
     np.testing.assert_array_equal(cells_c, cells)
+
+
+def test_batch_get_state_arguments():
+    """lbm_batch_get_state: unknown id and size mismatch are LBM_ERR_ARG, an
+    instance before initialisation LBM_ERR_STATE; afterwards the raw state
+    holds the initial deviations (rest state: zero cells)."""
+    from paper_1203_6350_gb300 import lbm
+    from paper_1203_6350_gb300.batch import Batch
+
+    with Batch("f32") as b:
+        i = b.add(45, 13, steps=4)
+        n = lbm.lbm_batch_state_bytes(b.b, i)
+        assert n == 9 * 13 * 64 * 4
+        assert lbm.lbm_batch_state_bytes(b.b, 12345) == 0
+        buf = np.empty(n, dtype=np.uint8)
+        assert lbm.lbm_batch_get_state(b.b, i, buf.ctypes.data, n, 0) == lbm.LBM_ERR_STATE
+        b.init_equilibrium(i, np.ones((13, 45)), np.zeros((13, 45)), np.zeros((13, 45)))
+        assert lbm.lbm_batch_get_state(b.b, 12345, buf.ctypes.data, n, 0) == lbm.LBM_ERR_ARG
+        assert lbm.lbm_batch_get_state(b.b, i, buf.ctypes.data, n - 4, 0) == lbm.LBM_ERR_ARG
+        cells, _ = _split(b.get_state(i), 9 * 13, 45, 4)
+        assert not cells.any()
