@@ -26,7 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm.h"
-#include "lbm_internal.h"
+#include "lbm_host.h"
 
 namespace {
 

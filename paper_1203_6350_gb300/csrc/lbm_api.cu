@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_host.h"
 #include "lbm_internal.h"
 
 using lbm::Geometry;

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_host.h"
 #include "lbm_step_tma.cuh"
 
 namespace lbm {
