@@ -780,6 +780,7 @@ def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = Batch("f32", stream=stream, config=cfg)
+        staged = lbm.lbm_batch_tma_staging(b.b) == 1
         for w in works:
             with_warn(lambda: b.add_workload(w))
         b.step(warmup)
@@ -814,7 +815,9 @@ def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
         "lattices": count, "cells": cells, "steps": steps, "tile": list(cfg["tile"]),
         "cells_per_thread": cfg["cells"], "steps_per_launch": cfg["steps_per_launch"],
         "kernel": {(1, 1): "batch_step_kernel<float>", (2, 1): "batch_step2_kernel<float>",
-                   (2, 2): "batch_tb2_kernel<float>"}[(cfg["cells"], cfg["steps_per_launch"])],
+                   (2, 2): ("batch_tb2_tma_kernel<variant> (Dirichlet instances staged by TMA)"
+                            if staged else "batch_tb2_kernel<float>")
+                   }[(cfg["cells"], cfg["steps_per_launch"])],
         "mlups": cells * steps / t_batch / 1e6,
         "plain_loop_mlups": cells * steps / t_plain / 1e6,
         "speedup_vs_plain_loop": t_plain / t_batch,
