@@ -32,7 +32,7 @@
  *   oracle_collide_cell_viscous.
  *   f_i(x + c_i, t + 1) = fhat_i(x, t)                               (Eq. blbs)
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - f^eq is the standard second-order D2Q9 equilibrium
  *       f^eq_i = w_i rho (1 + 3 c_i.u + 9/2 (c_i.u)^2 - 3/2 u.u)
  *     and its linear part is f^Leq_i(rho, j) = w_i (rho + 3 c_i.j).
