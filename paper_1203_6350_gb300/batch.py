@@ -99,12 +99,16 @@ class Batch:
         builds its Gaussian pulse on the device, None leaves it uninitialised."""
         i = self.add(w.nx, w.ny, w.steps if steps is None else steps, w.s, w.n, w.m, w.rho0,
                      w.u0, w.bc, w.variant, w.chi_x, w.chi_y, w.rho_f, w.u_f)
-        if init == "pulse" and w.rho_dev is None:
-            mt = w.meta
-            self.init_pulse(i, mt.get("eps", 0.0), mt.get("b", 1.0), mt.get("x0", 0.0),
-                            mt.get("y0", 0.0))
-        elif init:
-            self.init_equilibrium(i, *w.initial_fields())
+        try:
+            if init == "pulse" and w.rho_dev is None:
+                mt = w.meta
+                self.init_pulse(i, mt.get("eps", 0.0), mt.get("b", 1.0), mt.get("x0", 0.0),
+                                mt.get("y0", 0.0))
+            elif init:
+                self.init_equilibrium(i, *w.initial_fields())
+        except Exception:
+            self.remove(i)  # no half-initialised instance stays in the batch
+            raise
         return i
 
     def init_pulse(self, i, eps, half_width, x0, y0) -> None:

@@ -550,15 +550,19 @@ class Lattice:
         fields; init="pulse" builds its Gaussian pulse on the device (workloads
         whose initial state is a pulse described by eps, b, x0, y0)."""
         lat = cls(w.nx, w.ny, storage or w.storage, w.rho0, w.u0, w.s, w.n, w.m, w.bc, **kw)
-        lat.set_sponge(w.variant, w.chi_x, w.chi_y, w.rho_f, w.u_f)
-        if w.bc == "channel":
-            lat.set_source(*getattr(w, "source", (0.0, 0.0, 0.0)))
-        if init == "pulse" and w.rho_dev is None:
-            mt = w.meta
-            lat.init_pulse(mt.get("eps", 0.0), mt.get("b", 1.0), mt.get("x0", 0.0),
-                           mt.get("y0", 0.0))
-        else:
-            lat.init_equilibrium(*w.initial_fields())
+        try:
+            lat.set_sponge(w.variant, w.chi_x, w.chi_y, w.rho_f, w.u_f)
+            if w.bc == "channel":
+                lat.set_source(*getattr(w, "source", (0.0, 0.0, 0.0)))
+            if init == "pulse" and w.rho_dev is None:
+                mt = w.meta
+                lat.init_pulse(mt.get("eps", 0.0), mt.get("b", 1.0), mt.get("x0", 0.0),
+                               mt.get("y0", 0.0))
+            else:
+                lat.init_equilibrium(*w.initial_fields())
+        except Exception:
+            lat.close()  # release the device memory of a lattice that failed set-up
+            raise
         return lat
 
     @property

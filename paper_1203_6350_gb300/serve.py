@@ -10,6 +10,11 @@ added while others are running starts in the next chunk and shares their
 launches; each job still takes exactly its own steps, so its result is the
 same alone and in the mix.
 
+Failures stay with their job.  A job the library refuses at admission (an
+invalid problem, a failed allocation) is reported with its error and takes
+no memory; a job whose state has gone non-finite is reported as such when it
+is read out.  The other jobs carry on either way.
+
 :func:`serial_loop` is the comparison: the same jobs one after another through
 the single-lattice API.
 """
@@ -36,6 +41,7 @@ class Job:
     finished: Optional[float] = None
     result: Optional[np.ndarray] = None   # lbm diagnostics over the layer-free interior
     field: Optional[np.ndarray] = None    # final rho' (when the server keeps fields)
+    error: Optional[str] = None           # why the job failed (None: it did not)
 
     @property
     def latency(self) -> Optional[float]:
@@ -121,18 +127,24 @@ class Server:
                 break
             job = self.pending.popleft()
             w = job.workload
-            if self.solo_cells is not None and w.cells >= self.solo_cells:
-                # created and initialised on the side stream (lbm_create waits for
-                # its stream), then handed to the stepping stream
-                lat = lbm.Lattice.from_workload(w, init=self.init, stream=self.side,
-                                                device=self.device)
-                self.stream.wait_stream(self.side)
-                lat.set_stream(self.stream)
-                self.resident[job.id] = ("solo", lat, job)
-            else:
-                b = self._batch(w.storage)
-                i = b.add_workload(w, steps=w.steps, init=self.init)
-                self.resident[job.id] = (w.storage, i, job)
+            try:
+                if self.solo_cells is not None and w.cells >= self.solo_cells:
+                    # created and initialised on the side stream (lbm_create waits
+                    # for its stream), then handed to the stepping stream
+                    lat = lbm.Lattice.from_workload(w, init=self.init, stream=self.side,
+                                                    device=self.device)
+                    self.stream.wait_stream(self.side)
+                    lat.set_stream(self.stream)
+                    self.resident[job.id] = ("solo", lat, job)
+                else:
+                    b = self._batch(w.storage)
+                    i = b.add_workload(w, steps=w.steps, init=self.init)
+                    self.resident[job.id] = (w.storage, i, job)
+            except lbm.LbmError as e:  # refused: reported, holds nothing
+                job.error = f"admission failed: {e}"
+                job.finished = now
+                self.done.append(job)
+                continue
             self.used += job.bytes
             self.cells += w.cells
             job.admitted = now
@@ -174,6 +186,9 @@ class Server:
                     job.field = b.moments(h)[0]
                 b.set_stream(self.stream)
                 b.remove(h)  # freed once the launches issued so far have completed
+            if job.result[5] > 0:
+                job.error = (f"non-finite rho' or u in {int(job.result[5])} cells of the "
+                             "read-out region")
             self.used -= job.bytes
             self.cells -= job.workload.cells
             job.finished = clock()
@@ -273,10 +288,14 @@ def serial_loop(jobs, keep_fields: bool = False, realtime: bool = True, init: st
 
 
 def summary(jobs, wall: float) -> dict:
-    lat = np.array([j.latency for j in jobs if j.latency is not None])
-    cells = sum(j.workload.cells * j.workload.steps for j in jobs)
+    """Throughput and latency of the solved jobs (those with a result; jobs
+    refused at admission count as failed)."""
+    solved = [j for j in jobs if j.result is not None]
+    lat = np.array([j.latency for j in solved if j.latency is not None])
+    cells = sum(j.workload.cells * j.workload.steps for j in solved)
     return {
-        "jobs": len(jobs), "wall_s": wall, "solves_per_s": len(jobs) / wall if wall > 0 else None,
+        "jobs": len(solved), "failed": len(jobs) - len(solved), "wall_s": wall,
+        "solves_per_s": len(solved) / wall if wall > 0 else None,
         "mlups": cells / wall / 1e6 if wall > 0 else None,
         "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
         "p99_s": float(np.percentile(lat, 99)) if lat.size else None,

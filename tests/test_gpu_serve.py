@@ -80,3 +80,81 @@ def test_oversized_job_is_refused():
     with pytest.raises(ValueError):
         srv.submit(Job(id=0, workload=w))
     srv.close()
+
+
+def test_failed_jobs_are_reported_and_the_rest_carry_on(monkeypatch):
+    """Failures stay with their job.  Three jobs of the trace fail at admission:
+    a host-side fake of a failed allocation (LBM_ERR_OOM) on the
+    single-lattice path and on the batched path, and a poisoned problem
+    (rho0 < 0, refused by the library).  They are reported with their error
+    and hold no memory; every other job's result equals its result alone."""
+    from paper_1203_6350_gb300 import lbm
+    from paper_1203_6350_gb300.batch import Batch
+    from paper_1203_6350_gb300.serve import Job, Server, summary
+
+    jobs = _jobs()
+    solo_cells = 12000
+    solo = [j.id for j in jobs if j.workload.cells >= solo_cells]
+    batched = [j.id for j in jobs if j.workload.cells < solo_cells]
+    fail_solo, fail_batch = solo[1], batched[1]
+    poisoned = batched[2]
+    jobs[poisoned] = Job(id=poisoned, workload=jobs[poisoned].workload.with_(rho0=-1.0),
+                         arrival=jobs[poisoned].arrival)
+    victims = {fail_solo: "solo", fail_batch: "batch"}
+
+    orig_lat = lbm.Lattice.from_workload.__func__
+    orig_add = Batch.add_workload
+
+    def fake_lattice(cls, w, *a, **kw):
+        if w is jobs[fail_solo].workload:
+            raise lbm.LbmError(lbm.LBM_ERR_OOM, "device allocation failed (fake)")
+        return orig_lat(cls, w, *a, **kw)
+
+    def fake_add(self, w, *a, **kw):
+        if w is jobs[fail_batch].workload:
+            raise lbm.LbmError(lbm.LBM_ERR_OOM, "instance allocation failed (fake)")
+        return orig_add(self, w, *a, **kw)
+
+    monkeypatch.setattr(lbm.Lattice, "from_workload", classmethod(fake_lattice))
+    monkeypatch.setattr(Batch, "add_workload", fake_add)
+    per_job = max(j.bytes for j in jobs)
+    srv = Server(hbm_budget=3.5 * per_job, chunk=16, keep_fields=True, solo_cells=solo_cells)
+    done = {j.id: j for j in srv.run(jobs)}
+    assert srv.used == 0 and srv.cells == 0 and not srv.resident
+    srv.close()
+    monkeypatch.undo()
+
+    assert len(done) == len(jobs)
+    for jid in victims:
+        assert done[jid].result is None and "fake" in done[jid].error
+    assert done[poisoned].result is None and "far-field" in done[poisoned].error
+    s = summary(list(done.values()), 1.0)
+    assert s["failed"] == 3 and s["jobs"] == len(jobs) - 3
+
+    for j in _jobs():
+        if j.id in victims or j.id == poisoned:
+            continue
+        alone = Server(hbm_budget=1e12, chunk=16, keep_fields=True, solo_cells=solo_cells)
+        (res,) = alone.run([j], realtime=False)
+        alone.close()
+        assert done[j.id].error is None or "non-finite" in done[j.id].error
+        np.testing.assert_array_equal(res.field, done[j.id].field)
+        np.testing.assert_array_equal(res.result, done[j.id].result)
+
+
+def test_non_finite_job_is_reported():
+    """A type I layer with s + chi > 2 (Eq. effectrelax) blows up; the server
+    reports that job as non-finite at read-out and the stable job beside it
+    as solved."""
+    from paper_1203_6350_gb300.serve import Job, Server
+
+    bad = wl.pulse_workload(64, 64, variant="I", storage="f32", chi_max=1.0, width=12,
+                            steps=600, name="unstable")
+    good = wl.pulse_workload(64, 64, variant="II", storage="f32", chi_max=0.3, width=12,
+                             steps=600, name="stable")
+    srv = Server(hbm_budget=1e9, chunk=64)
+    done = {j.id: j for j in srv.run([Job(id=0, workload=bad), Job(id=1, workload=good)],
+                                     realtime=False)}
+    srv.close()
+    assert done[0].result[5] > 0 and "non-finite" in done[0].error
+    assert done[1].result[5] == 0 and done[1].error is None
