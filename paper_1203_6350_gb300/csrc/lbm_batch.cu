@@ -326,6 +326,29 @@ __global__ void __launch_bounds__(kTbThreads, 3)
 // step that ends a budget (pulled from global memory) -- and issues the next
 // tile's copy as soon as step one has read the box.  Waits are bounded as in
 // the single-lattice kernel; a CTA that gives up sets *err.
+//
+// A CTA's consecutive tiles are G apart in the table, so for small lattices
+// nearly every tile belongs to another instance.  Nothing the next tile needs
+// is fetched on the critical path: its tile record (one tile further ahead)
+// and its instance descriptor arrive by cp.async into the other of two
+// shared-memory slots while the current tile computes.
+constexpr int kDescChunks = (int)(sizeof(BatchInst<F2>) / 8);  // 8-byte cp.async pieces
+static_assert(sizeof(BatchInst<F2>) % 8 == 0 && kDescChunks <= kTmaThreads,
+              "descriptor slots: 8-byte multiples, one 8-byte piece per thread");
+constexpr size_t kTmaDescOff = kTmaBoxBytes + kTmaRingBytes + 16;  // box, ring, mbarrier, mode
+static_assert(kTmaDescOff % 16 == 0, "16-byte aligned slots (the tile records follow)");
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int VAR>
 __global__ void __launch_bounds__(kTmaThreads, 2)
     batch_tb2_tma_kernel(const BatchInst<F2>* __restrict__ insts,
@@ -337,10 +360,9 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     float* r1 = reinterpret_cast<float*>(tma_raw + kTmaBoxBytes);
     auto* bar = reinterpret_cast<unsigned long long*>(tma_raw + kTmaBoxBytes + kTmaRingBytes);
     auto* mode_sm = reinterpret_cast<int*>(tma_raw + kTmaBoxBytes + kTmaRingBytes + 8);
-    unsigned char* desc_raw = tma_raw + kTmaBoxBytes + kTmaRingBytes + 16;
-    const BatchInst<F2>& sd = *reinterpret_cast<const BatchInst<F2>*>(desc_raw);
-    constexpr int kWords = (int)(sizeof(BatchInst<F2>) / 4);
-    static_assert(kWords <= kTmaThreads, "one descriptor word per thread");
+    // two descriptor slots, then two tile-record slots
+    auto* desc = reinterpret_cast<BatchInst<F2>*>(tma_raw + kTmaDescOff);
+    auto* trec = reinterpret_cast<BatchTile*>(tma_raw + kTmaDescOff + 2 * sizeof(BatchInst<F2>));
     constexpr int c = batch_class(VAR, kDirichlet);
     const int tid = threadIdx.x, G = gridDim.x;
     if (tid == 0) mbar_init(bar);
@@ -351,9 +373,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     const long long step = counters[0] + step_off;
     const int lpar = (int)((counters[1] + launch_off) & 1);
     // 0: inactive, 1: two staged steps (copy issued), 2: the budget's last step
-    auto plan_and_issue = [&](int i) -> int {
-        const BatchTile tl = ct[i];
-        const BatchInst<F2>& d = insts[tl.inst];
+    auto plan_and_issue = [&](const BatchTile& tl, const BatchInst<F2>& d) -> int {
         const long long st = d.start, en = d.end;
         if (step < st || step >= en) return 0;
         if (step + 1 >= en) return 2;
@@ -361,21 +381,35 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         tma_box_load(box, maps + 2 * tl.inst + parity, bar, tl.x0 - kTmaPad, tl.y0 - 2);
         return 1;
     };
-    if (tid == 0) *mode_sm = (int)blockIdx.x < count ? plan_and_issue(blockIdx.x) : 0;
+    if ((int)blockIdx.x >= count) {
+        asm volatile("griddepcontrol.launch_dependents;");
+        return;
+    }
+    // the first tile's record and descriptor, and the second tile's record
+    if (tid < 2) {
+        const int t = blockIdx.x + tid * G;
+        if (t < count) trec[tid] = ct[t];
+    }
     __syncthreads();
-    int held = -1;
+    if (tid < kDescChunks)
+        reinterpret_cast<unsigned long long*>(desc)[tid] =
+            __ldg(reinterpret_cast<const unsigned long long*>(insts + trec[0].inst) + tid);
+    __syncthreads();
+    if (tid == 0) *mode_sm = plan_and_issue(trec[0], desc[0]);
+    __syncthreads();
     unsigned phase = 0;
-    for (int t = blockIdx.x; t < count; t += G) {
+    int n = 0;
+    for (int t = blockIdx.x; t < count; t += G, ++n) {
+        const int sl = n & 1, so = sl ^ 1;
         const int mode = *mode_sm;  // block-uniform
-        const BatchTile tile = ct[t];
-        if (tile.inst != held) {  // block-uniform
-            unsigned w = 0;
-            if (tid < kWords) w = __ldg(reinterpret_cast<const unsigned*>(insts + tile.inst) + tid);
-            __syncthreads();
-            if (tid < kWords) reinterpret_cast<unsigned*>(desc_raw)[tid] = w;
-            __syncthreads();
-            held = tile.inst;
-        }
+        const BatchTile tile = trec[sl];
+        const BatchInst<F2>& sd = desc[sl];
+        const bool more = t + G < count;
+        // the next tile's descriptor into the other slot, while this tile computes
+        if (more && tid < kDescChunks)
+            cp_async8(reinterpret_cast<unsigned long long*>(desc + so) + tid,
+                      reinterpret_cast<const unsigned long long*>(insts + trec[so].inst) + tid);
+        cp_async_commit();
         const int parity = lpar ^ (int)(sd.l0 & 1);
         const int nx = sd.nx, ny = sd.ny, pitch = sd.pitch;
         const unsigned plane = static_cast<unsigned>(sd.plane);
@@ -385,6 +419,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             const bool ok = mbar_wait(bar, phase);
             phase ^= 1u;
             if (!__syncthreads_and(ok)) {  // the whole CTA stops together
+                cp_async_wait_all();
                 if (tid == 0) {
                     mbar_wait(bar, phase ^ 1u);  // the copy in flight, once more (bounded)
                     atomicExch(err, 1);
@@ -411,8 +446,13 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                 store_pair<float>(r1, kR1Plane, static_cast<unsigned>(py * kR1W + 2 * px), v);
             }
         }
-        __syncthreads();  // the box is read (and *mode_sm with it)
-        if (tid == 0) *mode_sm = t + G < count ? plan_and_issue(t + G) : 0;
+        cp_async_wait_all();
+        __syncthreads();  // the box is read; the next descriptor has arrived
+        if (tid == 0) {
+            *mode_sm = more ? plan_and_issue(trec[so], desc[so]) : 0;
+            if (t + 2 * G < count) cp_async16(trec + sl, ct + (t + 2 * G));  // the record after
+            cp_async_commit();
+        }
         if (mode == 1) {
             for (int p = tid; p < (kTbW / 2) * kTbH; p += kTmaThreads) {
                 const int qx = p % (kTbW / 2), qy = p / (kTbW / 2);
@@ -446,13 +486,14 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                     store_lo<float>(dst, plane, o, v);
             }
         }
-        __syncthreads();  // R1 and the descriptor are read; *mode_sm is written
+        cp_async_wait_all();  // thread 0: the record after next has arrived
+        __syncthreads();  // R1 and this slot's descriptor are read; *mode_sm is written
     }
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
 constexpr size_t batch_tma_smem_bytes() {
-    return kTmaBoxBytes + kTmaRingBytes + 16 + sizeof(BatchInst<F2>);
+    return kTmaDescOff + 2 * sizeof(BatchInst<F2>) + 2 * sizeof(BatchTile);
 }
 
 __global__ void advance_counters_kernel(long long* counters, int steps, int launches) {
