@@ -76,9 +76,9 @@ class Server:
         solo_cells: a lattice this large runs through the single-lattice kernel
         (chunk by chunk as graph replays, on its own stream beside the batched
         launch of the smaller resident jobs); None sends every job through the
-        batch.  The default, 16384 cells (128^2), batches only
-        lattices too small to keep the GPU busy on their own: on the serving
-        trace, interleaving the graph-replayed chunks of jobs from 128^2 up
+        batch.  The default, 16384 cells (128^2), batches only lattices too
+        small to keep the GPU busy on their own: on the serving trace (one
+        stream, 4M-cell limit), the graph-replayed chunks of jobs from 128^2 up
         measured faster than sharing a batched launch (24.2 against 22.5
         solves/s with a 1M-cell threshold).  A job's path depends only on its
         size, so its result does not depend on what else is resident.
