@@ -59,6 +59,22 @@ def viscous_ramp(n: int, width: int) -> np.ndarray:
     return layer_depth(n, width) / width
 
 
+def polynomial_profile(n: int, width: int, A: float, power: int = 4) -> np.ndarray:
+    """Table tab:sigma's polynomial profile,
+    sigma(x) = A (x - x0)^power (L - x) (power + 1)(power + 2) / (L - x0)^(power + 2),
+    laid across the layer as orszag_profile lays its own (x0 at depth 0, L at depth
+    width + 1).  A is the profile's integral over [x0, L]: the Beta integral of
+    t^power (1 - t) is 1 / ((power + 1)(power + 2)).  With power = 4,
+    orszag_profile(chi) is this profile with A = chi (L - x0) 3125 / (256 * 30):
+    A is an integral over the layer, chi the peak of the normalised profile."""
+    if width <= 0:
+        return np.zeros(n)
+    d = layer_depth(n, width)
+    L = width + 1.0
+    sig = A * d**power * (L - d) * (power + 1) * (power + 2) / L ** (power + 2)
+    return np.where(d > 0, sig, 0.0)
+
+
 def orszag_profile(n: int, width: int, chi: float) -> np.ndarray:
     """sigma = chi * sigma~ with the normalised A = n = 4 profile of
     Eq. (normalizedsigma), sigma~(x) = 3125 (L - x)(x - x0)^4 / (256 (L - x0)^5),
