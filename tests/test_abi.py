@@ -191,3 +191,43 @@ def test_lbm3_null_handle_calls_are_argument_errors(lib):
     assert lbm.lbm3_set_sponge(None, 2, None, None, None, 1.0, (0, 0, 0)) == lbm.LBM_ERR_ARG
     assert lbm.lbm3_time(None) == -1
     lbm.lbm3_destroy(None)
+
+
+def test_header_is_c99_and_links_from_plain_c(lib, tmp_path):
+    """The boundary is usable from C: include/lbm.h compiles as strict C99,
+    a C program links against liblbm.so, reads the version and gets
+    LBM_ERR_ARG (nothing done, no device touched) for NULL handles."""
+    import shutil
+    import subprocess
+
+    from paper_1203_6350_gb300 import build
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "lbm.h"
+int main(void) {
+    const char* v = lbm_version();
+    if (!v || !strlen(v)) return 1;
+    if (lbm_step(NULL, 1) != LBM_ERR_ARG) return 2;
+    if (lbm_moments(NULL, NULL, NULL, NULL, 0) != LBM_ERR_ARG) return 3;
+    if (lbm_batch_step(NULL, 1) != LBM_ERR_ARG) return 4;
+    if (lbm3_step(NULL, 1) != LBM_ERR_ARG) return 5;
+    if (lbm_batch_state_bytes(NULL, 0) != 0) return 6;
+    printf("%s\n", v);
+    return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                        str(src), "-L", build.BUILD, "-llbm", "-Wl,-rpath," + build.BUILD,
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.strip()
