@@ -500,14 +500,20 @@ def roofline_large(peaks, side: int = 4096, steps: int = 100):
                                         ("one_cell_per_thread", 1, 1, None)):
         t, spl, staged = timed_steps(w, steps, cells=cells, per_launch=per_launch, tma=tma)
         per_launch_s = t / (steps / spl)
+        achieved = BYTES_PER_CELL["f32"] * w.cells / per_launch_s / 1e9
         out[key] = {"steps_per_launch": spl, "avg_launch_us": per_launch_s * 1e6,
                     "mlups": w.cells * steps / t / 1e6,
-                    "achieved": BYTES_PER_CELL["f32"] * w.cells / per_launch_s / 1e9,
+                    "achieved": achieved, "frac": achieved / peaks["hbm_gbs"],
                     "kernel": STEP_KERNEL[("tb2_tma" if staged else "tb2") if spl == 2
                                           else (cells or 2)]}
     d = out["default"]
+    # a kernel that moves 72 B per cell and step at the full copy bandwidth
+    one_step_bound = peaks["hbm_gbs"] * 1e9 / BYTES_PER_CELL["f32"] / 1e6
     return {"bound": "hbm", "achieved": d["achieved"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": d["achieved"] / peaks["hbm_gbs"], "case": f"{side}x{side} FP32, 128-cell layer",
+            "frac": d["achieved"] / peaks["hbm_gbs"],
+            "one_step_hbm_bound_mlups": one_step_bound,
+            "mlups_over_one_step_bound": d["mlups"] / one_step_bound,
+            "case": f"{side}x{side} FP32, 128-cell layer",
             "kernel": d["kernel"], "steps_per_launch": d["steps_per_launch"],
             "avg_launch_us": d["avg_launch_us"], "mlups": d["mlups"],
             "bytes_per_launch": BYTES_PER_CELL["f32"] * w.cells,
