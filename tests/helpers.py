@@ -32,3 +32,14 @@ def run_gpu(w, storage=None, steps=None):
 def rel_l2(a, b) -> float:
     den = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
+
+
+def ring_regions(nx, ny, r=2):
+    """The outermost r cells of an nx x ny lattice as four disjoint rectangles
+    (x0, y0, x1, y1): the cells next to the Dirichlet wall, behind the layer."""
+    return [(0, 0, nx, r), (0, ny - r, nx, ny), (0, r, r, ny - r), (nx - r, r, nx, ny - r)]
+
+
+def interior_region(w):
+    """The cells with chi = 0 of a workload with a `width`-cell layer on every side."""
+    return (w.width, w.width, w.nx - w.width, w.ny - w.width)

@@ -530,6 +530,96 @@ def test_thicker_layer_absorbs_better(oracle_lib):
     assert out[0] > out[1] > out[2], out
 
 
+def _sweep_energies(core, w, steps=300, every=5, ring_steps=150):
+    """(R, E_wall): the interior acoustic energy after `steps` over its initial value
+    (reading C14), and the energy in the two cells next to the wall summed every
+    `every` steps up to `ring_steps`, over the same initial value."""
+    from helpers import interior_region, ring_regions, oracle_problem
+    from oracle import diagnostics as dg
+
+    st = core.State(oracle_problem(core, w), *w.initial_fields())
+    reg = interior_region(w)
+    e0 = dg.reduce_fields(*st.moments(), region=reg)[3]
+    wall, t = 0.0, 0
+    while t < ring_steps:
+        st.run(every)
+        t += every
+        fields = st.moments()
+        wall += every * sum(dg.reduce_fields(*fields, region=q)[3] for q in ring_regions(w.nx, w.ny))
+    st.run(steps - t)
+    return dg.reduce_fields(*st.moments(), region=reg)[3] / e0, wall / e0
+
+
+def test_chi_sweep_toward_the_critical_strength(oracle_lib):
+    """Type II on the 100 x 100 pulse, peak strength swept to 4/s - 0.001 (Sec. 4.1's
+    choice; Eq. criticalchi).  What the paper's analysis fixes along the sweep:
+
+    * every strength of the sweep removes the reflection: the interior energy left
+      after 300 steps is more than 50x below no layer (Figs. n3-n4);
+    * the energy that crosses the layer and reaches the wall falls by more than
+      10^4 from chi_max = 0.1 to 0.5, then rises monotonically toward the critical
+      strength.  The uniform mode's amplification per step in the layer,
+      lambda_0 = (1 + n chi - s n chi - chi)/(1 + n chi) (Eq. criticalchi's
+      closed form), vanishes at chi = 1/(n(s - 1) + 1) and reaches -1 at 4/s, the
+      edge of stability: approaching it, the layer damps each step less.  The
+      sweep's R therefore does not fall monotonically toward 4/s.
+
+    Planted in a copy of the oracle, a lost type II term or one of the wrong sign
+    fails it.  (The explicit reading of rho* passes here; the Von Neumann pins of
+    the critical strength catch it.)"""
+    sweep = wl.chi_sweep("f64")
+    s = float(sweep[0].s[0])
+    bare = sweep[0].with_(chi_x=np.zeros(100), chi_y=np.zeros(100), variant="none")
+    r_none, wall_none = _sweep_energies(oracle_lib, bare)
+    got = [_sweep_energies(oracle_lib, w) for w in sweep]
+    R = np.array([g[0] for g in got])
+    wall = np.array([g[1] for g in got])
+    assert np.all(R < r_none / 50), (R, r_none)
+    assert wall[0] < wall_none / 50 and wall[0] > 1e4 * wall[1], (wall, wall_none)
+    assert np.all(np.diff(wall[1:]) > 0), wall
+    lam0 = [(1 + 0.5 * c - s * 0.5 * c - c) / (1 + 0.5 * c) for c in (w.chi_max for w in sweep)]
+    assert np.all(np.diff(np.abs(lam0[1:])) > 0) and abs(lam0[-1] + 1) < 1e-3, lam0
+
+
+@pytest.mark.parametrize("rho0,uf", [(1.3, (0.0, 0.0)), (0.8, (0.08, 0.0))])
+@pytest.mark.parametrize("direction", [1, -1])
+def test_acoustic_energy_weights_by_equipartition(oracle_lib, rho0, uf, direction):
+    """The acoustic energy of the diagnostics, c_s^2 rho'^2/(2 rho0) + rho0|u - u0|^2/2,
+    pinned without restating it: a travelling sound wave carries equal potential and
+    kinetic energy (rho' = rho0 |u'|/c_s), and a single mode of the linearised
+    scheme (Sec. 3.2) loses energy exactly as |lambda|^2 per step.  The wave is the
+    right- or left-running eigenvector of G(k), k = 2 pi/64, seeded on a periodic
+    lattice (rho0 != 1, with and without mean flow).  Each term is taken alone by
+    zeroing the other field.  A wrong c_s^2, a dropped 1/2, rho0 in the wrong place
+    or |u| instead of |u - u0| breaks the balance by 20 % or more; the lattice's
+    own dispersion leaves 2e-3."""
+    from oracle import diagnostics as dg
+    from oracle import vonneumann as vn
+
+    N, eps, s = 64, 1e-6, 1.99
+    k = 2 * np.pi / N
+    J = vn.jacobian("none", vn.rates(s), 0.0, 0.5, 0.5, rho0, uf)
+    lam, V = np.linalg.eig(vn.amplification((k, 0.0), J))
+    want = -(uf[0] + direction / math.sqrt(3.0)) * k  # phase of exp(-i omega)
+    idx = int(np.argmin(np.abs(np.angle(lam) - want) + 10 * np.abs(np.abs(lam) - 1)))
+    seed = np.real(V[:, idx][:, None] * np.exp(1j * k * np.arange(N))[None, :])
+    seed *= eps / np.abs(seed.sum(0)).max()
+    prob = _prob(oracle_lib, N, 1, vn.rates(s), variant="none", bc="periodic", rho0=rho0, u0=uf,
+                 rho_f=rho0, u_f=uf)
+    st = oracle_lib.State(prob, np.full((1, N), rho0), uf[0], uf[1])
+    st.f[:] = oracle_lib.feq(rho0, *uf)[:, None, None] + seed[:, None, :]
+    r, ux, uy = st.moments()
+    rest_u = (np.full_like(r, uf[0]), np.full_like(r, uf[1]))
+    pot = dg.reduce_fields(r, *rest_u, rho0=rho0, u0=uf)[3]
+    kin = dg.reduce_fields(np.zeros_like(r), ux, uy, rho0=rho0, u0=uf)[3]
+    e0 = dg.reduce_fields(r, ux, uy, rho0=rho0, u0=uf)[3]
+    assert abs(pot / kin - 1) < 5e-3, (pot, kin)
+    assert e0 == pytest.approx(pot + kin, rel=1e-12)
+    st.run(2 * N)
+    e1 = dg.reduce_fields(*st.moments(), rho0=rho0, u0=uf)[3]
+    assert e1 / e0 == pytest.approx(abs(lam[idx]) ** (4 * N), rel=1e-7)
+
+
 def test_orszag_profile_normalisation():
     """Eq. (normalizedsigma): sigma~ vanishes at x0 and L and peaks at 1 at 0.8."""
     rows = dict((r[0], float(r[1])) for r in golden_rows("normalized_sigma.txt"))

@@ -199,6 +199,20 @@ def small_pulse(variant="II", storage="f64") -> Workload:
     return pulse_workload(100, 100, variant=variant, storage=storage, name="pulse-100x100")
 
 
+def chi_sweep(storage="f64", steps=300) -> list:
+    """The 100 x 100 pulse geometry (20-cell quadratic ramp, type II) with the peak
+    strength swept toward the critical value of Eq. criticalchi: chi_max = 0.1, 0.5,
+    1.0, 1.5, 1.9 and 4/s - 0.001 (the choice of Sec. 4.1), s = 1/(3 nu + 1/2)."""
+    base = pulse_workload(100, 100, variant="II", storage=storage, steps=steps,
+                          name="chi-sweep-100x100")
+    s = float(base.s[0])
+    out = []
+    for cm in (0.1, 0.5, 1.0, 1.5, 1.9, 4.0 / s - 0.001):
+        prof = ramp_profile(100, base.width, cm)
+        out.append(base.with_(chi_x=prof, chi_y=prof.copy(), chi_max=cm))
+    return out
+
+
 CHI_MAX_CHOICES = (0.01, 0.05, 0.2, 1.0)
 
 
