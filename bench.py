@@ -54,6 +54,8 @@ def parse():
                     help="skip the 256-lattice batched-versus-plain-loop measurement")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the 2048^2-16384^2 storage-format roofline sweep")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the error-against-the-oracle table (about 2 min of host CPU)")
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="seconds of the 200 jobs/s arrival trace to serve (0 skips)")
     return ap.parse_args()
@@ -332,16 +334,22 @@ def run_native(args):
     bytes_launch = BYTES_PER_CELL[works[0].storage] * works[0].cells
     peaks = measured_peaks()
     achieved = bytes_launch / per_launch / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(),
+    # the state of one solve (both buffers, 75.5 MB) stays in L2 across its steps:
+    # the ceiling is the L2-resident copy rate over that same working set
+    l2 = measure_l2_copy_peak(dev, bytes_launch // 2)
+    roof = {"bound": "l2", "achieved": achieved, "peak": l2["gbs"], "unit": "GB/s",
+            "frac": achieved / l2["gbs"], "traffic": profiled_traffic(),
             "kernel": STEP_KERNEL[lats[0].cells_per_thread],
             "cells_per_thread": lats[0].cells_per_thread,
             "bytes_per_launch": bytes_launch, "avg_launch_us": per_launch * 1e6,
-            "peak_source": peaks["source"],
+            "peak_source": "measured in this run: " + l2["method"],
+            "hbm_peak": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"],
+            "achieved_over_hbm_peak": achieved / peaks["hbm_gbs"],
             "working_set": "the 75.5 MB double-buffered state of a 1024x1024 solve stays in L2 "
-                           "across its steps (ncu: ~21 MB of DRAM traffic per launch), so the "
-                           "algorithmic rate can exceed the HBM copy peak; see roofline_large "
-                           "for the same kernel on a 4096x4096 lattice, larger than L2"}
+                           "across its steps (ncu: ~21 MB of DRAM traffic per launch against "
+                           "75.5 MB algorithmic), so the bound is L2, measured by a copy over the "
+                           "same working set; roofline_large gives the same kernel family on a "
+                           "4096x4096 lattice, larger than L2, against HBM"}
     # the same solves with the one-cell-per-thread kernel, for comparison
     one_cell = None
     if lats[0].cells_per_thread == 2:
@@ -384,6 +392,11 @@ def run_native(args):
     serving = None
     if args.serve_seconds > 0 and rank == 0:
         serving = run_serving(args.serve_seconds)
+    parity = comp = decay = None
+    if rank == 0 and not args.no_parity:
+        parity = run_parity()
+        comp = run_compensated_throughput()
+        decay = run_decay_exponent()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -401,6 +414,9 @@ def run_native(args):
             "d3q15": d3q15,
             "batched": batched,
             "serving": serving,
+            "parity": parity,
+            "compensated_arithmetic": comp,
+            "decay_exponent": decay,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -721,6 +737,189 @@ def run_roofline_sweep(peaks, sides=(2048, 4096, 8192, 16384), storages=("f32", 
                         "error case adds a centred eps=1e-3, b=5 pulse"}
 
 
+def measure_l2_copy_peak(dev, nbytes: int, copies: int = 64, reps: int = 30) -> dict:
+    """Copy bandwidth with the working set held in L2: two device buffers of
+    `nbytes` each, copied into one another alternately (a -> b, b -> a, as the
+    double-buffered step alternates), `copies` copies per captured CUDA graph;
+    the best of `reps` replays timed with CUDA events.  Bytes = read + write."""
+    import torch
+
+    a = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    st = torch.cuda.Stream(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        for _ in range(4):
+            b.copy_(a)
+            a.copy_(b)
+        st.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            for k in range(copies):
+                (b if k % 2 == 0 else a).copy_(a if k % 2 == 0 else b)
+        g.replay()
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            g.replay()
+            e1.record(st)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+    del g
+    return {"gbs": 2 * nbytes * copies / best / 1e9, "buffer_bytes": nbytes,
+            "method": f"torch copy between two {nbytes / 1e6:.1f} MB device buffers, alternating "
+                      f"direction, {copies} copies per CUDA graph replay, best of {reps} replays "
+                      "(CUDA events); bytes = read + write"}
+
+
+# Targets stated for the error against the FP64 oracle (relative L2 of rho').
+GATES = {"f32": 1e-5, "f16dev": 1e-2, "bf16dev": 1e-2}
+
+
+def run_parity():
+    """Measured error of the CUDA path against the FP64 oracle per workload,
+    beside the stated target: the 100 x 100 pulse (300 steps, types II / III),
+    the 1024 x 1024 Mach-0.2 workload over its full 5000 steps (types II / III;
+    type I diverges on both sides), and the 2048 x 2048 error case of the
+    storage sweep (200 steps).  FP32 storage with the FP32 collision (the
+    default) and with the compensated (float-float) collision."""
+    from oracle import core
+    from paper_1203_6350_gb300 import lbm
+
+    def oracle(w, steps):
+        prob = core.Problem(w.nx, w.ny, w.s, n=w.n, m=w.m, variant=w.variant, bc=w.bc,
+                            rho0=w.rho0, u0=w.u0, rho_f=w.rho_f, u_f=w.u_f, chi_x=w.chi_x,
+                            chi_y=w.chi_y)
+        return core.State(prob, *w.initial_fields()).run(steps).moments()[0]
+
+    def gpu(w, storage, arith, steps):
+        lat = with_warn(lambda: lbm.Lattice.from_workload(w, storage=storage))
+        try:
+            if arith == "compensated":
+                lat.arithmetic = "compensated"
+            lat.step(steps)
+            return lat.moments()[0]
+        finally:
+            lat.close()
+
+    cases = []
+
+    def add(config, w, storage, arith, steps, got, ref):
+        fin = bool(np.isfinite(ref).all())
+        rec = {"config": config, "variant": w.variant, "storage": storage, "arithmetic": arith,
+               "steps": steps}
+        if not fin:
+            rec.update({"oracle_finite": False, "gpu_finite": bool(np.isfinite(got).all())})
+            rec["status"] = "met" if not rec["gpu_finite"] else "missed"
+        else:
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            gate = GATES[storage]
+            rec.update({"rel_l2_rho": err, "gate": gate,
+                        "status": "met" if err <= gate else "missed"})
+        cases.append(rec)
+
+    for variant in ("II", "III"):
+        w = wl.small_pulse(variant, "f32")
+        ref = oracle(w, w.steps)
+        for arith in ("native", "compensated"):
+            add("100x100 pulse", w, "f32", arith, w.steps, gpu(w, "f32", arith, w.steps), ref)
+    for variant in ("II", "III"):
+        w = wl.mean_flow_pulse(seed=SEED, variant=variant, storage="f32")
+        ref = oracle(w, w.steps)
+        for arith in ("native", "compensated"):
+            add("1024x1024 Mach 0.2", w, "f32", arith, w.steps, gpu(w, "f32", arith, w.steps), ref)
+    w = wl.mean_flow_pulse(seed=SEED, variant="I", storage="f32", steps=1000)
+    add("1024x1024 Mach 0.2", w, "f32", "native", w.steps, gpu(w, "f32", "native", w.steps),
+        oracle(w, w.steps))
+    w = wl.quiescent(2048, storage="f32", steps=200, width=128, pulse=True)
+    ref = oracle(w, w.steps)
+    for storage in ("f32", "f16dev", "bf16dev"):
+        add("2048x2048 pulse", w, storage, "native", w.steps, gpu(w, storage, "native", w.steps),
+            ref)
+    add("2048x2048 pulse", w, "f32", "compensated", w.steps,
+        gpu(w, "f32", "compensated", w.steps), ref)
+    return {"gates": GATES, "measure": "relative L2 of rho' against the FP64 oracle",
+            "cases": cases,
+            "missed": [c for c in cases if c["status"] == "missed"]}
+
+
+def run_compensated_throughput(steps: int = 1000):
+    """MLUPS of the compensated (float-float) FP32 step beside the FP32 one-cell
+    kernel on the 1024 x 1024 Mach-0.2 workload (type II) and a 4096 x 4096
+    lattice."""
+    import torch
+
+    from paper_1203_6350_gb300 import lbm
+
+    out = {}
+    for name, w in (("1024x1024 Mach 0.2", wl.mean_flow_pulse(seed=SEED, variant="II")),
+                    ("4096x4096 pulse", wl.quiescent(4096, storage="f32", steps=steps,
+                                                     width=128, pulse=True))):
+        res = {}
+        for arith in ("native", "compensated"):
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                lat = with_warn(lambda: lbm.Lattice.from_workload(w, stream=stream, init="pulse"))
+                lat.cells_per_thread = 1
+                if arith == "compensated":
+                    lat.arithmetic = "compensated"
+                lat.step(16)
+                a = torch.cuda.Event(enable_timing=True)
+                z = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lat.step(steps)
+                z.record(stream)
+                z.synchronize()
+                lat.close()
+            res[arith] = w.cells * steps / (a.elapsed_time(z) / 1e3) / 1e6
+        out[name] = {"one_cell_fp32_mlups": res["native"], "compensated_mlups": res["compensated"],
+                     "ratio": res["compensated"] / res["native"]}
+    return out
+
+
+def run_decay_exponent():
+    """E1 of Sec. 4.1 through the CUDA path (FP32): the 200 x 200 pulse, b = 10
+    cells (1/20 of the domain), layer 4b with the Orszag profile and
+    chi = 4/s - 0.001, Re = 1e7, at rest and with u = (0.1, 0).  E_L2 every 10
+    steps from the library's FP64 diagnostics (sum rho'^2); the log-log slope
+    over [t_b, 3 t_b], t_b = (N/2)/c_s the time the front reaches the walls,
+    beside the oracle's slope and the paper's reported exponents."""
+    from oracle import core
+    from oracle import diagnostics as dg
+    from paper_1203_6350_gb300 import lbm
+
+    n = 200
+    t_b = int(round((n / 2) * math.sqrt(3.0)))
+    out = {}
+    for name, u0, paper in (("rest", (0.0, 0.0), -3.5), ("mean_flow_0.1", (0.1, 0.0), -3.0)):
+        w = wl.pulse_workload(n, n, variant="II", storage="f32", b=10.0, width=40, chi_max=0.0,
+                              nu=1e-7, u0=u0)
+        c = wl.orszag_profile(n, 40, 4 / w.s[0] - 0.001)
+        w = w.with_(chi_x=c, chi_y=c)
+        prob = core.Problem(w.nx, w.ny, w.s, variant=w.variant, u0=w.u0, u_f=w.u_f,
+                            chi_x=w.chi_x, chi_y=w.chi_y)
+        st = core.State(prob, *w.initial_fields())
+        ts, eg, eo = [], [], []
+        with with_warn(lambda: lbm.Lattice.from_workload(w)) as lat:
+            t = 0
+            while t < 3 * t_b:
+                lat.step(10)
+                st.run(10)
+                t += 10
+                ts.append(t)
+                eg.append(math.sqrt(lat.diagnostics()[4] / (n * n)))
+                eo.append(dg.e_l2(st.moments()[0]))
+        ts, eg, eo = np.array(ts, float), np.array(eg), np.array(eo)
+        sel = ts >= t_b
+        out[name] = {"gpu_slope": float(np.polyfit(np.log(ts[sel]), np.log(eg[sel]), 1)[0]),
+                     "oracle_slope": float(np.polyfit(np.log(ts[sel]), np.log(eo[sel]), 1)[0]),
+                     "paper_exponent": paper, "window_steps": [t_b, 3 * t_b],
+                     "e_l2_gpu_at_window": [float(eg[sel][0]), float(eg[-1])],
+                     "max_rel_diff_gpu_oracle": float(np.max(np.abs(eg - eo) / eo))}
+    return out
+
+
 def job_value(cells_per_step: float, steps: int, t_job: float, world: int) -> float:
     """Whole-job MLUPS: every rank runs the same replica workload, so the cell
     updates of all ranks over the slowest rank's time."""
@@ -832,9 +1031,8 @@ def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
 
 
 # Accuracy stated for the served jobs, as relative L2 of rho' against the FP64
-# oracle in units of the job's initial pulse: FP32 1e-5, 16-bit deviations 1e-2
-# (at pulse amplitude 1e-3).
-SERVE_TOL = {"f32": 1e-5, "f16dev": 1e-2, "bf16dev": 6e-2, "f64": 1e-10}
+# oracle's final field: FP32 1e-5, 16-bit deviations 1e-2 (at pulse amplitude 1e-3).
+SERVE_TOL = {"f32": 1e-5, "f16dev": 1e-2, "bf16dev": 1e-2, "f64": 1e-10}
 
 
 def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
@@ -890,13 +1088,14 @@ def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
             err = float(np.linalg.norm(got - ref))
             tol = SERVE_TOL[w.storage]
             rec.update({
-                # error in units of the initial pulse (the signal the job was given) and
-                # of the final field (which may have decayed by orders of magnitude)
+                # the stated measure: relative to the oracle's final field; the error
+                # in units of the initial pulse is context (the field may have decayed
+                # by orders of magnitude)
+                "rel_l2_rho": err / (float(np.linalg.norm(ref)) or 1.0),
                 "rel_l2_rho_vs_initial": err / (float(np.linalg.norm(rho_init)) or 1.0),
-                "rel_l2_rho_vs_final": err / (float(np.linalg.norm(ref)) or 1.0),
                 "final_over_initial": float(np.linalg.norm(ref)) / (float(np.linalg.norm(rho_init)) or 1.0),
-                "tolerance_vs_initial": tol})
-            rec["within_tolerance"] = rec["rel_l2_rho_vs_initial"] <= tol
+                "tolerance": tol})
+            rec["within_tolerance"] = rec["rel_l2_rho"] <= tol
         else:
             # an unstable configuration (type I with s + chi > 2, Eq. effectrelax) must
             # blow up on both sides

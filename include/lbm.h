@@ -223,6 +223,28 @@ int lbm_set_steps_per_launch(lbm_handle h, int steps);
 /* The current choice (LBM_ERR_ARG for a NULL handle). */
 int lbm_steps_per_launch(lbm_handle h);
 
+/* Arithmetic of the collision (Sec. 2, Eq. blbs-abc-1; the same step, only the
+ * rounding differs).  LBM_ARITH_NATIVE (the default): FP64 for LBM_F64
+ * storage, FP32 otherwise.  LBM_ARITH_COMPENSATED (LBM_F32 storage only):
+ * the populations stay FP32 in memory, but the collision runs in float-float
+ * arithmetic -- each value carried as an unevaluated sum of two FP32 numbers,
+ * each operation built from error-free FP32 transformations (Knuth's TwoSum,
+ * Dekker's Fast2Sum, a fused-multiply-add product) -- about 44 correct bits,
+ * so the only per-step rounding left is the FP32 store.  Where a field decays
+ * by orders of magnitude (an absorbed pulse) the FP32 collision's own
+ * roundings, ~10 per population per step, dominate its error against an
+ * FP64 reference; the compensated step removes them at several times the
+ * FP32 kernel's instruction count (still on FP32 pipes, far above GB300's
+ * FP64 rate).  It steps one cell, one time step per launch: while it is
+ * selected, lbm_set_cells_per_thread(h, 2), lbm_set_steps_per_launch(h, 2)
+ * and lbm_set_tma_staging(h, 1) return LBM_ERR_ARG; selecting it sets one
+ * cell and one step per launch.  LBM_ERR_ARG for other values or storage.
+ * Waits for the handle's stream.  lbm_get_arithmetic returns the current choice
+ * (LBM_ERR_ARG for a NULL handle). */
+typedef enum { LBM_ARITH_NATIVE = 0, LBM_ARITH_COMPENSATED = 1 } lbm_arithmetic;
+int lbm_set_arithmetic(lbm_handle h, lbm_arithmetic a);
+int lbm_get_arithmetic(lbm_handle h);
+
 /* Staging of the two-step launches' input by the Tensor Memory Accelerator.
  * With it (1), each 64 x 16 tile's input -- the nine planes of the 72 x 20
  * cells around it -- arrives in shared memory as one bulk tensor copy whose
@@ -233,10 +255,15 @@ int lbm_steps_per_launch(lbm_handle h);
  * population buffers together exceed four times the L2 size (the environment
  * variable LBM_TMA=0 or 1 at lbm_create overrides that choice); LBM_ERR_ARG
  * for other handles or values.  A staged copy that has not
- * completed after a bounded wait stops its CTA and makes the next
- * lbm_moments / lbm_diagnostics / lbm_get_state on the host return
- * LBM_ERR_CUDA.  Waits for the handle's stream.  lbm_tma_staging returns 1
- * or 0. */
+ * completed after a bounded wait (2^20 polls of its mbarrier) stops its CTA,
+ * which waits for that copy once more with a 16 times longer bound, and makes
+ * the next lbm_moments / lbm_diagnostics / lbm_get_state on the host return
+ * LBM_ERR_CUDA; the lattice's state is then undefined, the context stays
+ * usable.  Test hook: the environment variable LBM_TMA_WAIT_POLLS=<n> when
+ * staging is set up (lbm_create, lbm_set_tma_staging; lbm_batch_create for a
+ * batch) sets the first bound to n polls; n = 0 takes the give-up path at
+ * every tile with every copy still completing.  Waits for the handle's
+ * stream.  lbm_tma_staging returns 1 or 0. */
 int lbm_set_tma_staging(lbm_handle h, int on);
 int lbm_tma_staging(lbm_handle h);
 
@@ -253,6 +280,16 @@ int lbm_set_source(lbm_handle h, double amplitude, double omega, double phase);
 
 /* Free the device buffers and the handle.  NULL is allowed. */
 void lbm_destroy(lbm_handle h);
+
+/* Device bytes an nx x ny lattice of this storage and boundary holds through
+ * its allocator at most: both population buffers, the per-axis absorbing
+ * tables, the diagnostics partials, the step counter, the line-source table
+ * (LBM_BC_CHANNEL), the TMA error flag (LBM_F32 with LBM_BC_DIRICHLET_EQ) and,
+ * with host_io = 1, the FP64 staging of three fields that the first
+ * host-memory lbm_init_equilibrium or lbm_moments allocates.  CUDA graphs
+ * and tensor maps live outside the allocator and are not counted.  For
+ * admission control; 0 for invalid arguments.  No CUDA call. */
+size_t lbm_lattice_bytes(int nx, int ny, lbm_storage storage, lbm_bc bc, int host_io);
 
 /* Message of the last non-zero return on h (h = NULL: of the last
  * lbm_create that failed).  Owned by the library. */

@@ -19,6 +19,7 @@
 // The linear equilibrium has moments rho, j, -rho, rho, -7/3 j and zeros.
 // Back-transform g = M^T D^-1 m (M's rows are orthogonal, D = diag(M M^T)).
 // Both transforms run as butterflies over the axis pairs and the diagonals.
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -213,8 +214,17 @@ __device__ __forceinline__ void d3_collide(CT (&g)[kQ], CT chi, const D3Const<CT
 #pragma unroll
         for (int r = 0; r < kQ; ++r) post[r] += chi * (k.dmlf[r] - lin[r]);
     }
+    // rows 0-3 (rho', j'): a correctly rounded 1/D, since 15 fl(1/15) and
+    // 10 fl(1/10) differ from 1 by 5.2e-8 and 1.5e-8 in FP32 and would scale the
+    // conserved deviations by that every step (the residual is 0 in FP64)
 #pragma unroll
-    for (int r = 0; r < kQ; ++r) post[r] *= CT(1.0 / d3norm(r));
+    for (int r = 0; r < 4; ++r) {
+        constexpr bool f32 = std::is_same<CT, float>::value;
+        const CT lo = CT(f32 ? 1.0 / d3norm(r) - double(float(1.0 / d3norm(r))) : 0.0);
+        post[r] = fma(post[r], CT(1.0 / d3norm(r)), post[r] * lo);
+    }
+#pragma unroll
+    for (int r = 4; r < kQ; ++r) post[r] *= CT(1.0 / d3norm(r));
     d3_backward(post, g);
 }
 

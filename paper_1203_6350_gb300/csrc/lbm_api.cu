@@ -41,6 +41,8 @@ struct lbm_ctx {
     StepConst<double> k64{};
     StepConst<float> k32{};
     StepConst<lbm::F2> k2{};          // the FP32 constants, duplicated for the pair kernel
+    StepConst<lbm::FF> kff{};         // float-float constants of the compensated step
+    int arith = LBM_ARITH_NATIVE;     // LBM_ARITH_COMPENSATED: FP32 storage, float-float collision
     int cpt = 1;                      // cells per thread of the step kernel: 1, or 2 (FP32 / 16-bit)
     int spl = 1;                      // time steps per launch: 1, or 2 (needs cpt == 2)
     lbm::LineSource src{};            // channel boundary: the line source (amp 0 until lbm_set_source)
@@ -56,6 +58,7 @@ struct lbm_ctx {
     CUtensorMap tmap[2];              // tensor maps of buf[0], buf[1]
     int tma_grid = 0;                 // persistent CTAs of the TMA kernel
     int* tma_err = nullptr;           // set on the device when a staged copy timed out
+    int tma_polls = -1;               // polls of each staged copy's wait (< 0: default)
     cudaStream_t capture_stream = nullptr;
     std::string err;
 };
@@ -124,6 +127,7 @@ void refresh_consts(lbm_ctx* h) {
     fill_const<double>(h, h->k64);
     fill_const<float>(h, h->k32);
     fill_const<lbm::F2>(h, h->k2);
+    fill_const<lbm::FF>(h, h->kff);
 }
 
 int ensure_staging(lbm_ctx* h) {
@@ -214,6 +218,8 @@ cudaError_t launch_one_step(lbm_ctx* h, const void* src, void* dst, cudaStream_t
     const lbm::LineSource ls = launch_source(h, t_off);
     const auto* tx = static_cast<const lbm::AxisCoef<float>*>(h->chi_x);
     const auto* ty = static_cast<const lbm::AxisCoef<float>*>(h->chi_y);
+    if (h->arith == LBM_ARITH_COMPENSATED)
+        return lbm::launch_step_ff(src, dst, h->geo, h->kff, tx, ty, h->variant, h->bc, st, p, ls);
     if (h->cpt == 2) {
         switch (h->storage) {
             case LBM_F32: return lbm::launch_step2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p, ls);
@@ -245,7 +251,8 @@ cudaError_t launch_two_steps(lbm_ctx* h, const void* src, void* dst, cudaStream_
     const auto* ty = static_cast<const lbm::AxisCoef<float>*>(h->chi_y);
     if (h->tma)
         return lbm::launch_step_tb2_tma_f32(h->tmap[src == h->buf[0] ? 0 : 1], dst, h->geo, h->k2,
-                                            tx, ty, h->variant, h->tma_grid, h->tma_err, st, p);
+                                            tx, ty, h->variant, h->tma_grid, h->tma_err, st, p,
+                                            h->tma_polls);
     switch (h->storage) {
         case LBM_F32: return lbm::launch_step_tb2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
         case LBM_F16DEV: return lbm::launch_step_tb2_f16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
@@ -276,6 +283,7 @@ int setup_tma(lbm_ctx* h) {
         if (e != cudaSuccess) return cuda_fail(h, e, "TMA error flag");
     }
     h->tma_grid = per_sm * sms;
+    h->tma_polls = lbm::tma_wait_polls();
     h->tma_ready = true;
     return LBM_OK;
 }
@@ -335,6 +343,23 @@ cudaError_t ensure_graph(lbm_ctx* h, int parity) {
 extern "C" {
 
 const char* lbm_version(void) { return "liblbm 0.1 (D2Q9 MRT + absorbing layers, sm_103a)"; }
+
+size_t lbm_lattice_bytes(int nx, int ny, lbm_storage storage, lbm_bc bc, int host_io) {
+    if (nx < 1 || ny < 1 || storage < LBM_F64 || storage > LBM_BF16DEV || bc < LBM_BC_DIRICHLET_EQ ||
+        bc > LBM_BC_CHANNEL || (host_io != 0 && host_io != 1))
+        return 0;
+    // the allocations of lbm_create, setup_tma and ensure_staging, in that order
+    const size_t es = lbm::storage_bytes(storage);
+    const size_t per_row = (static_cast<size_t>(nx) * es + 127) / 128 * 128 / es;
+    const size_t cts = storage == LBM_F64 ? 8 : 4;
+    size_t bytes = 2 * 9 * per_row * static_cast<size_t>(ny) * es;
+    bytes += static_cast<size_t>(nx + ny) * 4 * cts;
+    bytes += sizeof(double) * (lbm::kDiagBlocks * lbm::kDiag + lbm::kDiag) + 256;
+    if (bc == LBM_BC_CHANNEL) bytes += kGraphChunk * (sizeof(double) + 9 * sizeof(float));
+    if (storage == LBM_F32 && bc == LBM_BC_DIRICHLET_EQ) bytes += 256;
+    if (host_io) bytes += 3 * sizeof(double) * static_cast<size_t>(nx) * ny;
+    return bytes;
+}
 
 const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
@@ -725,6 +750,8 @@ int lbm_set_cells_per_thread(lbm_handle h, int cells) {
     if (cells != 1 && cells != 2) return fail(h, LBM_ERR_ARG, "cells per thread must be 1 or 2");
     if (cells == 2 && !pair_kernel_ok(h))
         return fail(h, LBM_ERR_ARG, "two cells per thread needs FP32 or 16-bit storage and 9 planes below 2^32 elements");
+    if (cells == 2 && h->arith == LBM_ARITH_COMPENSATED)
+        return fail(h, LBM_ERR_ARG, "compensated arithmetic steps one cell per thread");
     if (cells != h->cpt) {
         DeviceGuard dg(h->device);
         cudaStreamSynchronize(h->stream);
@@ -753,10 +780,33 @@ int lbm_set_steps_per_launch(lbm_handle h, int steps) {
 
 int lbm_steps_per_launch(lbm_handle h) { return h ? h->spl : LBM_ERR_ARG; }
 
+int lbm_set_arithmetic(lbm_handle h, lbm_arithmetic a) {
+    if (!h) return LBM_ERR_ARG;
+    if (a != LBM_ARITH_NATIVE && a != LBM_ARITH_COMPENSATED)
+        return fail(h, LBM_ERR_ARG, "arithmetic must be LBM_ARITH_NATIVE or LBM_ARITH_COMPENSATED");
+    if (a == LBM_ARITH_COMPENSATED && h->storage != LBM_F32)
+        return fail(h, LBM_ERR_ARG, "compensated arithmetic needs LBM_F32 storage");
+    if (a == h->arith) return LBM_OK;
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);  // the captured launches name the other kernel
+    h->arith = a;
+    if (a == LBM_ARITH_COMPENSATED) {  // one cell, one step per launch
+        h->cpt = 1;
+        h->spl = 1;
+        h->tma = false;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_arithmetic(lbm_handle h) { return h ? h->arith : LBM_ERR_ARG; }
+
 int lbm_set_tma_staging(lbm_handle h, int on) {
     if (!h) return LBM_ERR_ARG;
     if (on != 0 && on != 1) return fail(h, LBM_ERR_ARG, "on must be 0 or 1");
     if (on == (h->tma ? 1 : 0)) return LBM_OK;
+    if (on && h->arith == LBM_ARITH_COMPENSATED)
+        return fail(h, LBM_ERR_ARG, "compensated arithmetic steps one cell, one step per launch");
     DeviceGuard dg(h->device);
     if (on) {
         const int rc = setup_tma(h);

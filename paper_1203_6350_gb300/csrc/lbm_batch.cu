@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     batch_tb2_tma_kernel(const BatchInst<F2>* __restrict__ insts,
                          const CUtensorMap* __restrict__ maps, const BatchTile* __restrict__ tiles,
                          const int* __restrict__ table, const long long* __restrict__ counters,
-                         int step_off, int launch_off, int* __restrict__ err) {
+                         int step_off, int launch_off, int* __restrict__ err, int polls) {
     extern __shared__ __align__(128) unsigned char tma_raw[];
     float* box = reinterpret_cast<float*>(tma_raw);
     float* r1 = reinterpret_cast<float*>(tma_raw + kTmaBoxBytes);
@@ -416,12 +416,12 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         float* dst = static_cast<float*>(sd.buf[1 - parity]);
         const int x0 = tile.x0, y0 = tile.y0;
         if (mode == 1) {
-            const bool ok = mbar_wait(bar, phase);
+            const bool ok = mbar_wait(bar, phase, polls);
             phase ^= 1u;
             if (!__syncthreads_and(ok)) {  // the whole CTA stops together
                 cp_async_wait_all();
                 if (tid == 0) {
-                    mbar_wait(bar, phase ^ 1u);  // the copy in flight, once more (bounded)
+                    mbar_wait(bar, phase ^ 1u, kTmaDrainPolls);  // the copy in flight
                     atomicExch(err, 1);
                 }
                 return;
@@ -523,14 +523,14 @@ size_t batch_smem(int spl) {
 inline cudaError_t launch_tb2_tma_class(int c, cudaLaunchConfig_t cfg, const BatchInst<F2>* insts,
                                         const CUtensorMap* maps, const BatchTile* tiles,
                                         const int* table, const long long* counters, int step_off,
-                                        int launch_off, int* err, int grid) {
+                                        int launch_off, int* err, int grid, int polls) {
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kTmaThreads);
     cfg.dynamicSmemBytes = batch_tma_smem_bytes();
 #define LBM_TB2_TMA_CLASS(V)                                                                  \
     if (c == batch_class(V, kDirichlet))                                                      \
         return cudaLaunchKernelEx(&cfg, batch_tb2_tma_kernel<V>, insts, maps, tiles, table,   \
-                                  counters, step_off, launch_off, err);
+                                  counters, step_off, launch_off, err, polls);
     LBM_TB2_TMA_CLASS(kNone)
     LBM_TB2_TMA_CLASS(kTypeI)
     LBM_TB2_TMA_CLASS(kTypeII)
@@ -593,6 +593,7 @@ struct BatchTma {
     const CUtensorMap* maps = nullptr;
     int* err = nullptr;
     int grid = 0;
+    int polls = kTmaPolls;  // each tile's wait for its staged copy
 };
 
 template <typename T>
@@ -619,7 +620,8 @@ cudaError_t launch_batch_t(const void* insts, const BatchTile* tiles, const int*
             const bool staged = std::is_same<T, float>::value && tma.maps && c < 5;
             const cudaError_t e =
                 staged ? launch_tb2_tma_class(c, cfg, ip2, tma.maps, tiles, ntiles, counters,
-                                              step_off, launch_off, tma.err, tma.grid)
+                                              step_off, launch_off, tma.err, tma.grid,
+                                              tma.polls)
                        : launch_tb2_class<T>(c, cfg, ip2, tiles, ntiles, counters, step_off,
                                              launch_off);
             if (e != cudaSuccess) return e;
@@ -725,6 +727,7 @@ struct lbm_batch_ctx {
     size_t maps_cap = 0;            // entries
     std::vector<CUtensorMap> h_maps;
     int* d_tma_err = nullptr;
+    int tma_polls = lbm::kTmaPolls;  // each staged copy's wait (LBM_TMA_WAIT_POLLS overrides)
     // buffers of removed instances, freed once the launches issued before the
     // removal have completed (their event), so that removal never waits
     struct Retired {
@@ -867,7 +870,8 @@ cudaError_t launch_batch(lbm_batch_ctx* b, cudaStream_t st, int steps, int step_
             return lbm::launch_batch_t<float>(
                 b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters, step_off, launch_off, tx, ty,
                 b->grid, b->cpt, spl, st, pdl, b->class_mask,
-                lbm::BatchTma{b->tma ? b->d_maps : nullptr, b->d_tma_err, b->tma_grid});
+                lbm::BatchTma{b->tma ? b->d_maps : nullptr, b->d_tma_err, b->tma_grid,
+                              b->tma_polls});
         case LBM_F16DEV:
             return lbm::launch_batch_t<__half>(b->d_insts, b->d_tiles, b->d_ntiles, b->d_counters,
                                                step_off, launch_off, tx, ty, b->grid, b->cpt, spl,
@@ -1147,6 +1151,8 @@ int lbm_batch_create(lbm_storage storage, void* cuda_stream, const lbm_allocator
             cudaStreamSynchronize(b->stream) == cudaSuccess) {
             b->tma = true;
             b->tma_grid = per_sm * sms;
+            const int polls = lbm::tma_wait_polls();
+            if (polls >= 0) b->tma_polls = polls;
         }
         cudaGetLastError();
     }

@@ -31,6 +31,20 @@ inline bool canary_requested() {
     const char* c = std::getenv("LBM_CANARY");
     return c && !std::strcmp(c, "1");
 }
+// The bounded wait of the TMA-staged kernels, a test hook (environment
+// variable LBM_TMA_WAIT_POLLS=<n> when a lattice's staging is set up or a batch
+// is created): each tile's wait for its staged copy gives up after n polls of
+// the mbarrier instead of the default 2^20, so that n = 0 exercises the
+// give-up path (the CTA stops, drains its copy, raises the error flag) without
+// any copy failing.  Returns -1 (the default) when unset or not a number >= 0.
+inline int tma_wait_polls() {
+    const char* c = std::getenv("LBM_TMA_WAIT_POLLS");
+    if (!c || !*c) return -1;
+    char* end = nullptr;
+    const long v = std::strtol(c, &end, 10);
+    return (*end == '\0' && v >= 0 && v <= (1l << 30)) ? static_cast<int>(v) : -1;
+}
+
 // `rows` rows of `pitch` elements of `elem` bytes from `buf`, back to back.
 inline cudaError_t paint_canary(void* buf, size_t elem, long long nx, long long pitch,
                                 long long rows, cudaStream_t st) {

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -27,6 +28,14 @@ struct alignas(8) F2 {
     unsigned long long u;
 };
 
+// A float-float value h + l (|l| <= half an ulp of h): about 48 significant
+// bits carried in two FP32 registers, for the compensated-arithmetic step
+// (FP32 storage, collision in float-float; GB300's FP32 pipes are many times
+// faster than its FP64 ones).
+struct FF {
+    float h, l;
+};
+
 // Host-side conversion of an FP64 constant to the compute type.
 template <typename CT>
 inline CT to_ct(double v) {
@@ -38,6 +47,12 @@ inline F2 to_ct<F2>(double v) {
     unsigned w;
     std::memcpy(&w, &f, sizeof w);
     return F2{(static_cast<unsigned long long>(w) << 32) | w};
+}
+
+template <>
+inline FF to_ct<FF>(double v) {
+    const float h = static_cast<float>(v);
+    return FF{h, static_cast<float>(v - static_cast<double>(h))};
 }
 
 // Per-lattice constants of the step, in the compute type CT (double for FP64
@@ -58,6 +73,7 @@ struct StepConst {
     CT keep[9];       // (1 - s_k) / D_k
     CT take[9];       // s_k / D_k (negated for rows 5, 6)
     CT dinv[9];       // 1 / D_k
+    CT dinv_lo[3];    // 1 / D_k - dinv[k] of the conserved rows, so that their scaling is unbiased
     CT rho0, jx0, jy0;
     CT jx0_2, jy0_2;  // 2 j0
     CT njj0;          // -|j0|^2
@@ -109,6 +125,15 @@ inline StepConst<CT> make_step_const(const double* s, double n, double m, double
         k.keep[i] = to_ct<CT>((1.0 - s[i]) / D[i]);
         k.take[i] = to_ct<CT>(sign * s[i] / D[i]);
         k.dinv[i] = to_ct<CT>(1.0 / D[i]);
+    }
+    // 9 fl(1/9) and 6 fl(1/6) differ from 1 by 7.5e-9 and 3.0e-8 in FP32: applied
+    // every step to rho' and j', that drift grows linearly in time.  The residual
+    // makes a_k = m_k / D_k of rows 0-2 correctly rounded (zero in FP64).
+    for (int i = 0; i < 3; ++i) {
+        const float hi = static_cast<float>(1.0 / D[i]);
+        k.dinv_lo[i] = to_ct<CT>(std::is_same<CT, double>::value || std::is_same<CT, FF>::value
+                                     ? 0.0
+                                     : 1.0 / D[i] - hi);
     }
     const double jx0 = rho0 * ux0, jy0 = rho0 * uy0;
     k.rho0 = to_ct<CT>(rho0);
@@ -199,6 +224,10 @@ cudaError_t launch_step_f32(const void* src, void* dst, const Geometry& g,
                             const StepConst<float>& k, const AxisCoef<float>* tx,
                             const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
                             int pdl, const LineSource& ls);
+// FP32 storage, collision in float-float (compensated arithmetic).
+cudaError_t launch_step_ff(const void* src, void* dst, const Geometry& g, const StepConst<FF>& k,
+                           const AxisCoef<float>* tx, const AxisCoef<float>* ty, int variant,
+                           int bc, cudaStream_t st, int pdl, const LineSource& ls);
 cudaError_t launch_step_f16(const void* src, void* dst, const Geometry& g,
                             const StepConst<float>& k, const AxisCoef<float>* tx,
                             const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
@@ -238,11 +267,12 @@ cudaError_t launch_step_tb2_bf16(const void* src, void* dst, const Geometry& g,
 // Two steps per launch with the tile's input staged by TMA (FP32, Dirichlet):
 // src_map describes the buffer holding time t (extent nx x ny x 9 planes,
 // box 72 x 20 x 9 floats); a persistent grid of `grid` CTAs; *err is set when
-// a copy did not complete within the bounded wait.
+// a copy did not complete within the bounded wait of `polls` mbarrier polls
+// (< 0: the default bound).
 cudaError_t launch_step_tb2_tma_f32(const CUtensorMap& src_map, void* dst, const Geometry& g,
                                    const StepConst<F2>& k, const AxisCoef<float>* tx,
                                    const AxisCoef<float>* ty, int variant, int grid, int* err,
-                                   cudaStream_t st, int pdl);
+                                   cudaStream_t st, int pdl, int polls);
 // Shared-memory attributes of the TMA kernels; per_sm receives CTAs per SM.
 cudaError_t prepare_step_tb2_tma_f32(int* per_sm);
 // The tensor map of one FP32 population buffer for the TMA kernel; false when

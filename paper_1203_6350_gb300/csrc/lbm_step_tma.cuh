@@ -14,9 +14,10 @@
 //    tb2_tile.  The copy of the next tile is issued as soon as step one has
 //    read the box, so it overlaps step two.  Two CTAs of 320 threads per SM
 //    (96 KB of shared memory each) overlap one another's waits.
-//  - Every wait on the mbarrier gives up after a bounded number of polls; the
-//    CTA then agrees (a barrier vote) to stop, waits once more (bounded) for
-//    its copy in flight, records the failure in *err and returns.
+//  - Every wait on the mbarrier gives up after a bounded number of polls
+//    (`polls`, kTmaPolls by default); the CTA then agrees (a barrier vote) to
+//    stop, waits for its copy in flight with a bound 16 times longer, records
+//    the failure in *err and returns.
 #pragma once
 
 #include <cuda.h>
@@ -31,6 +32,7 @@ constexpr int kTmaH = kTbH + 4;             // 20: y0 - 2 .. y0 + 17
 constexpr int kTmaPlane = kTmaW * kTmaH;    // elements per plane of the staged box
 constexpr unsigned kTmaBoxBytes = 9u * kTmaPlane * sizeof(float);
 constexpr int kTmaPolls = 1 << 20;          // mbarrier polls before a wait gives up
+constexpr int kTmaDrainPolls = 16 * kTmaPolls;  // the copy in flight, after a give-up
 // 10 warps, two CTAs (96 KB each) per SM: step one's 612 pairs and step
 // two's 512 then take two rounds each at 96 % and 80 % use (256 threads need
 // three rounds for step one; 384 leave a half-empty second round in both).
@@ -64,9 +66,10 @@ __device__ __forceinline__ void tma_box_load(float* dst, const CUtensorMap* map,
         : "memory");
 }
 
-// Poll the barrier's phase `parity` at most kTmaPolls times.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int i = 0; i < kTmaPolls; ++i) {
+// Poll the barrier's phase `parity` at most `polls` times.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          int polls = kTmaPolls) {
+    for (int i = 0; i < polls; ++i) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                         int nx, int ny, int pitch, unsigned plane, StepConst<F2> k,
                         const AxisCoef<float>* __restrict__ tx,
                         const AxisCoef<float>* __restrict__ ty, int ntx, int ntiles,
-                        int* __restrict__ err) {
+                        int* __restrict__ err, int polls) {
     extern __shared__ __align__(128) unsigned char tma_raw[];
     float* box = reinterpret_cast<float*>(tma_raw);
     float* r1 = reinterpret_cast<float*>(tma_raw + kTmaBoxBytes);
@@ -103,11 +106,11 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     unsigned parity = 0;
     for (; t < ntiles; t += G) {
         const int x0 = (t % ntx) * kTbW, y0 = (t / ntx) * kTbH;
-        const bool ok = mbar_wait(bar, parity);
+        const bool ok = mbar_wait(bar, parity, polls);
         parity ^= 1u;
         if (!__syncthreads_and(ok)) {  // the whole CTA stops together
             if (tid == 0) {
-                mbar_wait(bar, parity ^ 1u);  // the copy in flight, once more (bounded)
+                mbar_wait(bar, parity ^ 1u, kTmaDrainPolls);  // the copy in flight
                 atomicExch(err, 1);
             }
             return;
@@ -158,11 +161,13 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 }
 
 // Launch two steps (the buffer behind src_map holds time t, dst receives
-// t + 2) on a persistent grid of `grid` CTAs; pdl as for the one-step kernels.
+// t + 2) on a persistent grid of `grid` CTAs; pdl as for the one-step kernels;
+// polls < 0 selects kTmaPolls for each tile's wait.
 inline cudaError_t launch_step_tb2_tma(const CUtensorMap& src_map, float* dst, const Geometry& g,
                                        const StepConst<F2>& k, const AxisCoef<float>* tx,
                                        const AxisCoef<float>* ty, int variant, int grid,
-                                       int* err, cudaStream_t st, int pdl) {
+                                       int* err, cudaStream_t st, int pdl, int polls) {
+    if (polls < 0) polls = kTmaPolls;
     if (9 * g.plane >= (1ll << 32)) return cudaErrorInvalidValue;
     const int ntx = (g.nx + kTbW - 1) / kTbW, nty = (g.ny + kTbH - 1) / kTbH;
     const int ntiles = ntx * nty;
@@ -181,7 +186,7 @@ inline cudaError_t launch_step_tb2_tma(const CUtensorMap& src_map, float* dst, c
 #define LBM_TMA_CASE(V)                                                                          \
     if (variant == V)                                                                            \
         return cudaLaunchKernelEx(&cfg, step_tb2_tma_kernel<V>, src_map, dst, g.nx, g.ny, pitch, \
-                                  plane, k, tx, ty, ntx, ntiles, err);
+                                  plane, k, tx, ty, ntx, ntiles, err, polls);
     LBM_TMA_CASE(kNone)
     LBM_TMA_CASE(kTypeI)
     LBM_TMA_CASE(kTypeII)

@@ -21,9 +21,9 @@ cudaError_t launch_step_tb2_f32(const void* src, void* dst, const Geometry& g,
 cudaError_t launch_step_tb2_tma_f32(const CUtensorMap& src_map, void* dst, const Geometry& g,
                                    const StepConst<F2>& k, const AxisCoef<float>* tx,
                                    const AxisCoef<float>* ty, int variant, int grid, int* err,
-                                   cudaStream_t st, int pdl) {
+                                   cudaStream_t st, int pdl, int polls) {
     return launch_step_tb2_tma(src_map, static_cast<float*>(dst), g, k, tx, ty, variant, grid, err,
-                               st, pdl);
+                               st, pdl, polls);
 }
 
 cudaError_t prepare_step_tb2_tma_f32(int* per_sm) { return prepare_step_tb2_tma(per_sm); }

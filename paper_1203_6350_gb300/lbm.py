@@ -34,6 +34,8 @@ STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
 VARIANT = {"none": 0, "I": 1, "II": 2, "III": 3, "viscous": 4}
 BC = {"dirichlet": 0, "periodic": 1, "channel": 2}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+ARITHMETIC = {"native": 0, "compensated": 1}
+ARITHMETIC_NAMES = {v: k for k, v in ARITHMETIC.items()}
 
 
 class lbm_rates(ctypes.Structure):
@@ -84,6 +86,8 @@ SIGNATURES = [
     ("lbm_cells_per_thread", ctypes.c_int, [_vp]),
     ("lbm_set_steps_per_launch", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_steps_per_launch", ctypes.c_int, [_vp]),
+    ("lbm_set_arithmetic", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_get_arithmetic", ctypes.c_int, [_vp]),
     ("lbm_set_tma_staging", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_tma_staging", ctypes.c_int, [_vp]),
     ("lbm_destroy", None, [_vp]),
@@ -94,6 +98,8 @@ SIGNATURES = [
                                                ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]),
     ("lbm_batch_instance_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("lbm_lattice_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int]),
     ("lbm_batch_create", ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(lbm_allocator),
                                         ctypes.POINTER(_vp)]),
     ("lbm_batch_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -275,6 +281,14 @@ def lbm_steps_per_launch(h) -> int:
     return load().lbm_steps_per_launch(h)
 
 
+def lbm_set_arithmetic(h, arithmetic) -> int:
+    return load().lbm_set_arithmetic(h, int(arithmetic))
+
+
+def lbm_get_arithmetic(h) -> int:
+    return load().lbm_get_arithmetic(h)
+
+
 def lbm_set_tma_staging(h, on) -> int:
     return load().lbm_set_tma_staging(h, int(on))
 
@@ -371,6 +385,10 @@ def lbm3_last_error(h) -> str:
 
 def lbm_batch_instance_bytes(nx, ny, storage) -> int:
     return int(load().lbm_batch_instance_bytes(int(nx), int(ny), int(storage)))
+
+
+def lbm_lattice_bytes(nx, ny, storage, bc, host_io) -> int:
+    return int(load().lbm_lattice_bytes(int(nx), int(ny), int(storage), int(bc), int(host_io)))
 
 
 def lbm_batch_create(storage, stream=None, alloc: Optional[lbm_allocator] = None):
@@ -662,6 +680,16 @@ class Lattice:
     @cells_per_thread.setter
     def cells_per_thread(self, cells: int) -> None:
         check(lbm_set_cells_per_thread(self.h, cells), self.h, "lbm_set_cells_per_thread")
+
+    @property
+    def arithmetic(self) -> str:
+        """"native" (FP32 collision for FP32/16-bit storage, FP64 for FP64) or
+        "compensated" (FP32 storage, float-float collision)."""
+        return ARITHMETIC_NAMES[check(lbm_get_arithmetic(self.h), self.h, "lbm_get_arithmetic")]
+
+    @arithmetic.setter
+    def arithmetic(self, name: str) -> None:
+        check(lbm_set_arithmetic(self.h, ARITHMETIC[name]), self.h, "lbm_set_arithmetic")
 
     @property
     def steps_per_launch(self) -> int:

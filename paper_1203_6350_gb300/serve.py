@@ -44,6 +44,7 @@ class Job:
     result: Optional[np.ndarray] = None   # lbm diagnostics over the layer-free interior
     field: Optional[np.ndarray] = None    # final rho' (when the server keeps fields)
     error: Optional[str] = None           # why the job failed (None: it did not)
+    charged: int = 0                      # device bytes counted against the budget while resident
 
     @property
     def latency(self) -> Optional[float]:
@@ -51,8 +52,16 @@ class Job:
 
     @property
     def bytes(self) -> int:
+        """Device bytes of the job as a batch instance."""
         w = self.workload
         return lbm.lbm_batch_instance_bytes(w.nx, w.ny, lbm.STORAGE[w.storage])
+
+    def lattice_bytes(self, host_io: bool) -> int:
+        """Device bytes of the job as a single lattice (its own diagnostics
+        buffers and flags, and with host_io the FP64 staging of host transfers)."""
+        w = self.workload
+        return lbm.lbm_lattice_bytes(w.nx, w.ny, lbm.STORAGE[w.storage], lbm.BC[w.bc],
+                                     1 if host_io else 0)
 
 
 def interior(w):
@@ -126,21 +135,33 @@ class Server:
                                           tiling=self.tiling, config=cfg)
         return self.batches[storage]
 
+    def _solo(self, job: Job) -> bool:
+        return self.solo_cells is not None and job.workload.cells >= self.solo_cells
+
+    def charge(self, job: Job) -> int:
+        """Device bytes the job holds while resident: a single lattice (with the
+        staging of host transfers when fields are uploaded or read back) or a
+        batch instance, by the path its size selects."""
+        if self._solo(job):
+            return job.lattice_bytes(self.init == "fields" or bool(self.keep_fields))
+        return job.bytes
+
     def submit(self, job: Job) -> None:
-        if job.bytes > self.budget:
-            raise ValueError(f"job {job.id} needs {job.bytes} bytes, more than the budget")
+        need = self.charge(job)
+        if need > self.budget:
+            raise ValueError(f"job {job.id} needs {need} bytes, more than the budget")
         self.pending.append(job)
 
     def admit(self, now: float) -> int:
         n = 0
-        while self.pending and self.used + self.pending[0].bytes <= self.budget:
+        while self.pending and self.used + self.charge(self.pending[0]) <= self.budget:
             if (self.max_cells is not None and self.resident
                     and self.cells >= self.max_cells):
                 break
             job = self.pending.popleft()
             w = job.workload
             try:
-                if self.solo_cells is not None and w.cells >= self.solo_cells:
+                if self._solo(job):
                     # created and initialised on the side stream (lbm_create waits
                     # for its stream), then handed to the stepping stream
                     lat = lbm.Lattice.from_workload(w, init=self.init, stream=self.side,
@@ -158,7 +179,8 @@ class Server:
                 job.finished = now
                 self.done.append(job)
                 continue
-            self.used += job.bytes
+            job.charged = self.charge(job)
+            self.used += job.charged
             self.cells += w.cells
             self.admitted += 1
             job.admitted = now
@@ -203,7 +225,7 @@ class Server:
             if job.result[5] > 0:
                 job.error = (f"non-finite rho' or u in {int(job.result[5])} cells of the "
                              "read-out region")
-            self.used -= job.bytes
+            self.used -= job.charged
             self.cells -= job.workload.cells
             job.finished = clock()
             self.done.append(job)

@@ -21,10 +21,15 @@ def run_oracle(w, steps=None, nthreads=0):
 
 
 def run_gpu(w, storage=None, steps=None):
-    """CUDA-library fields (rho', ux, uy) of workload w after `steps`."""
+    """CUDA-library fields (rho', ux, uy) of workload w after `steps`.  storage
+    "f32c": FP32 storage with the compensated (float-float) collision."""
     from paper_1203_6350_gb300 import lbm
 
-    with lbm.Lattice.from_workload(w, storage=storage) as lat:
+    storage = storage or w.storage
+    comp = storage == "f32c"
+    with lbm.Lattice.from_workload(w, storage="f32" if comp else storage) as lat:
+        if comp:
+            lat.arithmetic = "compensated"
         lat.step(w.steps if steps is None else steps)
         return lat.moments()
 

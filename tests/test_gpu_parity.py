@@ -14,8 +14,15 @@ the oracle's own rounding floor (see oracle_floor):
     of the kernel shows the gap is FP32 arithmetic, not storage: FP32 storage
     with exact arithmetic gives 3.8e-6, every FP32 formulation tried
     1.4e-5 to 2.9e-5.)
+  FP32 storage with the compensated collision ("f32c", float-float
+    arithmetic): 1e-5 everywhere, the absorbed pulse included -- what is left
+    is the rounding of the FP32 store (3.9e-6 on rho' after 300 steps in a CPU
+    emulation with exact arithmetic).
   16-bit deviation storage: FP16 1e-2 at rho' amplitude 1e-3 (the stated
     target); BF16 keeps 8 significant bits and is held to its measured level.
+Besides the global norm, every cell is held to CELL_FACTOR times the tolerance
+of the field's largest magnitude, so that one wrong row or tile seam cannot
+hide in the norm of a large lattice.
 """
 import math
 
@@ -27,7 +34,8 @@ from helpers import rel_l2, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-10, "f32": 1e-5, "f16dev": 1e-2, "bf16dev": 6e-2}
+TOL = {"f64": 1e-10, "f32": 1e-5, "f32c": 1e-5, "f16dev": 1e-2, "bf16dev": 6e-2}
+CELL_FACTOR = 10
 F32_ABSORBED = 5e-5  # FP32 after the 100 x 100 pulse has been absorbed (see above)
 
 
@@ -41,6 +49,10 @@ def assert_close(got, ref, tol, steps, what=""):
     err = float(np.linalg.norm(got - ref))
     bound = tol * float(np.linalg.norm(ref)) + oracle_floor(steps, ref.size)
     assert err <= bound, (what, err, bound, rel_l2(got, ref))
+    # per cell: CELL_FACTOR x tol of the largest magnitude, plus one cell's floor
+    cell = float(np.abs(got - ref).max())
+    cbound = CELL_FACTOR * tol * float(np.abs(ref).max()) + oracle_floor(steps, 1)
+    assert cell <= cbound, (what, "max-abs", cell, cbound)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -65,13 +77,13 @@ def _oracle(w, steps):
     return _oracle_cache[key]
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f32c"])
 @pytest.mark.parametrize("variant", ["none", "II", "III"])
 def test_small_pulse_all_fields(storage, variant):
     """100 x 100, nu = 1e-3, eps = 1e-3, b = 3, 20-cell layer chi = 0.1 (d/20)^2:
     rho', u_x, u_y against the oracle after 100 steps (pulse still in the box) and
     after the workload's 300 steps."""
-    w = wl.small_pulse(variant, storage)
+    w = wl.small_pulse(variant, "f32" if storage == "f32c" else storage)
     for steps in (100, w.steps):
         ref = _oracle(w, steps)
         got = run_gpu(w, storage, steps)
@@ -147,7 +159,7 @@ def test_ragged_and_tiny_lattices(shape, bc, variant):
     nx, ny = shape
     w = _rand_workload(nx, ny, bc, variant, seed=nx * 1000 + ny)
     ref = run_oracle(w)
-    for storage in ("f64", "f32"):
+    for storage in ("f64", "f32", "f32c"):
         got = run_gpu(w, storage)
         for a, b in zip(got, ref):
             assert_close(a, b, TOL[storage], w.steps, storage)
@@ -293,6 +305,43 @@ def test_mean_flow_pulse_1024_full_run_properties(variant):
         d = lat.diagnostics(reg)
     assert d[5] == 0
     assert d[3] < 0.05 * e0
+
+
+_c2_ref = {}
+
+
+@pytest.mark.parametrize("variant", ["II", "III"])
+def test_mean_flow_pulse_1024_full_run_against_the_oracle(variant):
+    """The 1024 x 1024 Mach-0.2 workload over its full 5000 steps against the
+    oracle.  By then the layer has absorbed the pulse and rho' is ~1/1700 of its
+    size at step 200.  FP32 storage with the compensated collision meets the
+    1e-5 target on rho' (and u - u0); the FP32 collision (the benchmark's
+    configuration) is held to the same field within 2e-3 -- its own roundings,
+    ~10 per population per step, are the gap -- and its error is reported by
+    the benchmark beside the target."""
+    w = wl.mean_flow_pulse(seed=0, variant=variant, storage="f32")
+    if variant not in _c2_ref:
+        _c2_ref[variant] = run_oracle(w)
+    ref = _c2_ref[variant]
+    got = run_gpu(w, "f32c")
+    assert_close(got[0], ref[0], TOL["f32c"], w.steps, "f32c rho'")
+    for g, r, u in zip(got[1:], ref[1:], w.u0):
+        assert_close(g - u, r - u, TOL["f32c"], w.steps, "f32c u")
+    nat = run_gpu(w, "f32")[0]
+    assert_close(nat, ref[0], 2e-3, w.steps, "f32 rho'")
+
+
+def test_mean_flow_pulse_1024_type_I_diverges_on_both_sides():
+    """Type I on the same workload (chi_max = 1, s + chi > 2 across most of the
+    layer, Eq. effectrelax): parity while the unstable mode is small, then
+    non-finite on both sides (reading C15)."""
+    w = wl.mean_flow_pulse(seed=0, variant="I", storage="f32", steps=1000)
+    ref = run_oracle(w, 20)
+    got = run_gpu(w, "f64", 20)
+    assert_close(got[0], ref[0], TOL["f64"], 20)
+    r = run_oracle(w)[0]
+    g = run_gpu(w, "f32")[0]
+    assert (~np.isfinite(r)).any() and (~np.isfinite(g)).any()
 
 
 _big_ref = {}

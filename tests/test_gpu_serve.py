@@ -158,3 +158,85 @@ def test_non_finite_job_is_reported():
     srv.close()
     assert done[0].result[5] > 0 and "non-finite" in done[0].error
     assert done[1].result[5] == 0 and done[1].error is None
+
+
+@pytest.mark.parametrize("solo_cells", [None, 12000])
+def test_served_results_match_the_oracle(solo_cells):
+    """Each served job's final rho' against the FP64 oracle run of the same
+    problem, relative to the oracle's final field: FP32 1e-5, FP16 deviations
+    1e-2.  solo_cells=None sends every job through the batched launch; 12000
+    runs the larger ones through the single-lattice kernel beside it.  The
+    trace mixes FP32 and FP16 storage and types I, II and III.  A type I job
+    with s + chi > 2 (Eq. effectrelax) amplifies every rounding difference
+    without bound (reading C15): where the oracle's field is non-finite the
+    served one must be too; where it has grown tenfold past the initial pulse
+    the served one must have grown as well (or overflowed a 16-bit format to
+    non-finite values); before that the error is taken in units of the initial
+    pulse."""
+    from helpers import run_oracle
+    from paper_1203_6350_gb300.serve import Server
+
+    jobs = _jobs()
+    assert {j.workload.variant for j in jobs} == {"I", "II", "III"}
+    srv = Server(hbm_budget=1e12, chunk=16, keep_fields=True, solo_cells=solo_cells)
+    done = {j.id: j for j in srv.run(jobs, realtime=False)}
+    srv.close()
+    tol = {"f32": 1e-5, "f16dev": 1e-2}
+    checked = set()
+    for j in jobs:
+        w = j.workload
+        got = done[j.id].field
+        ref = run_oracle(w)[0]
+        den = np.linalg.norm(ref)
+        if w.variant == "I" and w.s[7] + w.chi_max > 2:
+            init = w.density_deviation()
+            if not np.isfinite(ref).all():
+                assert not np.isfinite(got).all(), j.id
+                continue
+            if np.abs(ref).max() > 10 * np.abs(init).max():
+                # grown too, or past the 16-bit format's range (non-finite)
+                assert (not np.isfinite(got).all()
+                        or np.abs(got).max() > 10 * np.abs(init).max()), j.id
+                continue
+            den = np.linalg.norm(init)
+        err = np.linalg.norm(got - ref) / den
+        assert err <= tol[w.storage], (j.id, w.storage, w.variant, w.steps, err)
+        checked.add((w.storage, w.variant))
+    assert {s for s, _ in checked} == {"f32", "f16dev"} and len(checked) >= 4, checked
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev"])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic", "channel"])
+def test_lattice_bytes_are_what_the_allocator_hands_out(storage, bc, monkeypatch):
+    """lbm_lattice_bytes(host_io = 1) is the peak a lattice holds through its
+    allocator after a host-field initialisation and a host read-out, with TMA
+    staging set up where it exists (FP32, Dirichlet): counted on a wrapped
+    torch allocator."""
+    from paper_1203_6350_gb300 import lbm
+
+    live, peak = [0], [0]
+
+    class Counting(lbm.TorchAllocator):
+        def _alloc(self, nbytes, ctx):
+            live[0] += int(nbytes)
+            peak[0] = max(peak[0], live[0])
+            return super()._alloc(nbytes, ctx)
+
+        def _free(self, ptr, nbytes, ctx):
+            live[0] -= int(nbytes)
+            return super()._free(ptr, nbytes, ctx)
+
+    monkeypatch.setattr(lbm, "TorchAllocator", Counting)
+    w = wl.pulse_workload(333, 77, variant="II", storage=storage, steps=4, bc=bc, width=6)
+    with lbm.Lattice.from_workload(w) as lat:
+        if storage == "f32" and bc == "dirichlet":
+            lat.cells_per_thread = 2
+            lat.steps_per_launch = 2
+            lat.tma_staging = True
+        lat.step(w.steps)
+        lat.moments()
+    assert live[0] == 0
+    want = lbm.lbm_lattice_bytes(w.nx, w.ny, lbm.STORAGE[storage], lbm.BC[bc], 1)
+    assert peak[0] == want, (peak[0], want)
+    assert lbm.lbm_lattice_bytes(w.nx, w.ny, lbm.STORAGE[storage], lbm.BC[bc], 0) == \
+        want - 24 * w.nx * w.ny

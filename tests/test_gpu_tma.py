@@ -148,3 +148,58 @@ def test_tma_staging_in_batches_is_bit_identical(monkeypatch):
     for a, c in zip(*out):
         for x, y in zip(a, c):
             np.testing.assert_array_equal(x, y)
+
+
+# ------------------------------------------ the bounded wait's give-up path ----
+#
+# LBM_TMA_WAIT_POLLS=0 at set-up makes each tile's wait for its staged copy
+# give up before its first poll.  Every copy is still real and in bounds, so
+# nothing fails on the device: the CTA votes to stop, thread 0 waits for the
+# copy in flight (full bound) and raises the error flag, and the CTA returns.
+# The host must then report LBM_ERR_CUDA and the context must stay usable.
+
+
+def test_a_wait_that_gives_up_is_reported_single_lattice(monkeypatch):
+    from paper_1203_6350_gb300 import lbm
+
+    w = _random(300, 200, "II", seed=5, steps=6)
+    monkeypatch.setenv("LBM_TMA_WAIT_POLLS", "0")
+    lat = lbm.Lattice.from_workload(w, storage="f32")
+    try:
+        lat.cells_per_thread = 2
+        lat.steps_per_launch = 2
+        lat.tma_staging = True
+        monkeypatch.delenv("LBM_TMA_WAIT_POLLS")
+        lat.step(w.steps)
+        with pytest.raises(lbm.LbmError) as e:
+            lat.moments()
+        assert e.value.code == lbm.LBM_ERR_CUDA and "TMA" in str(e.value)
+    finally:
+        lat.close()
+    # the context survived: a new lattice gives the plain-load result
+    np.testing.assert_array_equal(_state(w, True, w.steps), _state(w, False, w.steps))
+
+
+def test_a_wait_that_gives_up_is_reported_batch(monkeypatch):
+    from paper_1203_6350_gb300 import lbm
+    from paper_1203_6350_gb300.batch import Batch
+
+    w = _random(130, 70, "III", seed=9, steps=8)
+    monkeypatch.setenv("LBM_TMA_WAIT_POLLS", "0")
+    with Batch("f32") as bt:
+        monkeypatch.delenv("LBM_TMA_WAIT_POLLS")
+        bt.configure(2, 2, (64, 16))
+        assert lbm.lbm_batch_tma_staging(bt.b) == 1
+        i = bt.add_workload(w)
+        bt.step(w.steps)
+        with pytest.raises(lbm.LbmError) as e:
+            bt.moments(i)
+        assert e.value.code == lbm.LBM_ERR_CUDA and "TMA" in str(e.value)
+    with Batch("f32") as bt:
+        bt.configure(2, 2, (64, 16))
+        i = bt.add_workload(w)
+        bt.step(w.steps)
+        got = bt.moments(i)[0]
+    from helpers import run_oracle
+    ref = run_oracle(w)[0]
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)

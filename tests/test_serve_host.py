@@ -22,6 +22,9 @@ class FJob(Job):
     def bytes(self) -> int:
         return self.nbytes
 
+    def lattice_bytes(self, host_io):
+        return self.nbytes
+
 
 class FakeStream:
     def wait_stream(self, other):
@@ -52,7 +55,7 @@ def _server(budget, max_cells, solo_cells, refuse_solo=(), refuse_batch=(), monk
     srv.pending, srv.resident, srv.done, srv.batches = serve.deque(), {}, [], {}
     srv.used, srv.cells, srv.admitted, srv.round = 0, 0, 0, 0
     srv.budget, srv.max_cells, srv.solo_cells = float(budget), max_cells, solo_cells
-    srv.init, srv.device = "pulse", 0
+    srv.init, srv.device, srv.keep_fields = "pulse", 0, False
     srv.stream, srv.side = FakeStream(), FakeStream()
     srv.solo_streams = [FakeStream() for _ in range(3)]
     fb = FakeBatch(set(refuse_batch))
