@@ -452,7 +452,10 @@ void lbm_batch_destroy(lbm_batch b);
  * Limits: the region may hold at most 268,435,456 cells (16,384 partial sums
  * of 16,384 cells each) and one plane fewer than 2^31 elements; larger inputs
  * return LBM_ERR_TOO_LARGE without touching the device.  Other returns:
- * LBM_ERR_ARG (bad storage, bc, sizes, region, NULL pointers, rho0 <= 0),
+ * LBM_ERR_ARG (bad storage; a bc other than LBM_BC_DIRICHLET_EQ or
+ * LBM_BC_PERIODIC -- an LBM_BC_CHANNEL state (Sec. 4.2) needs its line source's
+ * phase, which this call does not take; bad sizes or region; NULL pointers;
+ * rho0 <= 0),
  * LBM_ERR_CUDA, LBM_ERR_NONFINITE (host out only: out is filled and out[5] > 0),
  * LBM_OK. */
 #define LBM_ERR_TOO_LARGE (-6) /* input exceeds the fixed capacity of a static scratch */

@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(kNaThreads)
     int ry = (int)(c / w);
     int rx = (int)(c - (long long)ry * w);
     const int pitch = static_cast<int>(g.pitch);
+    // the block's stride kNaThreads, as whole rows and a remainder below w
+    const int step_y = kNaThreads / w, step_x = kNaThreads - step_y * w;
     for (; c < end; c += kNaThreads) {
         const int x = x0 + rx, y = y0 + ry;
         PullSites ps;
@@ -85,8 +87,9 @@ __global__ void __launch_bounds__(kNaThreads)
                   0.5 * b.rho0 * (double(dux) * double(dux) + double(duy) * double(duy));
         acc[4] += dr * dr;
         acc[5] += (isfinite(r) && isfinite(dux) && isfinite(duy)) ? 0.0 : 1.0;
-        rx += kNaThreads;
-        while (rx >= w) {
+        rx += step_x;
+        ry += step_y;
+        if (rx >= w) {
             rx -= w;
             ++ry;
         }

@@ -677,9 +677,11 @@ def test_type_II_beats_the_viscosity_sponge_and_no_layer(oracle_lib, u0):
     """Figs. n3-n6: once the pulse has reached the layer, the type II layer leaves an
     E_L2 several times below both the viscosity sponge and no layer (more than 5x
     from step 350, more than 10x at step 600), the viscosity sponge is only
-    slightly better than nothing, and the type II error falls fast -- a log-log
-    slope steeper than -2 over steps 200-600, against the paper's exponents of
-    about -3.5 (at rest) and -3 (mean flow)."""
+    slightly better than nothing, and the type II error falls fast: over steps
+    200-600 the log-log slope is -3.41 at rest and -3.68 with mean flow in this
+    setup (nu = 1e-5, E_L2 every 50 steps), against the paper's exponents of
+    about -3.5 and -3; held to below -3.0 (a 12 % margin on the shallower one).
+    A viscosity sponge in place of the type II term gives -1.9."""
     none = _e_l2_history(oracle_lib, "none", u0)
     visc = _e_l2_history(oracle_lib, "viscous", u0)
     typ2 = _e_l2_history(oracle_lib, "II", u0)
@@ -690,4 +692,4 @@ def test_type_II_beats_the_viscosity_sponge_and_no_layer(oracle_lib, u0):
     t = np.arange(1, len(typ2) + 1) * 50.0
     sel = (t >= 200) & (t <= 600)
     slope = np.polyfit(np.log(t[sel]), np.log(typ2[sel]), 1)[0]
-    assert slope < -2.0, slope
+    assert slope < -3.0, slope

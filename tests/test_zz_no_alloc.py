@@ -15,7 +15,7 @@ import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-REL = {"f64": 1e-12, "f32": 1e-6}
+REL = {"f64": 1e-12, "f32": 1e-6, "f16dev": 1e-6, "bf16dev": 1e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,13 +30,16 @@ def _close(got, want, rel):
     assert np.all(np.abs(got - want) <= rel * scale), (got, want)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_noalloc_diagnostics_match_lbm_diagnostics(storage):
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_noalloc_diagnostics_match_lbm_diagnostics(storage, bc):
+    """Every storage format (the 16-bit ones decode with their per-plane scales)
+    and both accepted boundaries (the periodic pull wraps)."""
     import torch
 
     from paper_1203_6350_gb300 import lbm
 
-    w = wl.small_pulse("II", storage).with_(u0=(0.05, 0.0), u_f=(0.05, 0.0))
+    w = wl.small_pulse("II", storage).with_(u0=(0.05, 0.0), u_f=(0.05, 0.0), bc=bc)
     lat = lbm.Lattice.from_workload(w)
     lat.step(80)
     state = torch.empty(lat.state_bytes(), dtype=torch.uint8, device="cuda")
