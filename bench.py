@@ -56,8 +56,12 @@ def parse():
                     help="skip the 2048^2-16384^2 storage-format roofline sweep")
     ap.add_argument("--no-parity", action="store_true",
                     help="skip the error-against-the-oracle table (about 2 min of host CPU)")
-    ap.add_argument("--serve-seconds", type=float, default=0.5,
-                    help="seconds of the 200 jobs/s arrival trace to serve (0 skips)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="seconds of the 200 jobs/s arrival trace to serve (0 skips); the "
+                         "workload's 60 s are about 12 000 jobs, ~10 min served and ~11 min "
+                         "through the serial plain loop")
+    ap.add_argument("--serve-serial", default="plain", choices=["plain", "graph", "both"],
+                    help="serial loop(s) the served trace is compared with")
     return ap.parse_args()
 
 
@@ -392,7 +396,7 @@ def run_native(args):
         batched = run_batched()
     serving = None
     if args.serve_seconds > 0 and rank == 0:
-        serving = run_serving(args.serve_seconds)
+        serving = run_serving(args.serve_seconds, serial=args.serve_serial)
     parity = comp = decay = None
     if rank == 0 and not args.no_parity:
         parity = run_parity()
@@ -1051,13 +1055,18 @@ def run_batched(steps: int = 1000, warmup: int = 64, count: int = 256):
 SERVE_TOL = {"f32": 1e-5, "f16dev": 1e-2, "bf16dev": 1e-2, "f64": 1e-10}
 
 
-def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
+def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9, serial: str = "plain",
+                oracle_cap: float = 1e8):
     """Serving workload: Poisson arrivals at 200 jobs/s for `seconds` (sides
     log-uniform in [128, 4096], 500-5000 steps, FP32 or FP16-deviation storage,
     parameters as the batched workload), replayed in real time through the
     continuous-batching server (150 GB HBM budget) and through a serial loop of
-    single-lattice solves; plus the error against the FP64 oracle on a seeded
-    1 % sample of the jobs small enough for the oracle (cells x steps <= 3e8)."""
+    single-lattice solves fed the same trace (one launch per step: "plain";
+    graph-replayed: "graph"); throughput and p50/p99 latency over every
+    completion, the queue drained after the arrivals stop.  Plus the error
+    against the FP64 oracle on a seeded 1 % sample of the jobs, drawn from
+    those small enough for the oracle to finish in about a second each
+    (cells x steps <= oracle_cap)."""
     import copy
 
     from paper_1203_6350_gb300.serve import Job, Server, serial_loop, summary
@@ -1065,7 +1074,7 @@ def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
     reqs = wl.request_trace(seed=seed, rate=200.0, duration=seconds)
     jobs = [Job(id=k, workload=r.workload, arrival=r.arrival) for k, r in enumerate(reqs)]
     rng = np.random.default_rng(seed)
-    small = [j.id for j in jobs if j.workload.cells * j.workload.steps <= 3e8]
+    small = [j.id for j in jobs if j.workload.cells * j.workload.steps <= oracle_cap]
     n_sample = max(1, int(math.ceil(0.01 * len(jobs))))
     sample = set(int(x) for x in rng.choice(small, size=min(n_sample, len(small)), replace=False))
     srv = Server(hbm_budget=budget, chunk=64, keep_fields=sample)
@@ -1074,13 +1083,15 @@ def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
     wall = time.perf_counter() - t0
     srv.close()
     served = summary(done, wall)
-    t0 = time.perf_counter()
-    ser = serial_loop(copy.deepcopy(jobs))
-    wall_s = time.perf_counter() - t0
-    serial = summary(ser, wall_s)
-    t0 = time.perf_counter()
-    ser_p = serial_loop(copy.deepcopy(jobs), launch="plain")
-    serial_plain = summary(ser_p, time.perf_counter() - t0)
+    serial_graph = serial_plain = None
+    if serial in ("graph", "both"):
+        t0 = time.perf_counter()
+        ser = serial_loop(copy.deepcopy(jobs))
+        serial_graph = summary(ser, time.perf_counter() - t0)
+    if serial in ("plain", "both"):
+        t0 = time.perf_counter()
+        ser_p = serial_loop(copy.deepcopy(jobs), launch="plain")
+        serial_plain = summary(ser_p, time.perf_counter() - t0)
     # oracle check of the sampled jobs' served results
     from oracle import core
 
@@ -1120,11 +1131,16 @@ def run_serving(seconds: float, seed: int = SEED, budget: float = 150e9):
     return {
         "workload": f"Poisson 200 jobs/s for {seconds} s (seed {seed}), sides log-uniform in "
                     f"[128, 4096], 500-5000 steps, FP32/FP16-dev, HBM budget {budget / 1e9:.0f} GB",
-        "served": served, "serial_loop": serial, "serial_plain_loop": serial_plain,
-        "solves_per_s_speedup": (served["solves_per_s"] / serial["solves_per_s"]
-                                 if serial["solves_per_s"] else None),
+        "arrivals": len(jobs),
+        "served": served, "serial_loop": serial_graph, "serial_plain_loop": serial_plain,
+        "solves_per_s_speedup": (served["solves_per_s"] / serial_graph["solves_per_s"]
+                                 if serial_graph and serial_graph["solves_per_s"] else None),
         "solves_per_s_speedup_vs_plain": (served["solves_per_s"] / serial_plain["solves_per_s"]
-                                          if serial_plain["solves_per_s"] else None),
+                                          if serial_plain and serial_plain["solves_per_s"]
+                                          else None),
+        "p99_ratio_vs_plain": (served["p99_s"] / serial_plain["p99_s"]
+                               if serial_plain and serial_plain["p99_s"] else None),
+        "oracle_sample_within_tolerance": sum(r["within_tolerance"] for r in errs),
         "oracle_sample": errs,
     }
 
