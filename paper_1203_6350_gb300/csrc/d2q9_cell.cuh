@@ -219,27 +219,44 @@ __device__ __forceinline__ void back9_scaled(const V (&a)[9], V (&g)[9]) {
     g[8] = um + xmy;
 }
 
-// a_k = v / D_k for a conserved row k = 0, 1, 2, correctly rounded: the product
-// with 1/D_k rounded once more would scale rho' or j' by 9 fl(1/9) or 6 fl(1/6)
-// every step.
-template <typename V>
+// a_k = v / D_k for a conserved row k = 0, 1, 2, correctly rounded (UB): the
+// product with 1/D_k rounded once more would scale rho' or j' by 9 fl(1/9) or
+// 6 fl(1/6) every step.  16-bit storage rounds each population to 2^-11 or
+// 2^-8 on every store, far above that drift, and takes the plain product
+// (UB = false), which keeps its kernels at the register count they had.
+template <bool UB, typename V>
 __device__ __forceinline__ V scale_conserved(V v, const StepConst<V>& k, int row) {
+    if (!UB) return mul(v, k.dinv[row]);
     return fmadd(v, k.dinv[row], mul(v, k.dinv_lo[row]));
 }
+
+// Whether a storage format takes the correctly rounded conserved scaling.
+template <typename T>
+struct UnbiasedScale {
+    static constexpr bool value = true;
+};
+template <>
+struct UnbiasedScale<__half> {
+    static constexpr bool value = false;
+};
+template <>
+struct UnbiasedScale<__nv_bfloat16> {
+    static constexpr bool value = false;
+};
 
 // Collision where chi = 0: rho* = rho, j* = j, no damping term.  The
 // conserved rows are unchanged; the other six relax toward m^eq(rho, j):
 // a_k = keep_k m_k + take_k E_k (see StepConst).
-template <typename V>
+template <typename V, bool UB = true>
 __device__ __forceinline__ void collide_bulk(V (&g)[9], const StepConst<V>& k) {
     V m[9];
     moments9(g, m);
     V e3, e4, e7, e8;
     quad_eq(m[0], m[1], m[2], k, e3, e4, e7, e8);
     V a[9];
-    a[0] = scale_conserved(m[0], k, 0);
-    a[1] = scale_conserved(m[1], k, 1);
-    a[2] = scale_conserved(m[2], k, 2);
+    a[0] = scale_conserved<UB>(m[0], k, 0);
+    a[1] = scale_conserved<UB>(m[1], k, 1);
+    a[2] = scale_conserved<UB>(m[2], k, 2);
     a[3] = fmadd(k.keep[3], m[3], mul(k.take[3], e3));
     a[4] = fmadd(k.keep[4], m[4], mul(k.take[4], e4));
     a[5] = fmadd(k.keep[5], m[5], mul(k.take[5], m[1]));
@@ -252,7 +269,7 @@ __device__ __forceinline__ void collide_bulk(V (&g)[9], const StepConst<V>& k) {
 // The comparison sponge of Sec. 4.1 ("viscosity absorbing"): no damping term,
 // and in the layer every non-conserved rate falls linearly toward 1,
 // s_k' = s_k + (1 - s_k) r, with r in [0, 1] the layer fraction of the cell.
-template <typename V>
+template <typename V, bool UB = true>
 __device__ __forceinline__ void collide_viscous(V (&g)[9], V r, const StepConst<V>& k) {
     V m[9];
     moments9(g, m);
@@ -263,9 +280,9 @@ __device__ __forceinline__ void collide_viscous(V (&g)[9], V r, const StepConst<
     for (int i = 3; i < 9; ++i) sk[i] = fmadd(k.oms[i], r, k.s[i]);
     // m_k^+ = m_k + s_k' (m_k^eq - m_k); rows 5, 6: m^eq = -j
     V a[9];
-    a[0] = scale_conserved(m[0], k, 0);
-    a[1] = scale_conserved(m[1], k, 1);
-    a[2] = scale_conserved(m[2], k, 2);
+    a[0] = scale_conserved<UB>(m[0], k, 0);
+    a[1] = scale_conserved<UB>(m[1], k, 1);
+    a[2] = scale_conserved<UB>(m[2], k, 2);
     a[3] = mul(fmadd(sk[3], e3 - m[3], m[3]), k.dinv[3]);
     a[4] = mul(fmadd(sk[4], e4 - m[4], m[4]), k.dinv[4]);
     a[5] = mul(m[5] - mul(sk[5], m[1] + m[5]), k.dinv[5]);
@@ -276,7 +293,7 @@ __device__ __forceinline__ void collide_viscous(V (&g)[9], V r, const StepConst<
 }
 
 // Collision with an absorbing strength chi > 0 and its Guo factors rn, rm.
-template <typename V, int VAR>
+template <typename V, int VAR, bool UB = true>
 __device__ __forceinline__ void collide_layer(V (&g)[9], V chi, V rn, V rm,
                                               const StepConst<V>& k) {
     V m[9];
@@ -315,12 +332,14 @@ __device__ __forceinline__ void collide_layer(V (&g)[9], V chi, V rn, V rm,
         ct[6] = ndy;
     }
     V a[9];
-    // conserved rows: the numerator m + s_c (E - m) + chi T first, then 1/D unbiased
+    // conserved rows (UB): the numerator m + s_c (E - m) + chi T first, then 1/D
+    if (UB) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-        a[i] = scale_conserved(fmadd(k.s[i], E[i] - m[i], m[i]) + ct[i], k, i);
+        for (int i = 0; i < 3; ++i)
+            a[i] = scale_conserved<UB>(fmadd(k.s[i], E[i] - m[i], m[i]) + ct[i], k, i);
+    }
 #pragma unroll
-    for (int i = 3; i < 9; ++i) {
+    for (int i = UB ? 3 : 0; i < 9; ++i) {
         if (VAR == kTypeIII && i >= 7)
             a[i] = fmadd(k.keep[i], m[i], mul(k.take[i], E[i]));
         else

@@ -134,6 +134,7 @@ __device__ __forceinline__ void walk_tiles(const Inst* __restrict__ insts,
 template <typename T>
 struct CellTile {
     using CT = typename Codec<T>::CT;
+    static constexpr bool UB = UnbiasedScale<T>::value;
     int tile_y;
     __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<CT>& sd,
                                                long long, int lpar) const {
@@ -162,11 +163,11 @@ struct CellTile {
                 pull_all_b<T, kDirichlet, true>(src, plane, o, ps, v);
             }
             switch (sd.variant) {
-                case kTypeI: collide_cell<CT, kTypeI>(v, x, y, sd.k, sd.tx, sd.ty); break;
-                case kTypeII: collide_cell<CT, kTypeII>(v, x, y, sd.k, sd.tx, sd.ty); break;
-                case kTypeIII: collide_cell<CT, kTypeIII>(v, x, y, sd.k, sd.tx, sd.ty); break;
-                case kViscous: collide_cell<CT, kViscous>(v, x, y, sd.k, sd.tx, sd.ty); break;
-                default: collide_cell<CT, kNone>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                case kTypeI: collide_cell<CT, kTypeI, UB>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                case kTypeII: collide_cell<CT, kTypeII, UB>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                case kTypeIII: collide_cell<CT, kTypeIII, UB>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                case kViscous: collide_cell<CT, kViscous, UB>(v, x, y, sd.k, sd.tx, sd.ty); break;
+                default: collide_cell<CT, kNone, UB>(v, x, y, sd.k, sd.tx, sd.ty); break;
             }
             store_all_b<T>(dst, plane, o, v);
         }
@@ -179,6 +180,7 @@ struct CellTile {
 // and store.
 template <typename T>
 struct PairTile {
+    static constexpr bool UB = UnbiasedScale<T>::value;
     int tile_y;
     __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<F2>& sd,
                                                long long, int lpar) const {
@@ -201,11 +203,11 @@ struct PairTile {
             else
                 pull_pair_edge<T, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
             switch (sd.variant) {
-                case kTypeI: collide_pair<kTypeI>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeII: collide_pair<kTypeII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeIII: collide_pair<kTypeIII>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kViscous: collide_pair<kViscous>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                default: collide_pair<kNone>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeI: collide_pair<kTypeI, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeII: collide_pair<kTypeII, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeIII: collide_pair<kTypeIII, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kViscous: collide_pair<kViscous, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                default: collide_pair<kNone, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
             }
             if (x + 1 < nx)
                 store_pair<T>(dst, plane, o, v);
@@ -230,7 +232,7 @@ __host__ __device__ constexpr int batch_class(int variant, int bc) {
 // steps; an instance whose budget ends after the first takes one step.
 template <typename T, int VAR, int BC>
 struct TwoStepTile {
-    T* sm;
+    float* sm;  // R1 in FP32
     __device__ __forceinline__ void operator()(const BatchTile& tile, const BatchInst<F2>& sd,
                                                long long step, int lpar) const {
         const int parity = lpar ^ (int)(sd.l0 & 1);
@@ -254,7 +256,7 @@ struct TwoStepTile {
                 pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch), o, v);
             else
                 pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v);
-            collide_pair<VAR>(v, x, y, nx, sd.k, sd.tx, sd.ty);
+            collide_pair<VAR, UnbiasedScale<T>::value>(v, x, y, nx, sd.k, sd.tx, sd.ty);
             if (x + 1 < nx)
                 store_pair<T>(dst, plane, o, v);
             else
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kTbThreads, 3)
     extern __shared__ __align__(16) unsigned char tb_raw[];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     constexpr int c = batch_class(VAR, BC);
-    TwoStepTile<T, VAR, BC> body{reinterpret_cast<T*>(tb_raw)};
+    TwoStepTile<T, VAR, BC> body{reinterpret_cast<float*>(tb_raw)};
     walk_tiles(insts, tiles + table[1 + 2 * c], table[2 + 2 * c], counters[0] + step_off,
                (int)((counters[1] + launch_off) & 1), raw, body);
     asm volatile("griddepcontrol.launch_dependents;");

@@ -25,24 +25,24 @@ __device__ __forceinline__ AxisCoef<double> load_coef(const AxisCoef<double>* t,
 }
 
 // Collide the pulled populations of one cell in place.
-template <typename CT, int VAR>
+template <typename CT, int VAR, bool UB = true>
 __device__ __forceinline__ void collide_cell(CT (&v)[9], int x, int y, const StepConst<CT>& k,
                                              const AxisCoef<CT>* tx, const AxisCoef<CT>* ty) {
     if (VAR == kNone || (x >= k.bulk_x0 && x < k.bulk_x1 && y >= k.bulk_y0 && y < k.bulk_y1)) {
-        collide_bulk(v, k);  // no layer here: skip the per-axis tables
+        collide_bulk<CT, UB>(v, k);  // no layer here: skip the per-axis tables
     } else if (VAR == kViscous) {  // the tables' chi slot holds the layer fraction r
         const CT r = fmax(load_coef(tx, x).chi, load_coef(ty, y).chi);
         if (r > CT(0))
-            collide_viscous(v, r, k);
+            collide_viscous<CT, UB>(v, r, k);
         else
-            collide_bulk(v, k);
+            collide_bulk<CT, UB>(v, k);
     } else {
         const AxisCoef<CT> ax = load_coef(tx, x), ay = load_coef(ty, y);
         const CT chi = fmax(ax.chi, ay.chi);
         if (chi > CT(0))
-            collide_layer<CT, VAR>(v, chi, fmin(ax.rn, ay.rn), fmin(ax.rm, ay.rm), k);
+            collide_layer<CT, VAR, UB>(v, chi, fmin(ax.rn, ay.rn), fmin(ax.rm, ay.rm), k);
         else
-            collide_bulk(v, k);
+            collide_bulk<CT, UB>(v, k);
     }
 }
 
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kStepBX* kStepBY)
         const double src_s = (BC == kChannel && x == 0) ? line_source_scale(ls) : 0.0;
         pull_all<T, BC, true>(src, o, ps, v, src_s, ls.e);
     }
-    collide_cell<CT, VAR>(v, x, y, k, tx, ty);
+    collide_cell<CT, VAR, UnbiasedScale<T>::value>(v, x, y, k, tx, ty);
     store_all<T>(dst, o, v);
     // let the next step's grid launch while this one drains
     asm volatile("griddepcontrol.launch_dependents;");

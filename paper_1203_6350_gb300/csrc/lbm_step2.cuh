@@ -207,14 +207,14 @@ __device__ __forceinline__ void store_lo(T* __restrict__ d, unsigned plane, unsi
 // both inside the lattice.  Both cells take the damping path as soon as one
 // of them lies in the layer; with chi = 0 that path reduces to the plain
 // relaxation.
-template <int VAR>
+template <int VAR, bool UB = true>
 __device__ __forceinline__ void collide_lanes(F2 (&v)[9], int xa, int xb, int y,
                                               const StepConst<F2>& k,
                                               const AxisCoef<float>* __restrict__ tx,
                                               const AxisCoef<float>* __restrict__ ty) {
     if (VAR == kNone || (xa >= k.bulk_x0 && xa < k.bulk_x1 && xb >= k.bulk_x0 &&
                          xb < k.bulk_x1 && y >= k.bulk_y0 && y < k.bulk_y1)) {
-        collide_bulk(v, k);
+        collide_bulk<F2, UB>(v, k);
         return;
     }
     const AxisCoef<float> a0 = load_coef(tx, xa), a1 = load_coef(tx, xb);
@@ -222,23 +222,24 @@ __device__ __forceinline__ void collide_lanes(F2 (&v)[9], int xa, int xb, int y,
     const float c0 = fmaxf(a0.chi, ay.chi), c1 = fmaxf(a1.chi, ay.chi);
     if (c0 > 0.0f || c1 > 0.0f) {
         if (VAR == kViscous)  // the tables' chi slot holds the layer fraction r
-            collide_viscous(v, f2(c0, c1), k);
+            collide_viscous<F2, UB>(v, f2(c0, c1), k);
         else
-            collide_layer<F2, VAR>(v, f2(c0, c1), f2(fminf(a0.rn, ay.rn), fminf(a1.rn, ay.rn)),
-                                   f2(fminf(a0.rm, ay.rm), fminf(a1.rm, ay.rm)), k);
+            collide_layer<F2, VAR, UB>(v, f2(c0, c1),
+                                       f2(fminf(a0.rn, ay.rn), fminf(a1.rn, ay.rn)),
+                                       f2(fminf(a0.rm, ay.rm), fminf(a1.rm, ay.rm)), k);
     } else {
-        collide_bulk(v, k);
+        collide_bulk<F2, UB>(v, k);
     }
 }
 
 // The pair (x, x + 1) of row y; the phantom cell x + 1 = nx of an odd-width
 // lattice borrows the coefficients of its neighbour (its result is dropped).
-template <int VAR>
+template <int VAR, bool UB = true>
 __device__ __forceinline__ void collide_pair(F2 (&v)[9], int x, int y, int nx,
                                              const StepConst<F2>& k,
                                              const AxisCoef<float>* __restrict__ tx,
                                              const AxisCoef<float>* __restrict__ ty) {
-    collide_lanes<VAR>(v, x, min(x + 1, nx - 1), y, k, tx, ty);
+    collide_lanes<VAR, UB>(v, x, min(x + 1, nx - 1), y, k, tx, ty);
 }
 
 template <typename T, int VAR, int BC>
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kPairBX* kPairBY)
         const float* src_pop = (BC == kChannel && x == 0) ? ls.pop + 9 * ls.t_off : nullptr;
         pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v, src_pop);
     }
-    collide_pair<VAR>(v, x, y, nx, k, tx, ty);
+    collide_pair<VAR, UnbiasedScale<T>::value>(v, x, y, nx, k, tx, ty);
     if (x + 1 < nx)
         store_pair<T>(dst, plane, o, v);
     else

@@ -4,11 +4,15 @@
 //  1. It pulls from HBM the post-collision state of time t around the tile
 //     and collides the ring-extended region R1 (the tile plus one row above
 //     and below and two columns on each side, to keep pairs aligned), giving
-//     the post-collision state of time t + 1 on R1.  That state goes to
-//     shared memory in the storage format, exactly as a one-step kernel would
-//     store it in HBM (so the result does not depend on the blocking).
-//     Cells of R1 outside the lattice hold the boundary value instead: zero
-//     deviation for the Dirichlet far field, the wrapped cell for periodic.
+//     the post-collision state of time t + 1 on R1.  That state stays in
+//     shared memory in FP32 whatever the storage format: for FP32 storage it
+//     is exactly what a one-step kernel would store in HBM; for 16-bit
+//     storage the intermediate time level is not rounded to 16 bits, so a
+//     two-step launch rounds to the format once per two steps (and skips the
+//     encode and decode of the intermediate level, ~12 of its ~150
+//     instructions per cell and step).  Cells of R1 outside the lattice hold
+//     the boundary value instead: zero deviation for the Dirichlet far field,
+//     the wrapped cell for periodic.
 //  2. After a block barrier it pulls time t + 1 from shared memory, collides
 //     the tile and stores time t + 2 to HBM.
 //
@@ -28,9 +32,10 @@ constexpr int kR1H = kTbH + 2;      // R1: rows y0 - 1 .. y0 + kTbH
 constexpr int kR1Pairs = kR1W / 2;  // pairs per R1 row
 constexpr int kR1Plane = kR1W * kR1H;  // elements per plane in shared memory
 
+// R1 in FP32 (44,064 bytes, inside the default 48 KB window) for every format.
 template <typename T>
 constexpr size_t tb_smem_bytes() {
-    return 9 * kR1Plane * sizeof(T);
+    return 9 * kR1Plane * sizeof(float);
 }
 
 // Periodic image of coordinate c in [0, n).
@@ -66,14 +71,14 @@ __device__ __forceinline__ void pull_lanes(const T* __restrict__ s, unsigned pla
 
 // Two steps on the tile at (x0, y0) by a block of NT threads (any shape,
 // numbered by thread_rank): src holds time t, dst receives time t + 2;
-// sm is the block's tb_smem_bytes<T>() of shared memory.  Ends with a block
-// barrier, so the caller may reuse sm for the next tile right away.
+// sm is the block's tb_smem_bytes<T>() of shared memory (R1 in FP32).  Ends
+// with a block barrier, so the caller may reuse sm for the next tile right away.
 template <typename T, int VAR, int BC, int NT = kTbThreads>
 __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restrict__ dst, int nx,
                                          int ny, int pitch, unsigned plane, const StepConst<F2>& k,
                                          const AxisCoef<float>* __restrict__ tx,
                                          const AxisCoef<float>* __restrict__ ty, int x0, int y0,
-                                         T* sm, int thread_rank) {
+                                         float* sm, int thread_rank) {
     // ---- step 1: time t (HBM) -> time t + 1 on R1 (shared memory) ----
     for (int p = thread_rank; p < kR1Pairs * kR1H; p += NT) {
         const int px = p % kR1Pairs, py = p / kR1Pairs;
@@ -83,7 +88,7 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
         if (x > 0 && x + 2 < nx && y > 0 && y + 1 < ny) {
             pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch),
                                   static_cast<unsigned>(y * pitch + x), v);
-            collide_lanes<VAR>(v, x, x + 1, y, k, tx, ty);
+            collide_lanes<VAR, UnbiasedScale<T>::value>(v, x, x + 1, y, k, tx, ty);
         } else {
             int ca = x, cb = x + 1, cy = y;
             if (BC == kPeriodic) {
@@ -100,14 +105,14 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
                 cy = min(max(cy, 0), ny - 1);
             }
             pull_lanes<T, BC>(src, plane, pitch, ca, cb, cy, nx, ny, v);
-            collide_lanes<VAR>(v, ca, cb, cy, k, tx, ty);
+            collide_lanes<VAR, UnbiasedScale<T>::value>(v, ca, cb, cy, k, tx, ty);
             if (!(keep_a && keep_b)) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
                     v[i] = f2(keep_a ? f2_lo(v[i]) : 0.0f, keep_b ? f2_hi(v[i]) : 0.0f);
             }
         }
-        store_pair<T>(sm, kR1Plane, static_cast<unsigned>(py * kR1W + 2 * px), v);
+        store_pair<float>(sm, kR1Plane, static_cast<unsigned>(py * kR1W + 2 * px), v);
     }
     __syncthreads();
 
@@ -117,9 +122,9 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
         const int x = x0 + 2 * qx, y = y0 + qy;
         if (x >= nx || y >= ny) continue;
         F2 v[9];
-        pull_pair_interior<T, true>(sm, kR1Plane, kR1W,
-                                    static_cast<unsigned>((qy + 1) * kR1W + 2 * qx + 2), v);
-        collide_pair<VAR>(v, x, y, nx, k, tx, ty);
+        pull_pair_interior<float, true>(sm, kR1Plane, kR1W,
+                                        static_cast<unsigned>((qy + 1) * kR1W + 2 * qx + 2), v);
+        collide_pair<VAR, UnbiasedScale<T>::value>(v, x, y, nx, k, tx, ty);
         const unsigned o = static_cast<unsigned>(y * pitch + x);
         if (x + 1 < nx)
             store_pair<T>(dst, plane, o, v);
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kTbThreads)
     extern __shared__ __align__(16) unsigned char tb_raw[];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     tb2_tile<T, VAR, BC>(src, dst, nx, ny, pitch, plane, k, tx, ty, blockIdx.x * kTbW,
-                         blockIdx.y * kTbH, reinterpret_cast<T*>(tb_raw), threadIdx.x);
+                         blockIdx.y * kTbH, reinterpret_cast<float*>(tb_raw), threadIdx.x);
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
