@@ -39,6 +39,8 @@ def main(argv=None):
                     help="cells per thread (default: the library's choice)")
     ap.add_argument("--per-launch", type=int, default=None, choices=[1, 2],
                     help="time steps per launch (default: the library's choice)")
+    ap.add_argument("--arithmetic", default="native", choices=["native", "compensated"],
+                    help="collision arithmetic (compensated: FP32 storage, float-float)")
     args = ap.parse_args(argv)
 
     import torch
@@ -63,6 +65,8 @@ def main(argv=None):
             lat.cells_per_thread = args.cells
         if args.per_launch is not None:
             lat.steps_per_launch = args.per_launch
+        if args.arithmetic != "native":
+            lat.arithmetic = args.arithmetic
         spl = lat.steps_per_launch
         lat.step(args.warmup)
         a = torch.cuda.Event(enable_timing=True)
@@ -85,6 +89,7 @@ def main(argv=None):
         "case": f"{copies} x {args.side}x{args.side} {args.storage} variant {args.variant} "
                 f"layer {args.width}" + (" (batched)" if args.batch else ""),
         "steps": args.steps, "cells_per_thread": cpt, "steps_per_launch": spl,
+        "arithmetic": args.arithmetic,
         "mlups": cells / t / 1e6, "gbs": gbs,
         "frac_of_measured_hbm": gbs / peak if peak else None, "us_per_step": 1e6 * t / args.steps,
         "nonfinite_cells": d[5],

@@ -74,6 +74,11 @@ def _run(w, storage, cells, steps, per_launch=1):
 # format at the largest magnitude; after 25 steps: relative L2 of the fields
 ONE_STEP = {"f32": 2.0**-21, "f16dev": 2.0**-9, "bf16dev": 2.0**-6}
 MANY_STEPS = {"f32": 2e-5, "f16dev": 2e-3, "bf16dev": 2e-2}
+# Two steps per launch keep the intermediate time level in FP32, so with 16-bit
+# storage the two paths round at different steps: after 25 steps they differ
+# by a random walk of ~12 roundings of 2^-11 (FP16) or 2^-8 (BF16), amplified
+# where type I has s + chi > 2; held to ten roundings' worth.
+MANY_STEPS_TB = {"f32": 2e-5, "f16dev": 10 * 2.0**-11, "bf16dev": 10 * 2.0**-8}
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 7), (130, 3), (257, 129), (33, 64),
@@ -107,7 +112,9 @@ def test_two_steps_per_launch_match_one(shape, bc, variant):
     """Temporal blocking: one launch of the two-step kernel against two
     launches of the two-cell kernel (tiles of 64 x 16 cells whose ring of
     step-one cells crosses the lattice edge, wraps, or stays inside), then
-    25 steps (12 two-step launches and one one-step launch)."""
+    25 steps (12 two-step launches and one one-step launch).  With 16-bit
+    storage one two-step launch rounds to the format once, two launches twice
+    (MANY_STEPS_TB)."""
     nx, ny = shape
     for layer in (0, 5):
         if layer and 2 * layer >= min(nx, ny):
@@ -123,7 +130,7 @@ def test_two_steps_per_launch_match_one(shape, bc, variant):
             for x, y in zip(fa, fb):
                 den = np.linalg.norm(x)
                 if den > 0:
-                    assert np.linalg.norm(x - y) <= MANY_STEPS[storage] * den, (storage, layer)
+                    assert np.linalg.norm(x - y) <= MANY_STEPS_TB[storage] * den, (storage, layer)
 
 
 def test_two_steps_per_launch_through_graph_chunks():
