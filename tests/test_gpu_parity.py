@@ -477,3 +477,36 @@ def test_paper_strategy_comparison_on_the_gpu():
         np.testing.assert_allclose(g_hist, o_hist, rtol=1e-3)
         hist[variant] = np.array(g_hist)
     assert hist["II"][-1] < 0.1 * hist["viscous"][-1] < 0.1 * hist["none"][-1] * 1.0e1
+
+
+def test_arithmetic_modes_and_their_limits():
+    """lbm_set_arithmetic: compensated needs FP32 storage and runs one cell, one
+    step per launch; while it is selected, two cells, two steps or TMA staging
+    are refused; switching back restores the FP32 collision (same result as a
+    lattice that never left it)."""
+    from paper_1203_6350_gb300 import lbm
+
+    w = wl.small_pulse("II", "f32")
+    with lbm.Lattice.from_workload(w, storage="f64") as lat:
+        assert lat.arithmetic == "native"
+        with pytest.raises(lbm.LbmError):
+            lat.arithmetic = "compensated"
+    with lbm.Lattice.from_workload(w, storage="f16dev") as lat:
+        with pytest.raises(lbm.LbmError):
+            lat.arithmetic = "compensated"
+    ref = run_gpu(w, "f32", 40)
+    with lbm.Lattice.from_workload(w, storage="f32") as lat:
+        lat.cells_per_thread = 2
+        lat.arithmetic = "compensated"
+        assert lat.arithmetic == "compensated" and lat.cells_per_thread == 1
+        assert lat.steps_per_launch == 1
+        for bad in (lambda: setattr(lat, "cells_per_thread", 2),
+                    lambda: setattr(lat, "steps_per_launch", 2)):
+            with pytest.raises(lbm.LbmError):
+                bad()
+        assert lbm.lbm_set_tma_staging(lat.h, 1) == lbm.LBM_ERR_ARG
+        assert lbm.lbm_set_arithmetic(lat.h, 7) == lbm.LBM_ERR_ARG
+        lat.arithmetic = "native"
+        lat.cells_per_thread = 2
+        lat.step(40)
+        np.testing.assert_array_equal(lat.moments()[0], ref[0])
