@@ -251,10 +251,13 @@ int lbm_get_arithmetic(lbm_handle h);
  * out-of-lattice elements read as zero (the Dirichlet far-field deviation);
  * the copy of a CTA's next tile overlaps the current tile's second step.
  * The results are bit-identical to those without it (0).  Available for
- * LBM_F32 storage with LBM_BC_DIRICHLET_EQ; the default where both
- * population buffers together exceed four times the L2 size (the environment
- * variable LBM_TMA=0 or 1 at lbm_create overrides that choice); LBM_ERR_ARG
- * for other handles or values.  A staged copy that has not
+ * LBM_F32, LBM_F16DEV and LBM_BF16DEV storage with LBM_BC_DIRICHLET_EQ (a
+ * 72 x 20 box of FP32, or 80 x 20 of 16-bit elements, starting 16 bytes left
+ * of the tile); the default for LBM_F32 where both population buffers
+ * together exceed four times the L2 size (the environment variable LBM_TMA=0
+ * or 1 at lbm_create overrides that choice; 16-bit storage measured level
+ * with plain loads and is not staged by default); LBM_ERR_ARG for other
+ * handles or values.  A staged copy that has not
  * completed after a bounded wait (2^20 polls of its mbarrier) stops its CTA,
  * which waits for that copy once more with a 16 times longer bound, and makes
  * the next lbm_moments / lbm_diagnostics / lbm_get_state on the host return

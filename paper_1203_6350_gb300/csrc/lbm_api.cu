@@ -249,10 +249,21 @@ cudaError_t launch_two_steps(lbm_ctx* h, const void* src, void* dst, cudaStream_
     const int p = pdl ? 1 : 0;
     const auto* tx = static_cast<const lbm::AxisCoef<float>*>(h->chi_x);
     const auto* ty = static_cast<const lbm::AxisCoef<float>*>(h->chi_y);
-    if (h->tma)
-        return lbm::launch_step_tb2_tma_f32(h->tmap[src == h->buf[0] ? 0 : 1], dst, h->geo, h->k2,
-                                            tx, ty, h->variant, h->tma_grid, h->tma_err, st, p,
-                                            h->tma_polls);
+    if (h->tma) {
+        const CUtensorMap& m = h->tmap[src == h->buf[0] ? 0 : 1];
+        switch (h->storage) {
+            case LBM_F32:
+                return lbm::launch_step_tb2_tma_f32(m, dst, h->geo, h->k2, tx, ty, h->variant,
+                                                    h->tma_grid, h->tma_err, st, p, h->tma_polls);
+            case LBM_F16DEV:
+                return lbm::launch_step_tb2_tma_f16(m, dst, h->geo, h->k2, tx, ty, h->variant,
+                                                    h->tma_grid, h->tma_err, st, p, h->tma_polls);
+            case LBM_BF16DEV:
+                return lbm::launch_step_tb2_tma_bf16(m, dst, h->geo, h->k2, tx, ty, h->variant,
+                                                     h->tma_grid, h->tma_err, st, p, h->tma_polls);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (h->storage) {
         case LBM_F32: return lbm::launch_step_tb2_f32(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
         case LBM_F16DEV: return lbm::launch_step_tb2_f16(src, dst, h->geo, h->k2, tx, ty, h->variant, h->bc, st, p);
@@ -265,15 +276,20 @@ cudaError_t launch_two_steps(lbm_ctx* h, const void* src, void* dst, cudaStream_
 // LBM_OK, or the reason it is not available for this handle.
 int setup_tma(lbm_ctx* h) {
     if (h->tma_ready) return LBM_OK;
-    if (h->storage != LBM_F32 || h->bc != LBM_BC_DIRICHLET_EQ)
-        return fail(h, LBM_ERR_ARG, "TMA staging needs FP32 storage and the Dirichlet boundary");
+    if (h->storage == LBM_F64 || h->bc != LBM_BC_DIRICHLET_EQ)
+        return fail(h, LBM_ERR_ARG,
+                    "TMA staging needs FP32, FP16 or BF16 storage and the Dirichlet boundary");
     int per_sm = 0, sms = 0;
-    cudaError_t e = lbm::prepare_step_tb2_tma_f32(&per_sm);
+    cudaError_t e = h->storage == LBM_F32      ? lbm::prepare_step_tb2_tma_f32(&per_sm)
+                    : h->storage == LBM_F16DEV ? lbm::prepare_step_tb2_tma_f16(&per_sm)
+                                               : lbm::prepare_step_tb2_tma_bf16(&per_sm);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "TMA kernel set-up");
     if (per_sm < 1) return fail(h, LBM_ERR_CUDA, "the TMA kernel does not fit an SM");
-    if (!lbm::encode_tma_map_f32(&h->tmap[0], h->buf[0], h->geo) ||
-        !lbm::encode_tma_map_f32(&h->tmap[1], h->buf[1], h->geo))
+    const int elem = h->storage == LBM_F32 ? 4 : 2;
+    const bool bf16 = h->storage == LBM_BF16DEV;
+    if (!lbm::encode_tma_map(&h->tmap[0], h->buf[0], h->geo, elem, bf16) ||
+        !lbm::encode_tma_map(&h->tmap[1], h->buf[1], h->geo, elem, bf16))
         return fail(h, LBM_ERR_CUDA, "the driver did not encode the tensor maps");
     if (!h->tma_err) {
         h->tma_err = static_cast<int*>(dev_alloc(h, 256));
@@ -472,10 +488,12 @@ int lbm_create(int nx, int ny, lbm_storage storage, double rho0, double ux0, dou
     // FP32 Dirichlet lattices whose state exceeds four times L2 stage the
     // two-step tiles' input by TMA: measured 2-8 % ahead of plain loads from
     // 4096^2 up, 3 % behind at 2048^2 (LBM_TMA=0 or 1 overrides the choice).
+    // 16-bit storage can be staged too (LBM_TMA=1), measured level with plain loads.
     const char* tma_env = std::getenv("LBM_TMA");
-    bool want_tma = h->spl == 2 && 2 * h->buf_bytes > 4 * static_cast<size_t>(l2);
+    bool want_tma = storage == LBM_F32 && h->spl == 2 &&
+                    2 * h->buf_bytes > 4 * static_cast<size_t>(l2);
     if (tma_env) want_tma = std::strcmp(tma_env, "0") != 0;
-    if (storage == LBM_F32 && bc == LBM_BC_DIRICHLET_EQ && want_tma)
+    if (storage != LBM_F64 && bc == LBM_BC_DIRICHLET_EQ && want_tma)
         h->tma = setup_tma(h) == LBM_OK;
     h->err.clear();
     set_source_shape(h);

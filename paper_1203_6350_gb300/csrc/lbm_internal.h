@@ -273,10 +273,22 @@ cudaError_t launch_step_tb2_tma_f32(const CUtensorMap& src_map, void* dst, const
                                    const StepConst<F2>& k, const AxisCoef<float>* tx,
                                    const AxisCoef<float>* ty, int variant, int grid, int* err,
                                    cudaStream_t st, int pdl, int polls);
+// The same for FP16 / BF16 deviation storage (80 x 20 x 9 box of 16-bit elements).
+cudaError_t launch_step_tb2_tma_f16(const CUtensorMap& src_map, void* dst, const Geometry& g,
+                                    const StepConst<F2>& k, const AxisCoef<float>* tx,
+                                    const AxisCoef<float>* ty, int variant, int grid, int* err,
+                                    cudaStream_t st, int pdl, int polls);
+cudaError_t launch_step_tb2_tma_bf16(const CUtensorMap& src_map, void* dst, const Geometry& g,
+                                     const StepConst<F2>& k, const AxisCoef<float>* tx,
+                                     const AxisCoef<float>* ty, int variant, int grid, int* err,
+                                     cudaStream_t st, int pdl, int polls);
 // Shared-memory attributes of the TMA kernels; per_sm receives CTAs per SM.
 cudaError_t prepare_step_tb2_tma_f32(int* per_sm);
-// The tensor map of one FP32 population buffer for the TMA kernel; false when
-// the driver cannot encode it.
+cudaError_t prepare_step_tb2_tma_f16(int* per_sm);
+cudaError_t prepare_step_tb2_tma_bf16(int* per_sm);
+// The tensor map of one population buffer for the TMA kernel (elem = 4: FP32;
+// 2: FP16, or BF16 when bf16); false when the driver cannot encode it.
+bool encode_tma_map(CUtensorMap* map, void* base, const Geometry& g, int elem, bool bf16);
 bool encode_tma_map_f32(CUtensorMap* map, void* base, const Geometry& g);
 
 // Base-state parameters of the auxiliary kernels (always FP64).

@@ -1,6 +1,6 @@
 // Two-cells-per-thread step kernels for __nv_bfloat16 population storage (packed FP32
 // compute): one step per launch, and two steps per launch (temporal blocking).
-#include "lbm_step_tb.cuh"
+#include "lbm_step_tma.cuh"
 
 namespace lbm {
 
@@ -15,6 +15,18 @@ cudaError_t launch_step_tb2_bf16(const void* src, void* dst, const Geometry& g,
                               const AxisCoef<float>* ty, int variant, int bc, cudaStream_t st,
                               int pdl) {
     return launch_step_tb2_t<__nv_bfloat16>(src, dst, g, k, tx, ty, variant, bc, st, pdl);
+}
+
+cudaError_t launch_step_tb2_tma_bf16(const CUtensorMap& src_map, void* dst, const Geometry& g,
+                                    const StepConst<F2>& k, const AxisCoef<float>* tx,
+                                    const AxisCoef<float>* ty, int variant, int grid, int* err,
+                                    cudaStream_t st, int pdl, int polls) {
+    return launch_step_tb2_tma<__nv_bfloat16>(src_map, static_cast<__nv_bfloat16*>(dst), g, k, tx, ty, variant,
+                                   grid, err, st, pdl, polls);
+}
+
+cudaError_t prepare_step_tb2_tma_bf16(int* per_sm) {
+    return prepare_step_tb2_tma<__nv_bfloat16>(per_sm);
 }
 
 }  // namespace lbm

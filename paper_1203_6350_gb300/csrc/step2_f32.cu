@@ -26,7 +26,7 @@ cudaError_t launch_step_tb2_tma_f32(const CUtensorMap& src_map, void* dst, const
                                st, pdl, polls);
 }
 
-cudaError_t prepare_step_tb2_tma_f32(int* per_sm) { return prepare_step_tb2_tma(per_sm); }
+cudaError_t prepare_step_tb2_tma_f32(int* per_sm) { return prepare_step_tb2_tma<float>(per_sm); }
 
 namespace {
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -49,18 +49,28 @@ EncodeTiled encode_tiled() {
 }
 }  // namespace
 
-bool encode_tma_map_f32(CUtensorMap* map, void* base, const Geometry& g) {
+// elem = 4 (FP32) or 2 (FP16 / BF16 deviations, bf16 selecting the type).
+bool encode_tma_map(CUtensorMap* map, void* base, const Geometry& g, int elem, bool bf16) {
     const EncodeTiled f = encode_tiled();
-    if (!f || !base) return false;
+    if (!f || !base || (elem != 4 && elem != 2)) return false;
     const cuuint64_t dim[3] = {static_cast<cuuint64_t>(g.nx), static_cast<cuuint64_t>(g.ny), 9};
-    const cuuint64_t stride[2] = {static_cast<cuuint64_t>(g.pitch) * sizeof(float),
-                                  static_cast<cuuint64_t>(g.plane) * sizeof(float)};
-    const cuuint32_t box[3] = {kTmaW, kTmaH, 9};
+    const cuuint64_t stride[2] = {static_cast<cuuint64_t>(g.pitch) * elem,
+                                  static_cast<cuuint64_t>(g.plane) * elem};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(elem == 4 ? TmaBox<float>::w
+                                                                  : TmaBox<__half>::w),
+                               static_cast<cuuint32_t>(TmaBox<float>::h), 9};
     const cuuint32_t step[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : bf16    ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     // elements outside the extent read as zero (OOB fill "none")
-    return f(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dim, stride, box, step,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return f(map, dt, 3, base, dim, stride, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_tma_map_f32(CUtensorMap* map, void* base, const Geometry& g) {
+    return encode_tma_map(map, base, g, 4, false);
 }
 
 }  // namespace lbm

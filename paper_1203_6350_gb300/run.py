@@ -41,6 +41,8 @@ def main(argv=None):
                     help="time steps per launch (default: the library's choice)")
     ap.add_argument("--arithmetic", default="native", choices=["native", "compensated"],
                     help="collision arithmetic (compensated: FP32 storage, float-float)")
+    ap.add_argument("--tma", type=int, default=None, choices=[0, 1],
+                    help="TMA staging of two-step launches (default: the library's choice)")
     args = ap.parse_args(argv)
 
     import torch
@@ -67,6 +69,8 @@ def main(argv=None):
             lat.steps_per_launch = args.per_launch
         if args.arithmetic != "native":
             lat.arithmetic = args.arithmetic
+        if args.tma is not None and not args.batch:
+            lat.tma_staging = bool(args.tma)
         spl = lat.steps_per_launch
         lat.step(args.warmup)
         a = torch.cuda.Event(enable_timing=True)
@@ -84,12 +88,14 @@ def main(argv=None):
         peak = float(json.load(open(p))["hbm_gbs"])
     d = lat.diagnostics(ids[0]) if args.batch else lat.diagnostics()
     cpt = lat.cells_per_thread
+    staged = None if args.batch else bool(lat.tma_staging)
     lat.close()
     print(json.dumps({
         "case": f"{copies} x {args.side}x{args.side} {args.storage} variant {args.variant} "
                 f"layer {args.width}" + (" (batched)" if args.batch else ""),
         "steps": args.steps, "cells_per_thread": cpt, "steps_per_launch": spl,
         "arithmetic": args.arithmetic,
+        "tma_staging": staged,
         "mlups": cells / t / 1e6, "gbs": gbs,
         "frac_of_measured_hbm": gbs / peak if peak else None, "us_per_step": 1e6 * t / args.steps,
         "nonfinite_cells": d[5],

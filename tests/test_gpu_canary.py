@@ -76,7 +76,8 @@ def _run(monkeypatch, canary, w, storage, cpt, spl, tma):
 # (storage, cells per thread, steps per launch, TMA staging)
 KERNELS = [("f64", 1, 1, None), ("f32", 1, 1, None), ("f32", 2, 1, None), ("f32", 2, 2, False),
            ("f32", 2, 2, True), ("f16dev", 1, 1, None), ("f16dev", 2, 1, None),
-           ("f16dev", 2, 2, None), ("bf16dev", 2, 1, None), ("bf16dev", 2, 2, None)]
+           ("f16dev", 2, 2, None), ("f16dev", 2, 2, True), ("bf16dev", 2, 1, None),
+           ("bf16dev", 2, 2, None), ("bf16dev", 2, 2, True)]
 
 
 @pytest.mark.parametrize("kernel", KERNELS, ids=lambda k: "-".join(map(str, k)))

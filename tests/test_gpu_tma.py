@@ -1,5 +1,5 @@
-"""The two-step kernel with TMA-staged input (FP32, Dirichlet) against the
-same two-step arithmetic on plain loads: bit-identical stored states on
+"""The two-step kernel with TMA-staged input (FP32, FP16 and BF16 storage,
+Dirichlet) against the same two-step arithmetic on plain loads: bit-identical stored states on
 ragged, tiny and large lattices, every damping variant, odd step counts (the
 one-step remainder) and graph-replayed chunks; where it is available.
 """
@@ -21,10 +21,10 @@ def _cuda():
     lbm.load()
 
 
-def _state(w, tma, steps, chunks=None):
+def _state(w, tma, steps, chunks=None, storage="f32"):
     from paper_1203_6350_gb300 import lbm
 
-    with lbm.Lattice.from_workload(w, storage="f32") as lat:
+    with lbm.Lattice.from_workload(w, storage=storage) as lat:
         lat.cells_per_thread = 2
         lat.steps_per_launch = 2
         lat.tma_staging = tma
@@ -49,10 +49,11 @@ def _random(nx, ny, variant, seed, steps):
 @pytest.mark.parametrize("shape", [(1, 1), (2, 3), (3, 5), (64, 16), (65, 17), (129, 33),
                                    (1025, 40), (300, 200)])
 @pytest.mark.parametrize("variant", ["none", "I", "II", "III", "viscous"])
-def test_tma_staging_is_bit_identical_to_plain_loads(shape, variant):
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev"])
+def test_tma_staging_is_bit_identical_to_plain_loads(shape, variant, storage):
     w = _random(*shape, variant, seed=shape[0] * 7 + shape[1], steps=11)
-    a = _state(w, True, w.steps)
-    b = _state(w, False, w.steps)
+    a = _state(w, True, w.steps, storage=storage)
+    b = _state(w, False, w.steps, storage=storage)
     np.testing.assert_array_equal(a, b)
 
 
@@ -60,9 +61,10 @@ def test_tma_staging_across_graph_chunks():
     """150 steps as 64 + 64 + 22: graph replays of 32 two-step launches and a
     one-step remainder."""
     w = _random(333, 97, "II", seed=5, steps=150)
-    a = _state(w, True, w.steps, chunks=[64, 64, 22])
-    b = _state(w, False, w.steps, chunks=[150])
-    np.testing.assert_array_equal(a, b)
+    for storage in ("f32", "f16dev"):
+        a = _state(w, True, w.steps, chunks=[64, 64, 22], storage=storage)
+        b = _state(w, False, w.steps, chunks=[150], storage=storage)
+        np.testing.assert_array_equal(a, b)
 
 
 def test_tma_staging_availability():
@@ -79,9 +81,11 @@ def test_tma_staging_availability():
             lat.tma_staging = True
     with lbm.Lattice.from_workload(w, storage="f16dev") as lat:
         assert not lat.tma_staging
-        assert lbm.lbm_set_tma_staging(lat.h, 1) == lbm.LBM_ERR_ARG
+        assert lbm.lbm_set_tma_staging(lat.h, 1) == lbm.LBM_OK
         assert lbm.lbm_set_tma_staging(lat.h, 0) == lbm.LBM_OK
         assert lbm.lbm_set_tma_staging(lat.h, 2) == lbm.LBM_ERR_ARG
+    with lbm.Lattice.from_workload(w, storage="f64") as lat:
+        assert lbm.lbm_set_tma_staging(lat.h, 1) == lbm.LBM_ERR_ARG
 
 
 def test_tma_staging_at_2048_is_bit_identical_to_plain_loads():
@@ -159,12 +163,13 @@ def test_tma_staging_in_batches_is_bit_identical(monkeypatch):
 # The host must then report LBM_ERR_CUDA and the context must stay usable.
 
 
-def test_a_wait_that_gives_up_is_reported_single_lattice(monkeypatch):
+@pytest.mark.parametrize("storage", ["f32", "f16dev"])
+def test_a_wait_that_gives_up_is_reported_single_lattice(monkeypatch, storage):
     from paper_1203_6350_gb300 import lbm
 
     w = _random(300, 200, "II", seed=5, steps=6)
     monkeypatch.setenv("LBM_TMA_WAIT_POLLS", "0")
-    lat = lbm.Lattice.from_workload(w, storage="f32")
+    lat = lbm.Lattice.from_workload(w, storage=storage)
     try:
         lat.cells_per_thread = 2
         lat.steps_per_launch = 2
@@ -177,7 +182,8 @@ def test_a_wait_that_gives_up_is_reported_single_lattice(monkeypatch):
     finally:
         lat.close()
     # the context survived: a new lattice gives the plain-load result
-    np.testing.assert_array_equal(_state(w, True, w.steps), _state(w, False, w.steps))
+    np.testing.assert_array_equal(_state(w, True, w.steps, storage=storage),
+                                  _state(w, False, w.steps, storage=storage))
 
 
 def test_a_wait_that_gives_up_is_reported_batch(monkeypatch):
