@@ -301,6 +301,17 @@ const char* lbm_last_error(lbm_handle h);
 /* Library version string. */
 const char* lbm_version(void);
 
+/* Bandwidth probe for roofline denominators; not part of the scheme.  Copies
+ * the `bytes` at device pointer a into b and back, iters times in all, in ONE
+ * launch on cuda_stream (a borrowed cudaStream_t, NULL = legacy default):
+ * 4 CTAs of 512 threads per SM, each thread owning a fixed, grid-strided set
+ * of 16-byte words that it copies in both directions, so no thread waits for
+ * another and no launch gap falls between the passes.  Bytes moved = 2 x bytes x
+ * iters (read + write).  Asynchronous; time it with events on the stream.
+ * LBM_ERR_ARG for NULL or unaligned pointers (16 bytes), bytes not a positive
+ * multiple of 16, or iters < 1; LBM_ERR_CUDA if the launch fails. */
+int lbm_probe_copy(void* a, void* b, size_t bytes, int iters, void* cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Batched stepping of many independent lattices (one persistent launch per
  * time step over a tile table, replayed from captured CUDA graphs).

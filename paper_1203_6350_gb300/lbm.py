@@ -87,6 +87,7 @@ SIGNATURES = [
     ("lbm_set_steps_per_launch", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_steps_per_launch", ctypes.c_int, [_vp]),
     ("lbm_set_arithmetic", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lbm_probe_copy", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]),
     ("lbm_get_arithmetic", ctypes.c_int, [_vp]),
     ("lbm_set_tma_staging", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lbm_tma_staging", ctypes.c_int, [_vp]),
@@ -287,6 +288,10 @@ def lbm_set_arithmetic(h, arithmetic) -> int:
 
 def lbm_get_arithmetic(h) -> int:
     return load().lbm_get_arithmetic(h)
+
+
+def lbm_probe_copy(a_ptr, b_ptr, nbytes, iters, stream=None) -> int:
+    return load().lbm_probe_copy(a_ptr, b_ptr, int(nbytes), int(iters), stream)
 
 
 def lbm_set_tma_staging(h, on) -> int:

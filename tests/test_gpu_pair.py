@@ -115,7 +115,10 @@ def test_two_steps_per_launch_match_one(shape, bc, variant):
     step-one cells crosses the lattice edge, wraps, or stays inside), then
     25 steps (12 two-step launches and one one-step launch).  With 16-bit
     storage one two-step launch rounds to the format once, two launches twice
-    (MANY_STEPS_TB)."""
+    (MANY_STEPS_TB).  Type I here has s + chi up to 2.4 (rates 1.9, chi up to
+    0.5): it amplifies any rounding difference without bound (Eq. effectrelax,
+    reading C15), so its two 16-bit paths, which round at different steps, are
+    compared after one launch only."""
     nx, ny = shape
     for layer in (0, 5):
         if layer and 2 * layer >= min(nx, ny):
@@ -126,6 +129,8 @@ def test_two_steps_per_launch_match_one(shape, bc, variant):
             b, _ = _run(w, storage, 2, 2, per_launch=2)
             scale = np.abs(a).max()
             assert np.abs(a - b).max() <= 2 * ONE_STEP[storage] * scale, (storage, layer)
+            if variant == "I" and storage != "f32":
+                continue
             _, fa = _run(w, storage, 2, w.steps, per_launch=1)
             _, fb = _run(w, storage, 2, w.steps, per_launch=2)
             for x, y in zip(fa, fb):
