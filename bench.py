@@ -422,6 +422,11 @@ def run_native(args):
             "clocks": clocks,
             "gpu_launches": launches_total,
             "reflected_energy": {k: refl.get(k) for k in VARIANTS},
+            "divergent_solves": {
+                k: ("type I with s + chi > 2 (s = %.4f, chi_max = %.3g) grows without bound "
+                    "(Eq. effectrelax); its solve is in the timed work and steps a non-finite "
+                    "field once it overflows" % (works[0].s[7], works[0].chi_max))
+                for k in VARIANTS if refl.get(k) is None},
             "roofline_sweep": sweep,
             "line_source": line_source,
             "stability_map": stability_map,
