@@ -203,11 +203,11 @@ struct PairTile {
             else
                 pull_pair_edge<T, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
             switch (sd.variant) {
-                case kTypeI: collide_pair<kTypeI, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeII: collide_pair<kTypeII, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeIII: collide_pair<kTypeIII, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kViscous: collide_pair<kViscous, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                default: collide_pair<kNone, UB>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeI: collide_pair<kTypeI, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeII: collide_pair<kTypeII, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeIII: collide_pair<kTypeIII, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kViscous: collide_pair<kViscous, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                default: collide_pair<kNone, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
             }
             if (x + 1 < nx)
                 store_pair<T>(dst, plane, o, v);
@@ -438,8 +438,9 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                 const bool row_in = y >= 0 && y < ny;
                 const bool keep_a = row_in && x >= 0 && x < nx;
                 const bool keep_b = row_in && x + 1 >= 0 && x + 1 < nx;
-                collide_lanes<VAR>(v, min(max(x, 0), nx - 1), min(max(x + 1, 0), nx - 1),
-                                   min(max(y, 0), ny - 1), sd.k, sd.tx, sd.ty);
+                collide_lanes<VAR, true, true>(v, min(max(x, 0), nx - 1),
+                                               min(max(x + 1, 0), nx - 1),
+                                               min(max(y, 0), ny - 1), sd.k, sd.tx, sd.ty);
                 if (!(keep_a && keep_b)) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i)
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                 F2 v[9];
                 pull_pair_interior<float, true>(
                     r1, kR1Plane, kR1W, static_cast<unsigned>((qy + 1) * kR1W + 2 * qx + 2), v);
-                collide_pair<VAR>(v, x, y, nx, sd.k, sd.tx, sd.ty);
+                collide_pair<VAR, true, true>(v, x, y, nx, sd.k, sd.tx, sd.ty);
                 const unsigned o = static_cast<unsigned>(y * pitch + x);
                 if (x + 1 < nx)
                     store_pair<float>(dst, plane, o, v);
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                     pull_pair_interior<float>(src, plane, static_cast<unsigned>(pitch), o, v);
                 else
                     pull_pair_edge<float, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
-                collide_pair<VAR>(v, x, y, nx, sd.k, sd.tx, sd.ty);
+                collide_pair<VAR, true, true>(v, x, y, nx, sd.k, sd.tx, sd.ty);
                 if (x + 1 < nx)
                     store_pair<float>(dst, plane, o, v);
                 else

@@ -206,21 +206,34 @@ __device__ __forceinline__ void store_lo(T* __restrict__ d, unsigned plane, unsi
 // Collide a pair of cells of row y at columns xa (lo lane) and xb (hi lane),
 // both inside the lattice.  Both cells take the damping path as soon as one
 // of them lies in the layer; with chi = 0 that path reduces to the plain
-// relaxation.
-template <int VAR, bool UB = true>
+// relaxation (rho* = rho, j* = j, no damping term; the bulk's tables hold
+// chi = 0 and Guo factors 1).
+//
+// VOTE makes that choice for all the lanes that arrive together (a warp vote)
+// instead of lane by lane: a warp across the edge of the bulk would otherwise
+// run both paths one after the other.  Measured where layer edges do not fall
+// on warp boundaries: the TMA-staged batched kernel 9.5 % faster on 256 mixed
+// lattices, the one-step pair kernel and the single-lattice TMA kernel 5 %
+// faster with a 37-cell layer (1024^2, 4096^2), no change with aligned edges.
+// In the plain-load two-step kernel it raised the register count (FP16: 64 to
+// 98, FP32: 77 to 90) and cost 16-25 %, so that kernel decides lane by lane.
+template <int VAR, bool UB = true, bool VOTE = false>
 __device__ __forceinline__ void collide_lanes(F2 (&v)[9], int xa, int xb, int y,
                                               const StepConst<F2>& k,
                                               const AxisCoef<float>* __restrict__ tx,
                                               const AxisCoef<float>* __restrict__ ty) {
-    if (VAR == kNone || (xa >= k.bulk_x0 && xa < k.bulk_x1 && xb >= k.bulk_x0 &&
-                         xb < k.bulk_x1 && y >= k.bulk_y0 && y < k.bulk_y1)) {
+    const unsigned lanes = VOTE ? __activemask() : 0u;
+    const bool bulk = xa >= k.bulk_x0 && xa < k.bulk_x1 && xb >= k.bulk_x0 && xb < k.bulk_x1 &&
+                      y >= k.bulk_y0 && y < k.bulk_y1;
+    if (VAR == kNone || (VOTE ? __all_sync(lanes, bulk) : bulk)) {
         collide_bulk<F2, UB>(v, k);
         return;
     }
     const AxisCoef<float> a0 = load_coef(tx, xa), a1 = load_coef(tx, xb);
     const AxisCoef<float> ay = load_coef(ty, y);
     const float c0 = fmaxf(a0.chi, ay.chi), c1 = fmaxf(a1.chi, ay.chi);
-    if (c0 > 0.0f || c1 > 0.0f) {
+    const bool layer = c0 > 0.0f || c1 > 0.0f;
+    if (VOTE ? __any_sync(lanes, layer) : layer) {
         if (VAR == kViscous)  // the tables' chi slot holds the layer fraction r
             collide_viscous<F2, UB>(v, f2(c0, c1), k);
         else
@@ -234,12 +247,12 @@ __device__ __forceinline__ void collide_lanes(F2 (&v)[9], int xa, int xb, int y,
 
 // The pair (x, x + 1) of row y; the phantom cell x + 1 = nx of an odd-width
 // lattice borrows the coefficients of its neighbour (its result is dropped).
-template <int VAR, bool UB = true>
+template <int VAR, bool UB = true, bool VOTE = false>
 __device__ __forceinline__ void collide_pair(F2 (&v)[9], int x, int y, int nx,
                                              const StepConst<F2>& k,
                                              const AxisCoef<float>* __restrict__ tx,
                                              const AxisCoef<float>* __restrict__ ty) {
-    collide_lanes<VAR, UB>(v, x, min(x + 1, nx - 1), y, k, tx, ty);
+    collide_lanes<VAR, UB, VOTE>(v, x, min(x + 1, nx - 1), y, k, tx, ty);
 }
 
 template <typename T, int VAR, int BC>
@@ -267,7 +280,7 @@ __global__ void __launch_bounds__(kPairBX* kPairBY)
         const float* src_pop = (BC == kChannel && x == 0) ? ls.pop + 9 * ls.t_off : nullptr;
         pull_pair_edge<T, BC>(src, plane, pitch, x, y, nx, ny, v, src_pop);
     }
-    collide_pair<VAR, UnbiasedScale<T>::value>(v, x, y, nx, k, tx, ty);
+    collide_pair<VAR, UnbiasedScale<T>::value, true>(v, x, y, nx, k, tx, ty);
     if (x + 1 < nx)
         store_pair<T>(dst, plane, o, v);
     else

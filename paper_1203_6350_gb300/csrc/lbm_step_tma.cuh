@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(TmaLaunch<T>::threads, TmaLaunch<T>::min_block
             const bool row_in = y >= 0 && y < ny;
             const bool keep_a = row_in && x >= 0 && x < nx;
             const bool keep_b = row_in && x + 1 >= 0 && x + 1 < nx;
-            collide_lanes<VAR, UB>(v, min(max(x, 0), nx - 1), min(max(x + 1, 0), nx - 1),
-                                   min(max(y, 0), ny - 1), k, tx, ty);
+            collide_lanes<VAR, UB, true>(v, min(max(x, 0), nx - 1), min(max(x + 1, 0), nx - 1),
+                                         min(max(y, 0), ny - 1), k, tx, ty);
             if (!(keep_a && keep_b)) {  // lanes outside the lattice hold the wall value 0
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(TmaLaunch<T>::threads, TmaLaunch<T>::min_block
             F2 v[9];
             pull_pair_interior<float, true>(r1, kR1Plane, kR1W,
                                             static_cast<unsigned>((qy + 1) * kR1W + 2 * qx + 2), v);
-            collide_pair<VAR, UB>(v, x, y, nx, k, tx, ty);
+            collide_pair<VAR, UB, true>(v, x, y, nx, k, tx, ty);
             const unsigned o = static_cast<unsigned>(y * pitch + x);
             if (x + 1 < nx)
                 store_pair<T>(dst, plane, o, v);

@@ -590,7 +590,7 @@ class Lattice:
 
     @property
     def tma_staging(self) -> bool:
-        """Whether two-step launches stage their input by TMA (FP32, Dirichlet)."""
+        """Whether two-step launches stage their input by TMA (Dirichlet; FP32, FP16 or BF16)."""
         return lbm_tma_staging(self.h) == 1
 
     @tma_staging.setter
@@ -690,7 +690,10 @@ class Lattice:
     def arithmetic(self) -> str:
         """"native" (FP32 collision for FP32/16-bit storage, FP64 for FP64) or
         "compensated" (FP32 storage, float-float collision)."""
-        return ARITHMETIC_NAMES[check(lbm_get_arithmetic(self.h), self.h, "lbm_get_arithmetic")]
+        rc = lbm_get_arithmetic(self.h)
+        if rc < 0:  # a non-negative return is the mode, not a warning
+            raise LbmError(rc, f"lbm_get_arithmetic: {lbm_last_error(self.h)}")
+        return ARITHMETIC_NAMES[rc]
 
     @arithmetic.setter
     def arithmetic(self, name: str) -> None:

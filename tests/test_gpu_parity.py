@@ -25,6 +25,7 @@ of the field's largest magnitude, so that one wrong row or tile seam cannot
 hide in the norm of a large lattice.
 """
 import math
+import warnings
 
 import numpy as np
 import pytest
@@ -498,7 +499,9 @@ def test_arithmetic_modes_and_their_limits():
     with lbm.Lattice.from_workload(w, storage="f32") as lat:
         lat.cells_per_thread = 2
         lat.arithmetic = "compensated"
-        assert lat.arithmetic == "compensated" and lat.cells_per_thread == 1
+        with warnings.catch_warnings():
+            warnings.simplefilter("error")  # reading the mode is not a warning
+            assert lat.arithmetic == "compensated" and lat.cells_per_thread == 1
         assert lat.steps_per_launch == 1
         for bad in (lambda: setattr(lat, "cells_per_thread", 2),
                     lambda: setattr(lat, "steps_per_launch", 2)):
