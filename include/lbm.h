@@ -23,8 +23,8 @@
  *  - Fields passed in or out are FP64, [ny][nx] row-major (x fastest).
  *  - The lattice is double-buffered in device memory as 9 planes per buffer
  *    of populations stored as DEVIATIONS g_i = f_i - f^eq_i(rho0, u0) from the
- *    far-field state given to lbm_create (FP64, FP32, or 16-bit with a fixed
- *    power-of-two scale per plane).
+ *    far-field state given to lbm_create (FP64, FP32, FP16 with a fixed
+ *    power-of-two scale per plane, or BF16).
  *  - "Time" counts steps; lbm_init_equilibrium sets time 0.
  *  - Boundary: LBM_BC_DIRICHLET_EQ makes every population that would stream
  *    in from outside equal to f^eq(rho0, u0), at every time level including

@@ -42,9 +42,10 @@ __host__ __device__ constexpr int cy(int i) {
     return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
 }
 
-// 16-bit storage keeps q_i = g_i * 2^e_i: a power of two per plane that puts
+// FP16 storage keeps q_i = g_i * 2^e_i: a power of two per plane that puts
 // g_i / w_i (w = 4/9, 1/9, 1/36) near the middle of the format's range and is
-// exact to apply.
+// exact to apply.  BF16 has FP32's exponent range, where such a scale changes
+// no rounding (short of FP32 subnormals), so it stores g_i itself.
 __host__ __device__ constexpr int scale_exp(int i) { return 8 + (i == 0 ? 1 : i < 5 ? 3 : 5); }
 __host__ __device__ constexpr float pow2f(int e) {
     float r = 1.0f;
@@ -87,11 +88,11 @@ struct Codec<__nv_bfloat16> {
     using CT = float;
     template <int I>
     __device__ static __forceinline__ float dec(__nv_bfloat16 v) {
-        return __bfloat162float(v) * pow2f(-scale_exp(I));
+        return __bfloat162float(v);
     }
     template <int I>
     __device__ static __forceinline__ __nv_bfloat16 enc(float v) {
-        return __float2bfloat16_rn(v * pow2f(scale_exp(I)));
+        return __float2bfloat16_rn(v);
     }
 };
 

@@ -36,25 +36,32 @@ struct PairCodec<float> {
     __device__ static __forceinline__ float enc_lo(F2 v) { return f2_lo(v); }
 };
 
-// 16-bit formats: q_i = g_i 2^e_i (see scale_exp); the scale is applied in
-// FP32 on the pair, the format conversion packs or unpacks both cells.
+// 16-bit formats, FP16 as q_i = g_i 2^e_i (see scale_exp), BF16 as g_i.  FP16
+// decodes each element with one mixed-precision FMA, q_i * 2^-e_i + (-0) in
+// FP32: exact, the sign of a zero kept; it encodes by scaling the pair in FP32
+// and converting both cells in one instruction.  BF16 converts both ways with
+// no scale.
 template <typename H, typename H2>
 struct PairCodec16 {
     using Raw2 = unsigned;
+    static constexpr bool kScaled = std::is_same<H, __half>::value;
     template <int I>
     __device__ static __forceinline__ F2 dec2(Raw2 w) {
         H2 h;
         memcpy(&h, &w, sizeof w);
-        return mul(f2(to_f(h.x), to_f(h.y)), lit<F2>(pow2f(-scale_exp(I))));
+        return dec11<I>(h.x, h.y);
     }
     template <int I>
     __device__ static __forceinline__ F2 dec11(H a, H b) {
-        return mul(f2(to_f(a), to_f(b)), lit<F2>(pow2f(-scale_exp(I))));
+        if constexpr (kScaled)
+            return f2(dec_scaled<I>(a), dec_scaled<I>(b));
+        else
+            return f2(to_f(a), to_f(b));
     }
     template <int I>
     __device__ static __forceinline__ Raw2 enc2(F2 v) {
-        const F2 s = mul(v, lit<F2>(pow2f(scale_exp(I))));
-        const H2 h = pack(f2_lo(s), f2_hi(s));
+        if constexpr (kScaled) v = mul(v, lit<F2>(pow2f(scale_exp(I))));
+        const H2 h = pack(f2_lo(v), f2_hi(v));
         Raw2 w;
         memcpy(&w, &h, sizeof w);
         return w;
@@ -62,6 +69,17 @@ struct PairCodec16 {
     template <int I>
     __device__ static __forceinline__ H enc_lo(F2 v) {
         return Codec<H>::template enc<I>(f2_lo(v));
+    }
+    // FP16 q times 2^-scale_exp(I) (a normal FP16 power of two) in FP32.
+    template <int I>
+    __device__ static __forceinline__ float dec_scaled(__half q) {
+        static_assert(scale_exp(I) <= 14, "2^-e must be a normal FP16 number");
+        const unsigned short s = static_cast<unsigned short>((15 - scale_exp(I)) << 10);
+        float r;
+        asm("fma.rn.f32.f16 %0, %1, %2, %3;"
+            : "=f"(r)
+            : "h"(__half_as_ushort(q)), "h"(s), "f"(-0.0f));
+        return r;
     }
     __device__ static __forceinline__ float to_f(__half h) { return __half2float(h); }
     __device__ static __forceinline__ float to_f(__nv_bfloat16 h) { return __bfloat162float(h); }
