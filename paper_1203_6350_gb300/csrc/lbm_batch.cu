@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                 collide_pair<VAR, true, true>(v, x, y, nx, sd.k, sd.tx, sd.ty);
                 const unsigned o = static_cast<unsigned>(y * pitch + x);
                 if (x + 1 < nx)
-                    store_pair<float>(dst, plane, o, v);
+                    store_pair<float, true>(dst, plane, o, v);
                 else
                     store_lo<float>(dst, plane, o, v);
             }

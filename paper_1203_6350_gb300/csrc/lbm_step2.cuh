@@ -185,25 +185,32 @@ __device__ __forceinline__ void pull_pair_edge(const T* __restrict__ s, unsigned
     v[8] = pull_pair_one<T, BC, 8>(s, plane, pitch, x, y, nx, ny, src_pop);
 }
 
-template <typename T, int I>
+// STREAM stores with the evict-first policy (st.global.cs): for a lattice far
+// larger than L2, whose output is not read again before L2 has turned over,
+// so that it does not push out input lines a neighbouring tile still needs.
+template <typename T, int I, bool STREAM = false>
 __device__ __forceinline__ void store_pair_plane(T* __restrict__ d, unsigned plane, unsigned o,
                                                  const F2 (&v)[9]) {
-    *reinterpret_cast<typename PairCodec<T>::Raw2*>(d + (I * plane + o)) =
-        PairCodec<T>::template enc2<I>(v[I]);
+    auto* p = reinterpret_cast<typename PairCodec<T>::Raw2*>(d + (I * plane + o));
+    const typename PairCodec<T>::Raw2 w = PairCodec<T>::template enc2<I>(v[I]);
+    if constexpr (STREAM)
+        __stcs(p, w);
+    else
+        *p = w;
 }
 
-template <typename T>
+template <typename T, bool STREAM = false>
 __device__ __forceinline__ void store_pair(T* __restrict__ d, unsigned plane, unsigned o,
                                            const F2 (&v)[9]) {
-    store_pair_plane<T, 0>(d, plane, o, v);
-    store_pair_plane<T, 1>(d, plane, o, v);
-    store_pair_plane<T, 2>(d, plane, o, v);
-    store_pair_plane<T, 3>(d, plane, o, v);
-    store_pair_plane<T, 4>(d, plane, o, v);
-    store_pair_plane<T, 5>(d, plane, o, v);
-    store_pair_plane<T, 6>(d, plane, o, v);
-    store_pair_plane<T, 7>(d, plane, o, v);
-    store_pair_plane<T, 8>(d, plane, o, v);
+    store_pair_plane<T, 0, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 1, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 2, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 3, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 4, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 5, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 6, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 7, STREAM>(d, plane, o, v);
+    store_pair_plane<T, 8, STREAM>(d, plane, o, v);
 }
 
 // Store only cell x of the pair (the last column of an odd-width lattice).

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(TmaLaunch<T>::threads, TmaLaunch<T>::min_block
             collide_pair<VAR, UB, true>(v, x, y, nx, k, tx, ty);
             const unsigned o = static_cast<unsigned>(y * pitch + x);
             if (x + 1 < nx)
-                store_pair<T>(dst, plane, o, v);
+                store_pair<T, true>(dst, plane, o, v);
             else
                 store_lo<T>(dst, plane, o, v);
         }
