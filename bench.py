@@ -556,7 +556,7 @@ def roofline_large(peaks, side: int = 4096, steps: int = 100):
             "two_steps_plain_loads": out["two_steps_plain_loads"],
             "one_step_per_launch": out["one_step_per_launch"],
             "one_cell_per_thread": out["one_cell_per_thread"],
-            "traffic_profile": "profiles/step_tb2_kernel_f32_4096x4096_full.md"}
+            "traffic_profile": "profiles/two_step_kernels_2048_to_16384_traffic.md"}
 
 
 def run_line_source(peaks):
