@@ -231,3 +231,23 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.strip()
+
+
+def test_arithmetic_property_reads_the_mode_without_a_warning(lib, monkeypatch):
+    """Lattice.arithmetic turns lbm_get_arithmetic's non-negative return into the
+    mode's name (1 is "compensated", not a warning code) and raises on an error."""
+    import warnings
+
+    from paper_1203_6350_gb300 import lbm
+
+    lat = object.__new__(lbm.Lattice)
+    lat.h = None
+    for code, name in lbm.ARITHMETIC_NAMES.items():
+        monkeypatch.setattr(lbm, "lbm_get_arithmetic", lambda h, c=code: c)
+        with warnings.catch_warnings():
+            warnings.simplefilter("error")
+            assert lat.arithmetic == name
+    monkeypatch.setattr(lbm, "lbm_get_arithmetic", lambda h: lbm.LBM_ERR_ARG)
+    with pytest.raises(lbm.LbmError):
+        _ = lat.arithmetic
+    lat.h = None  # nothing to close
