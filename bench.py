@@ -796,8 +796,9 @@ def measure_l2_copy_peak(dev, nbytes: int, copies: int = 64, reps: int = 30) -> 
 def measure_probe_copy(dev, nbytes: int, iters: int = 256, reps: int = 10) -> dict:
     """Copy rate over two device buffers of `nbytes` each from the library's
     bandwidth probe (lbm_probe_copy): one launch that copies a into b and back
-    `iters` times, every CTA on its own slice, so no launch gap falls between
-    the passes; best of `reps` launches, CUDA events.  Bytes = read + write."""
+    `iters` times, each thread on its own grid-strided 16-byte words, so no
+    launch gap falls between the passes; best of `reps` launches, CUDA events.
+    Bytes = read + write."""
     import torch
 
     from paper_1203_6350_gb300 import lbm
