@@ -270,26 +270,33 @@ __device__ __forceinline__ void collide_bulk(V (&g)[9], const StepConst<V>& k) {
 // The comparison sponge of Sec. 4.1 ("viscosity absorbing"): no damping term,
 // and in the layer every non-conserved rate falls linearly toward 1,
 // s_k' = s_k + (1 - s_k) r, with r in [0, 1] the layer fraction of the cell.
+// Written as the plain relaxation with keep' = (1 - s')/D = keep (1 - r) and
+// take' = +-s'/D = take +- keep r, so that r = 0 gives keep and take exactly
+// and the result is collide_bulk's bit for bit.
 template <typename V, bool UB = true>
 __device__ __forceinline__ void collide_viscous(V (&g)[9], V r, const StepConst<V>& k) {
     V m[9];
     moments9(g, m);
     V e3, e4, e7, e8;
     quad_eq(m[0], m[1], m[2], k, e3, e4, e7, e8);
-    V sk[9];
+    const V nr = lit<V>(0.0f) - r;
+    V kp[9], tp[9];
 #pragma unroll
-    for (int i = 3; i < 9; ++i) sk[i] = fmadd(k.oms[i], r, k.s[i]);
-    // m_k^+ = m_k + s_k' (m_k^eq - m_k); rows 5, 6: m^eq = -j
+    for (int i = 3; i < 9; ++i) {
+        kp[i] = fmadd(k.keep[i], nr, k.keep[i]);
+        // rows 5, 6 carry s' with a minus sign (their m^eq is -j)
+        tp[i] = fmadd(k.keep[i], (i == 5 || i == 6) ? nr : r, k.take[i]);
+    }
     V a[9];
     a[0] = scale_conserved<UB>(m[0], k, 0);
     a[1] = scale_conserved<UB>(m[1], k, 1);
     a[2] = scale_conserved<UB>(m[2], k, 2);
-    a[3] = mul(fmadd(sk[3], e3 - m[3], m[3]), k.dinv[3]);
-    a[4] = mul(fmadd(sk[4], e4 - m[4], m[4]), k.dinv[4]);
-    a[5] = mul(m[5] - mul(sk[5], m[1] + m[5]), k.dinv[5]);
-    a[6] = mul(m[6] - mul(sk[6], m[2] + m[6]), k.dinv[6]);
-    a[7] = mul(fmadd(sk[7], e7 - m[7], m[7]), k.dinv[7]);
-    a[8] = mul(fmadd(sk[8], e8 - m[8], m[8]), k.dinv[8]);
+    a[3] = fmadd(kp[3], m[3], mul(tp[3], e3));
+    a[4] = fmadd(kp[4], m[4], mul(tp[4], e4));
+    a[5] = fmadd(kp[5], m[5], mul(tp[5], m[1]));
+    a[6] = fmadd(kp[6], m[6], mul(tp[6], m[2]));
+    a[7] = fmadd(kp[7], m[7], mul(tp[7], e7));
+    a[8] = fmadd(kp[8], m[8], mul(tp[8], e8));
     back9_scaled(a, g);
 }
 
@@ -333,14 +340,13 @@ __device__ __forceinline__ void collide_layer(V (&g)[9], V chi, V rn, V rm,
         ct[6] = ndy;
     }
     V a[9];
-    // conserved rows (UB): the numerator m + s_c (E - m) + chi T first, then 1/D
-    if (UB) {
+    // conserved rows: the numerator m + s_c (E - m) + chi T first, then 1/D (with
+    // chi = 0: E = m and T = 0, so this is collide_bulk's scaling of m itself)
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            a[i] = scale_conserved<UB>(fmadd(k.s[i], E[i] - m[i], m[i]) + ct[i], k, i);
-    }
+    for (int i = 0; i < 3; ++i)
+        a[i] = scale_conserved<UB>(fmadd(k.s[i], E[i] - m[i], m[i]) + ct[i], k, i);
 #pragma unroll
-    for (int i = UB ? 3 : 0; i < 9; ++i) {
+    for (int i = 3; i < 9; ++i) {
         if (VAR == kTypeIII && i >= 7)
             a[i] = fmadd(k.keep[i], m[i], mul(k.take[i], E[i]));
         else

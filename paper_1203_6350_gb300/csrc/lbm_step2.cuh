@@ -230,9 +230,11 @@ __device__ __forceinline__ void store_lo(T* __restrict__ d, unsigned plane, unsi
 
 // Collide a pair of cells of row y at columns xa (lo lane) and xb (hi lane),
 // both inside the lattice.  Both cells take the damping path as soon as one
-// of them lies in the layer; with chi = 0 that path reduces to the plain
-// relaxation (rho* = rho, j* = j, no damping term; the bulk's tables hold
-// chi = 0 and Guo factors 1).
+// of them lies in the layer; with chi = 0 that path is the plain relaxation
+// bit for bit (rho* = rho, j* = j, no damping term, the bulk's tables holding
+// chi = 0 and Guo factors 1; collide_layer and collide_viscous are written so
+// that the arithmetic coincides), so where the choice is made changes no
+// result.
 //
 // VOTE makes that choice for all the lanes that arrive together (a warp vote)
 // instead of lane by lane: a warp across the edge of the bulk would otherwise

@@ -57,6 +57,37 @@ def test_tma_staging_is_bit_identical_to_plain_loads(shape, variant, storage):
     np.testing.assert_array_equal(a, b)
 
 
+def _edged(nx, ny, variant, width, seed, steps):
+    """A lattice with a real bulk: chi = 0.4 (d / width)^2 in a layer `width`
+    cells deep on every side and zero inside, random deviations everywhere."""
+    rng = np.random.default_rng(seed)
+
+    def ramp(n):
+        i = np.arange(n)
+        d = np.maximum(np.maximum(width - i, i - (n - 1 - width)), 0) / width
+        return 0.4 * d * d
+
+    return wl.Workload(name=f"edged-{nx}x{ny}", nx=nx, ny=ny,
+                       s=np.array([1.6, 1.6, 1.6, 1.1, 1.2, 1.3, 1.3, 1.9, 1.9]),
+                       variant=variant, bc="dirichlet", n=0.4, m=0.6, rho0=1.0,
+                       u0=(0.04, -0.02), rho_f=1.002, u_f=(0.05, -0.01),
+                       chi_x=ramp(nx), chi_y=ramp(ny),
+                       rho_dev=1e-3 * rng.standard_normal((ny, nx)), steps=steps, storage="f32")
+
+
+@pytest.mark.parametrize("variant", ["I", "II", "III", "viscous"])
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev"])
+def test_a_layer_edge_inside_a_warp_changes_no_bit(variant, storage):
+    """The TMA kernel chooses between the bulk and the layer collision per warp,
+    the plain-load two-step kernel per pair; with the edge of the bulk inside
+    warps (a 37-cell layer) their stored states still agree bit for bit, since
+    the layer collision at chi = 0 is the bulk collision exactly."""
+    w = _edged(300, 200, variant, 37, seed=11, steps=11)
+    a = _state(w, True, w.steps, storage=storage)
+    b = _state(w, False, w.steps, storage=storage)
+    np.testing.assert_array_equal(a, b)
+
+
 def test_tma_staging_across_graph_chunks():
     """150 steps as 64 + 64 + 22: graph replays of 32 two-step launches and a
     one-step remainder."""
