@@ -63,9 +63,10 @@ bool encode_tma_map(CUtensorMap* map, void* base, const Geometry& g, int elem, b
     const CUtensorMapDataType dt = elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : bf16    ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    // elements outside the extent read as zero (OOB fill "none")
+    // elements outside the extent read as zero (OOB fill "none"); L2 fills from DRAM in
+    // 256-byte units (measured 0.6 % ahead of 128 at 4096^2, level at 16384^2 and batched)
     return f(map, dt, 3, base, dim, stride, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
