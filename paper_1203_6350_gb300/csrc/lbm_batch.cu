@@ -202,12 +202,17 @@ struct PairTile {
                 pull_pair_edge<T, kPeriodic>(src, plane, pitch, x, y, nx, ny, v);
             else
                 pull_pair_edge<T, kDirichlet>(src, plane, pitch, x, y, nx, ny, v);
+            const auto& k = sd.k;  // the collisions choose bulk or layer per warp (VOTE)
             switch (sd.variant) {
-                case kTypeI: collide_pair<kTypeI, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeII: collide_pair<kTypeII, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kTypeIII: collide_pair<kTypeIII, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                case kViscous: collide_pair<kViscous, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
-                default: collide_pair<kNone, UB, true>(v, x, y, nx, sd.k, sd.tx, sd.ty); break;
+                case kTypeI: collide_pair<kTypeI, UB, true>(v, x, y, nx, k, sd.tx, sd.ty); break;
+                case kTypeII: collide_pair<kTypeII, UB, true>(v, x, y, nx, k, sd.tx, sd.ty); break;
+                case kTypeIII:
+                    collide_pair<kTypeIII, UB, true>(v, x, y, nx, k, sd.tx, sd.ty);
+                    break;
+                case kViscous:
+                    collide_pair<kViscous, UB, true>(v, x, y, nx, k, sd.tx, sd.ty);
+                    break;
+                default: collide_pair<kNone, UB, true>(v, x, y, nx, k, sd.tx, sd.ty); break;
             }
             if (x + 1 < nx)
                 store_pair<T>(dst, plane, o, v);
