@@ -242,8 +242,10 @@ __device__ __forceinline__ void store_lo(T* __restrict__ d, unsigned plane, unsi
 // on warp boundaries: the TMA-staged batched kernel 9.5 % faster on 256 mixed
 // lattices, the one-step pair kernel and the single-lattice TMA kernel 5 %
 // faster with a 37-cell layer (1024^2, 4096^2), no change with aligned edges.
-// In the plain-load two-step kernel it raised the register count (FP16: 64 to
-// 98, FP32: 77 to 90) and cost 16-25 %, so that kernel decides lane by lane.
+// In the plain-load two-step kernel the vote raises the register count (FP16:
+// 64 to 98, FP32: 77 to 90, 16-25 % slower as compiled freely); with FP32 held
+// to three blocks per SM it gains, for 16-bit storage that kernel decides pair
+// by pair (kTbVote).
 template <int VAR, bool UB = true, bool VOTE = false>
 __device__ __forceinline__ void collide_lanes(F2 (&v)[9], int xa, int xb, int y,
                                               const StepConst<F2>& k,

@@ -32,6 +32,14 @@ constexpr int kR1H = kTbH + 2;      // R1: rows y0 - 1 .. y0 + kTbH
 constexpr int kR1Pairs = kR1W / 2;  // pairs per R1 row
 constexpr int kR1Plane = kR1W * kR1H;  // elements per plane in shared memory
 
+// Whether the two-step tile chooses bulk or layer collision per warp (VOTE of
+// collide_lanes).  FP32: yes, with the kernel held to three blocks per SM
+// (80 registers): 2.6 % faster at 2048^2 with a 37-cell layer, level with a
+// 128-cell one.  16-bit: per pair, which keeps the kernel at 64 registers and
+// four blocks per SM; the vote measured 0.2-0.9 % slower there.
+template <typename T>
+constexpr bool kTbVote = sizeof(T) == 4;
+
 // R1 in FP32 (44,064 bytes, inside the default 48 KB window) for every format.
 template <typename T>
 constexpr size_t tb_smem_bytes() {
@@ -88,7 +96,7 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
         if (x > 0 && x + 2 < nx && y > 0 && y + 1 < ny) {
             pull_pair_interior<T>(src, plane, static_cast<unsigned>(pitch),
                                   static_cast<unsigned>(y * pitch + x), v);
-            collide_lanes<VAR, UnbiasedScale<T>::value>(v, x, x + 1, y, k, tx, ty);
+            collide_lanes<VAR, UnbiasedScale<T>::value, kTbVote<T>>(v, x, x + 1, y, k, tx, ty);
         } else {
             int ca = x, cb = x + 1, cy = y;
             if (BC == kPeriodic) {
@@ -105,7 +113,7 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
                 cy = min(max(cy, 0), ny - 1);
             }
             pull_lanes<T, BC>(src, plane, pitch, ca, cb, cy, nx, ny, v);
-            collide_lanes<VAR, UnbiasedScale<T>::value>(v, ca, cb, cy, k, tx, ty);
+            collide_lanes<VAR, UnbiasedScale<T>::value, kTbVote<T>>(v, ca, cb, cy, k, tx, ty);
             if (!(keep_a && keep_b)) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
@@ -124,7 +132,7 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
         F2 v[9];
         pull_pair_interior<float, true>(sm, kR1Plane, kR1W,
                                         static_cast<unsigned>((qy + 1) * kR1W + 2 * qx + 2), v);
-        collide_pair<VAR, UnbiasedScale<T>::value>(v, x, y, nx, k, tx, ty);
+        collide_pair<VAR, UnbiasedScale<T>::value, kTbVote<T>>(v, x, y, nx, k, tx, ty);
         const unsigned o = static_cast<unsigned>(y * pitch + x);
         if (x + 1 < nx)
             store_pair<T>(dst, plane, o, v);
@@ -134,8 +142,10 @@ __device__ __forceinline__ void tb2_tile(const T* __restrict__ src, T* __restric
     __syncthreads();
 }
 
+// Blocks per SM the registers must allow: three with the vote (FP32); 0 leaves
+// the choice to the compiler (64 registers for 16-bit storage, four blocks).
 template <typename T, int VAR, int BC>
-__global__ void __launch_bounds__(kTbThreads)
+__global__ void __launch_bounds__(kTbThreads, kTbVote<T> ? 3 : 0)
     step_tb2_kernel(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
                     unsigned plane, StepConst<F2> k, const AxisCoef<float>* __restrict__ tx,
                     const AxisCoef<float>* __restrict__ ty) {
